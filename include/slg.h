@@ -1,0 +1,196 @@
+/*
+ * libslg -- s-line graphs of non-uniform hypergraphs on one GB300 (sm_103a).
+ *
+ * C ABI. Plain pointers and sizes only; no C++ or framework types cross this
+ * boundary. Every call returns an slg_status (0 = SLG_OK); on failure the
+ * calling thread's message is available from slg_last_error().
+ *
+ * The problem (Liu et al., "High-order Line Graphs of Non-uniform
+ * Hypergraphs", arXiv 2201.11326):
+ *   - a hypergraph H = <V, E> has n vertices and an indexable family of m
+ *     hyperedges e_0..e_{m-1}, each a subset of V; two hyperedges with equal
+ *     vertex sets are distinct by index (Section I);
+ *   - e_i and e_j are s-incident when |e_i ∩ e_j| >= s, s >= 1 (Section II-B);
+ *   - the s-line graph L_s(H) joins every s-incident pair; its weighted form
+ *     is L = H^T H with the diagonal ignored (Section II-B);
+ *   - Algorithm 2 (Section III-C) states the computation: input (H, s),
+ *     output the edge list of L_s(H), each pair once (i < j).
+ *
+ * Conventions shared by every call:
+ *   - Input incidence: int32 CSR over hyperedges. off[m+1] with off[0] = 0
+ *     and off non-decreasing; idx[off[m]] with row i = idx[off[i]..off[i+1])
+ *     listing the vertices of e_i in strictly increasing order, each in
+ *     [0, n). Rows may be empty; vertices need not be covered.
+ *   - Output: the canonical edge list of L_s(H): triples (I[p], J[p], O[p])
+ *     with I[p] < J[p], O[p] = |e_I ∩ e_J| >= s (the exact overlap, not capped
+ *     at s), sorted by (I, J), as three int32 arrays (structure of arrays).
+ *     Hyperedge ids are the caller's 0-based ids; there is no relabelling.
+ *   - Pointers to arrays may be host memory (pageable or pinned) or device
+ *     memory of the current device; the library detects which. The caller
+ *     keeps ownership of every array it passes in; the library never frees
+ *     or retains them past the call.
+ *   - All device work of a graph runs on the CUDA stream given to slg_load
+ *     (NULL = the legacy default stream). Calls that return host-visible
+ *     results synchronise that stream before returning.
+ *   - A graph handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef SLG_H
+#define SLG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t slg_status;
+
+#define SLG_OK 0
+#define SLG_EINVAL 1    /* bad argument: malformed CSR, s < 1, bad range, NULL */
+#define SLG_ENOMEM 2    /* device memory exhausted */
+#define SLG_ECUDA 3     /* a CUDA runtime error (message in slg_last_error) */
+#define SLG_ETIMEOUT 4  /* a bounded device wait gave up */
+#define SLG_ECAPACITY 5 /* caller's output buffer too small; *pairs holds the need */
+#define SLG_EBUSY 6     /* resource in use */
+#define SLG_EINTERNAL 7 /* an internal consistency check failed */
+
+typedef struct slg_graph slg_graph;
+
+/* Message describing the last failure on the calling thread ("" if none).
+ * The string stays valid until the next libslg call on the same thread. */
+const char* slg_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t slg_version(void);
+
+/*
+ * slg_load -- upload and validate a hypergraph, build its dual.
+ *
+ * Implements the input side of Algorithm 2 (Section III-C) and the dual /
+ * transposed incidence H^T of Section II-A, which the "ikj" order of
+ * Section III-B walks (for k in H^T.Adj[i], for j in H.Adj[k]).
+ *
+ *   off, idx  : CSR as described above (m+1 and off[m] int32 entries), host
+ *               or device memory; copied, the caller may free them after.
+ *   m, n      : number of hyperedges and vertices (m, n >= 0).
+ *   stream    : cudaStream_t (as void*) for all device work of this graph.
+ *   out       : receives the new handle (release with slg_free).
+ *
+ * Errors: SLG_EINVAL if the CSR is malformed (off[0] != 0, a decreasing
+ * offset, an id outside [0, n), a row not strictly increasing -- which
+ * includes a repeated vertex, since hyperedges are sets), SLG_ENOMEM,
+ * SLG_ECUDA. On error *out is NULL and nothing is retained.
+ */
+slg_status slg_load(const int32_t* off, const int32_t* idx, int32_t m, int32_t n,
+                    void* stream, slg_graph** out);
+
+/* Release a handle and all its device memory. NULL is ignored. */
+void slg_free(slg_graph* g);
+
+/* Sizes of a loaded graph (any output may be NULL). */
+slg_status slg_graph_info(const slg_graph* g, int32_t* m, int32_t* n, int64_t* nnz);
+
+/*
+ * slg_transpose_copy -- copy out the dual incidence H^T (Section II-A):
+ * offT[n+1] and idxT[nnz] where adj(v) = idxT[offT[v]..offT[v+1]) lists the
+ * hyperedges containing v in increasing id. Host or device destinations.
+ */
+slg_status slg_transpose_copy(slg_graph* g, int32_t* offT, int32_t* idxT);
+
+/*
+ * slg_count -- exact size of L_s(H) and the algorithmic work, without
+ * writing the list (the counting half of Algorithm 2, Section III-C).
+ *
+ *   pairs  : receives |L_s(H)|, the number of pairs i < j with
+ *            |e_i ∩ e_j| >= s (may be NULL).
+ *   wedges : receives W_s = sum over v of C(d_s(v), 2), where d_s(v) counts
+ *            the hyperedges of size >= s containing v: the number of
+ *            increments of the overlap counters of Algorithm 2 when both
+ *            sides are pruned to E_s (Section III-E) (may be NULL).
+ * Errors: SLG_EINVAL for s < 1.
+ */
+slg_status slg_count(slg_graph* g, int32_t s, int64_t* pairs, int64_t* wedges);
+
+/*
+ * slg_bound -- cheap upper bound floor(W_s / s) on |L_s(H)|: every s-incident
+ * pair accounts for at least s wedges (Section III-E). Needs no counting pass.
+ */
+slg_status slg_bound(slg_graph* g, int32_t s, int64_t* pairs_ub);
+
+/*
+ * slg_row_offsets -- per-row output offsets of L_s(H): rowoff[i] is the
+ * position of row i's first pair in the canonical list, rowoff[m] = |L_s|.
+ * rowoff has m+1 int64 entries (host or device).
+ */
+slg_status slg_row_offsets(slg_graph* g, int32_t s, int64_t* rowoff);
+
+/*
+ * slg_build -- the whole edge list of L_s(H) (Algorithm 2, Section III-C).
+ *
+ *   I, J, O : output arrays of at least cap int32 entries each, host or
+ *             device memory (all three of the same kind).
+ *   cap     : capacity in pairs.
+ *   pairs   : receives |L_s(H)|.
+ * Errors: SLG_ECAPACITY when |L_s(H)| > cap (*pairs is set, nothing is
+ * written), SLG_EINVAL for s < 1.
+ */
+slg_status slg_build(slg_graph* g, int32_t s, int32_t* I, int32_t* J, int32_t* O, int64_t cap,
+                     int64_t* pairs);
+
+/*
+ * slg_build_window -- the pairs of rows [row_begin, row_end) only: the
+ * contiguous slice rowoff[row_begin]..rowoff[row_end] of the canonical list.
+ * Lets a list larger than device memory be produced in pieces; rows are the
+ * independent units of Algorithm 2's parallel loop (Section III-C).
+ *
+ *   digest      : if not NULL, receives the sum over the slice of
+ *                 mix(mix((i<<32)|k) ^ ((j<<32)|o)) mod 2^64, with k the
+ *                 position of the pair inside its row and mix the SplitMix64
+ *                 output function (Steele, Lea, Flood 2014).
+ *   row_digests : if not NULL, receives the same sum per row
+ *                 (row_end - row_begin uint64 entries, host or device).
+ * Errors: SLG_EINVAL for a bad range or s < 1; SLG_ECAPACITY as slg_build.
+ */
+slg_status slg_build_window(slg_graph* g, int32_t s, int32_t row_begin, int32_t row_end,
+                            int32_t* I, int32_t* J, int32_t* O, int64_t cap, int64_t* pairs,
+                            uint64_t* digest, uint64_t* row_digests);
+
+/*
+ * slg_plan_windows -- split rows [0, m) into consecutive windows whose pair
+ * count is at most cap each: row_splits[0] = 0 < ... < row_splits[w] = m.
+ * A single row with more than cap pairs makes the call fail with
+ * SLG_ECAPACITY (*nwindows = 0). row_splits (host) holds max_windows + 1
+ * entries; SLG_ECAPACITY also when more than max_windows windows are needed
+ * (*nwindows is then set to the number needed).
+ */
+slg_status slg_plan_windows(slg_graph* g, int32_t s, int64_t cap, int32_t* row_splits,
+                            int32_t max_windows, int32_t* nwindows);
+
+/*
+ * Phase timing. When enabled, the library records CUDA events on the graph's
+ * stream around each phase; slg_last_timing then returns, for the last
+ * counting pass and the last fill, ms[0..4] = planning (pruning, per-row
+ * work, binning), counting pass, scan of the counts, fill pass, digest.
+ */
+slg_status slg_set_timing(slg_graph* g, int32_t enable);
+slg_status slg_last_timing(slg_graph* g, float* ms5);
+
+/*
+ * Binning of rows into work items (replaces the relabel-by-degree and the
+ * blocked/cyclic ranges of Sections III-F and IV). A row with W_i wedges and
+ * candidate span S_i (last minus first partner id, plus one) is handled
+ *   - by one warp with a 256-slot table when W_i <= warp_max_wedges (<= 128);
+ *   - by direct j-tiled counters when 256 * W_i >= dense_min_density * S_i
+ *     (or S_i <= 4096), dense_item_tiles tiles of 32768 ids per item;
+ *     dense_min_density < 0 disables this handler;
+ *   - otherwise by CTA hash tables, about block_item_wedges wedges per item.
+ * Results do not depend on these values; only speed does. Resets the plan.
+ */
+slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_item_wedges,
+                        int32_t dense_min_density, int32_t dense_item_tiles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLG_H */

@@ -66,6 +66,9 @@ def _load():
                                             ctypes.c_int32, _i32p, _i32p, ctypes.c_int64]
             lib.oracle_list_digest.restype = ctypes.c_uint64
             lib.oracle_list_digest.argtypes = [_i32p, _i32p, _i32p, ctypes.c_int64]
+            lib.oracle_slg_fill_rows.restype = None
+            lib.oracle_slg_fill_rows.argtypes = [_i32p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                                 _i64p, _i32p, _i32p, _i32p, ctypes.c_int]
             lib.oracle_mix.restype = ctypes.c_uint64
             lib.oracle_mix.argtypes = [ctypes.c_uint64]
             lib.oracle_pair_hash.restype = ctypes.c_uint64
@@ -121,6 +124,25 @@ def slg(off, idx, s: int):
     J = np.zeros(max(total, 1), np.int32)
     O = np.zeros(max(total, 1), np.int32)
     lib.oracle_slg(_p32(off), _p32(idx), m, s, _p32(I), _p32(J), _p32(O), total)
+    return I[:total], J[:total], O[:total]
+
+
+def slg_par(off, idx, s: int, nthreads: int | None = None):
+    """Same list as ``slg``, rows spread over threads (per-row counts first)."""
+    if s < 1:
+        raise ValueError("s must be >= 1")
+    counts, _, _ = rows(off, idx, None, [s], nthreads)
+    off, idx = _csr(off, idx)
+    m = off.size - 1
+    rowoff = np.zeros(m + 1, np.int64)
+    np.cumsum(counts[:, 0], out=rowoff[1:])
+    total = int(rowoff[-1])
+    I = np.zeros(max(total, 1), np.int32)
+    J = np.zeros(max(total, 1), np.int32)
+    O = np.zeros(max(total, 1), np.int32)
+    if m:
+        _load().oracle_slg_fill_rows(_p32(off), _p32(idx), m, s, rowoff.ctypes.data_as(_i64p),
+                                     _p32(I), _p32(J), _p32(O), nthreads or default_threads())
     return I[:total], J[:total], O[:total]
 
 

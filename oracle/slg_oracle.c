@@ -265,3 +265,66 @@ uint64_t oracle_list_digest(const int32_t* I, const int32_t* Jo, const int32_t* 
     }
     return d;
 }
+
+/* ----------------------------------------------- threaded full edge list */
+
+typedef struct {
+    const int32_t* off;
+    const int32_t* idx;
+    int32_t m;
+    int32_t s;
+    const int64_t* rowoff; /* where row i's list starts (from per-row counts) */
+    int32_t* I;
+    int32_t* J;
+    int32_t* O;
+    int64_t next;
+    pthread_mutex_t lock;
+} orc_fill_job;
+
+static void* orc_fill_worker(void* arg) {
+    orc_fill_job* F = (orc_fill_job*)arg;
+    for (;;) {
+        pthread_mutex_lock(&F->lock);
+        const int64_t i = F->next++;
+        pthread_mutex_unlock(&F->lock);
+        if (i >= F->m) break;
+        const int32_t* ei = F->idx + F->off[i];
+        const int32_t ni = F->off[i + 1] - F->off[i];
+        int64_t p = F->rowoff[i];
+        for (int32_t j = (int32_t)i + 1; j < F->m; ++j) {
+            const int32_t o = orc_intersect(ei, ni, F->idx + F->off[j], F->off[j + 1] - F->off[j]);
+            if (o >= F->s) {
+                F->I[p] = (int32_t)i;
+                F->J[p] = j;
+                F->O[p] = o;
+                ++p;
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Same list as oracle_slg, rows spread over threads: row i writes its
+ * (i, j, overlap) triples, ascending j, from rowoff[i] on. rowoff comes from
+ * the per-row counts of oracle_rows. */
+void oracle_slg_fill_rows(const int32_t* off, const int32_t* idx, int32_t m, int32_t s,
+                          const int64_t* rowoff, int32_t* I, int32_t* Jo, int32_t* O,
+                          int nthreads) {
+    orc_fill_job F;
+    memset(&F, 0, sizeof(F));
+    F.off = off;
+    F.idx = idx;
+    F.m = m;
+    F.s = s;
+    F.rowoff = rowoff;
+    F.I = I;
+    F.J = Jo;
+    F.O = O;
+    if (nthreads < 1) nthreads = 1;
+    pthread_mutex_init(&F.lock, NULL);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, orc_fill_worker, &F);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&F.lock);
+}

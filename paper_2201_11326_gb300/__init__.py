@@ -1,0 +1,266 @@
+"""s-line graphs of non-uniform hypergraphs on GB300: Python binding of libslg.
+
+Argument marshalling only: each function below calls the C entry point of the
+same name in ``libslg.so`` (declared in ``include/slg.h``), and every step of
+the computation runs in that library's CUDA kernels. Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA); torch is used for device memory
+and streams only. There is no CPU fallback: if the library is missing, the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "SlgError", "Graph", "slg_load", "slg_free", "slg_count", "slg_bound", "slg_build",
+    "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
+    "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "library_path",
+    "lib",
+]
+
+SLG_OK = 0
+SLG_EINVAL = 1
+SLG_ENOMEM = 2
+SLG_ECUDA = 3
+SLG_ETIMEOUT = 4
+SLG_ECAPACITY = 5
+SLG_EBUSY = 6
+SLG_EINTERNAL = 7
+_NAMES = {0: "SLG_OK", 1: "SLG_EINVAL", 2: "SLG_ENOMEM", 3: "SLG_ECUDA", 4: "SLG_ETIMEOUT",
+          5: "SLG_ECAPACITY", 6: "SLG_EBUSY", 7: "SLG_EINTERNAL"}
+
+
+class SlgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+_SIGS = {
+    "slg_last_error": (ctypes.c_char_p, []),
+    "slg_version": (_i32, []),
+    "slg_load": (_i32, [_vp, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "slg_free": (None, [_vp]),
+    "slg_graph_info": (_i32, [_vp, _i32p, _i32p, _i64p]),
+    "slg_transpose_copy": (_i32, [_vp, _vp, _vp]),
+    "slg_count": (_i32, [_vp, _i32, _i64p, _i64p]),
+    "slg_bound": (_i32, [_vp, _i32, _i64p]),
+    "slg_row_offsets": (_i32, [_vp, _i32, _vp]),
+    "slg_build": (_i32, [_vp, _i32, _vp, _vp, _vp, _i64, _i64p]),
+    "slg_build_window": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _i64, _i64p, _u64p, _vp]),
+    "slg_plan_windows": (_i32, [_vp, _i32, _i64, _i32p, _i32, _i32p]),
+    "slg_set_timing": (_i32, [_vp, _i32]),
+    "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libslg (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"libslg is not built ({path} missing); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != SLG_OK:
+        raise SlgError(code, (lib().slg_last_error() or b"").decode())
+
+
+def _ptr(a) -> int:
+    """Data pointer of a contiguous int array (numpy or torch) or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Graph:
+    """A hypergraph resident on the GPU (handle of libslg)."""
+
+    def __init__(self, handle: int, m: int, n: int, nnz: int, keep=None):
+        self._h = handle
+        self.m, self.n, self.nnz = m, n, nnz
+        self._keep = keep
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("graph was freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().slg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _as_i32(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.int32)
+    import torch
+    if a.dtype != torch.int32:
+        raise TypeError("CSR arrays must be int32")
+    return a.contiguous()
+
+
+def slg_load(off, idx, m: int, n: int, stream=None) -> Graph:
+    off = _as_i32(off)
+    idx = _as_i32(idx)
+    h = _vp()
+    _check(lib().slg_load(_ptr(off), _ptr(idx) if len(idx) else None, m, n,
+                          _stream_handle(stream), ctypes.byref(h)))
+    mm, nn, nz = _i32(), _i32(), _i64()
+    _check(lib().slg_graph_info(h, ctypes.byref(mm), ctypes.byref(nn), ctypes.byref(nz)))
+    return Graph(h.value, mm.value, nn.value, nz.value)
+
+
+def slg_free(g: Graph):
+    g.free()
+
+
+def slg_graph_info(g: Graph):
+    mm, nn, nz = _i32(), _i32(), _i64()
+    _check(lib().slg_graph_info(g.handle, ctypes.byref(mm), ctypes.byref(nn), ctypes.byref(nz)))
+    return mm.value, nn.value, nz.value
+
+
+def slg_transpose_copy(g: Graph, offT=None, idxT=None):
+    if offT is None:
+        offT = np.zeros(g.n + 1, np.int32)
+    if idxT is None:
+        idxT = np.zeros(max(g.nnz, 1), np.int32)
+    _check(lib().slg_transpose_copy(g.handle, _ptr(offT), _ptr(idxT)))
+    return offT, idxT[:g.nnz]
+
+
+def slg_count(g: Graph, s: int):
+    """(|L_s|, W_s)."""
+    p, w = _i64(), _i64()
+    _check(lib().slg_count(g.handle, s, ctypes.byref(p), ctypes.byref(w)))
+    return p.value, w.value
+
+
+def slg_bound(g: Graph, s: int) -> int:
+    b = _i64()
+    _check(lib().slg_bound(g.handle, s, ctypes.byref(b)))
+    return b.value
+
+
+def slg_row_offsets(g: Graph, s: int, out=None):
+    if out is None:
+        out = np.zeros(g.m + 1, np.int64)
+    _check(lib().slg_row_offsets(g.handle, s, _ptr(out)))
+    return out
+
+
+def slg_build(g: Graph, s: int, I=None, J=None, O=None, cap: int | None = None):
+    """The whole edge list of L_s(H). Returns (I, J, O) trimmed to |L_s|.
+
+    Without output arrays, host numpy arrays of the exact size are allocated
+    (one counting pass first).
+    """
+    if I is None:
+        pairs, _ = slg_count(g, s)
+        I = np.zeros(max(pairs, 1), np.int32)
+        J = np.zeros(max(pairs, 1), np.int32)
+        O = np.zeros(max(pairs, 1), np.int32)
+        cap = pairs
+    if cap is None:
+        cap = len(I)
+    p = _i64()
+    _check(lib().slg_build(g.handle, s, _ptr(I), _ptr(J), _ptr(O), cap, ctypes.byref(p)))
+    return I[:p.value], J[:p.value], O[:p.value]
+
+
+def slg_build_window(g: Graph, s: int, row_begin: int, row_end: int, I, J, O,
+                     cap: int | None = None, digest: bool = False, row_digests=None):
+    """Rows [row_begin, row_end) into I/J/O. Returns (pairs, digest or None)."""
+    if cap is None:
+        cap = len(I)
+    p = _i64()
+    d = ctypes.c_uint64()
+    _check(lib().slg_build_window(g.handle, s, row_begin, row_end, _ptr(I), _ptr(J), _ptr(O),
+                                  cap, ctypes.byref(p), ctypes.byref(d) if digest else None,
+                                  _ptr(row_digests)))
+    return p.value, (d.value if digest else None)
+
+
+def slg_plan_windows(g: Graph, s: int, cap: int, max_windows: int = 1 << 20) -> np.ndarray:
+    splits = np.zeros(max_windows + 1, np.int32)
+    nw = _i32()
+    _check(lib().slg_plan_windows(g.handle, s, cap, splits.ctypes.data_as(_i32p), max_windows,
+                                  ctypes.byref(nw)))
+    return splits[:nw.value + 1].copy()
+
+
+def slg_set_timing(g: Graph, enable: bool = True):
+    _check(lib().slg_set_timing(g.handle, 1 if enable else 0))
+
+
+def slg_last_timing(g: Graph):
+    ms = (ctypes.c_float * 5)()
+    _check(lib().slg_last_timing(g.handle, ms))
+    return list(ms)
+
+
+def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,
+                 dense_min_density: int = 64, dense_item_tiles: int = 4):
+    _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
+                              dense_item_tiles))

@@ -1,0 +1,476 @@
+// C-ABI entry points of libslg (declared in include/slg.h).
+//
+// Host orchestration only: every step of the computation runs in the kernels
+// of transpose.cu, plan.cu, count_fill.cu and scan.cu. There is no CPU path.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace slg {
+
+static thread_local std::string g_last_error;
+
+void set_error(slg_status code, const std::string& msg) {
+    (void)code;
+    g_last_error = msg;
+}
+
+namespace {
+
+__global__ void k_size_range(const int32_t* __restrict__ size, int32_t m,
+                             int32_t* __restrict__ mm) {
+    int32_t lo = INT32_MAX, hi = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t z = size[i];
+        if (z > 0) lo = min(lo, z);
+        hi = max(hi, z);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+T* dalloc(size_t count, cudaStream_t st) {
+    T* p = nullptr;
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st));
+    return p;
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+}
+
+BinParams default_bins() {
+    BinParams b;
+    b.warp_max_wedges = 128;
+    b.block_item_wedges = 1024;
+    b.dense_min_density = 64;  // dense when W_i >= span / 4
+    b.dense_item_tiles = 4;
+    return b;
+}
+
+struct Timer {
+    bool on = false;
+    cudaEvent_t ev[6] = {};
+    void init() {
+        for (auto& e : ev)
+            if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
+    }
+    void mark(int k, cudaStream_t st) {
+        if (on) SLG_CUDA_TRY(cudaEventRecord(ev[k], st));
+    }
+    void destroy() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+}  // namespace slg
+
+struct slg_graph {
+    slg::GraphDev g;
+    slg::Plan plan;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    slg::BinParams bp = slg::default_bins();
+    slg::Timer timer;
+    float ms[5] = {0, 0, 0, 0, 0};
+};
+
+using slg::Error;
+
+namespace {
+
+slg_status fail(slg_status code, const std::string& msg) {
+    slg::set_error(code, msg);
+    return code;
+}
+
+#define API_BEGIN try {
+#define API_END                                              \
+    }                                                        \
+    catch (const Error& e) {                                 \
+        return fail(e.code, e.msg);                          \
+    }                                                        \
+    catch (const std::exception& e) {                        \
+        return fail(SLG_EINTERNAL, e.what());                \
+    }                                                        \
+    slg::g_last_error.clear();                               \
+    return SLG_OK;
+
+void free_graph_dev(slg::GraphDev& g, cudaStream_t st) {
+    slg::dfree(g.off, st);
+    slg::dfree(g.idx, st);
+    slg::dfree(g.size, st);
+    slg::dfree(g.rowid, st);
+    slg::dfree(g.offT, st);
+    slg::dfree(g.idxT, st);
+    slg::dfree(g.tpos, st);
+}
+
+// Count pass for s (cached per handle): plan, count, offsets.
+void ensure_counted(slg_graph* h, int32_t s) {
+    if (s < 1) throw Error{SLG_EINVAL, "s must be >= 1"};
+    slg::Plan& p = h->plan;
+    if (p.s == s && p.counted) return;
+    h->timer.mark(0, h->st);
+    slg::plan_build(h->g, s, h->bp, p, h->st);
+    h->timer.mark(1, h->st);
+    slg::run_count(h->g, p, h->st);
+    h->timer.mark(2, h->st);
+    slg::plan_offsets(h->g, p, h->st);  // synchronises
+    h->timer.mark(3, h->st);
+    if (h->timer.on) {
+        SLG_CUDA_TRY(cudaEventSynchronize(h->timer.ev[3]));
+        SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[0], h->timer.ev[0], h->timer.ev[1]));
+        SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[1], h->timer.ev[1], h->timer.ev[2]));
+        SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[2], h->timer.ev[2], h->timer.ev[3]));
+        h->ms[3] = h->ms[4] = 0;
+    }
+}
+
+// Copy `bytes` from device src to dst (host or device).
+void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes) SLG_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+}
+
+struct WindowInfo {
+    int64_t base, end;
+    int32_t q0, q1;
+};
+
+WindowInfo window_info(slg_graph* h, int32_t r0, int32_t r1) {
+    WindowInfo w;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&w.base, h->plan.rowoff + r0, 8, cudaMemcpyDeviceToHost, h->st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&w.end, h->plan.rowoff + r1, 8, cudaMemcpyDeviceToHost, h->st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&w.q0, h->plan.row_item + r0, 4, cudaMemcpyDeviceToHost, h->st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&w.q1, h->plan.row_item + r1, 4, cudaMemcpyDeviceToHost, h->st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    return w;
+}
+
+// Fill rows [r0, r1) into device buffers I/J/O (at least end-base entries),
+// optionally digesting. Returns the pair count.
+int64_t fill_window_dev(slg_graph* h, int32_t r0, int32_t r1, int32_t* I, int32_t* J,
+                        int32_t* O, unsigned long long* dtot, unsigned long long* drows,
+                        const WindowInfo& w) {
+    const int64_t P = w.end - w.base;
+    h->timer.mark(3, h->st);
+    slg::run_fill(h->g, h->plan, w.q0, w.q1, I, J, O, P, h->st);
+    h->timer.mark(4, h->st);
+    if (dtot || drows) slg::run_digest(h->g, h->plan, r0, r1, I, J, O, P, dtot, drows, h->st);
+    h->timer.mark(5, h->st);
+    return P;
+}
+
+void finish_timing(slg_graph* h, int64_t pairs_written) {
+    if (!h->timer.on) return;
+    SLG_CUDA_TRY(cudaEventSynchronize(h->timer.ev[5]));
+    SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[3], h->timer.ev[3], h->timer.ev[4]));
+    SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[4], h->timer.ev[4], h->timer.ev[5]));
+    (void)pairs_written;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* slg_last_error(void) { return slg::g_last_error.c_str(); }
+
+int32_t slg_version(void) { return 100; }
+
+slg_status slg_load(const int32_t* off, const int32_t* idx, int32_t m, int32_t n, void* stream,
+                    slg_graph** out) {
+    if (!out) return fail(SLG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (m < 0 || n < 0) return fail(SLG_EINVAL, "m and n must be >= 0");
+    if (!off) return fail(SLG_EINVAL, "off is NULL");
+    slg_graph* h = new slg_graph();
+    h->st = (cudaStream_t)stream;
+    try {
+        SLG_CUDA_TRY(cudaGetDevice(&h->device));
+        slg::GraphDev& g = h->g;
+        g.m = m;
+        g.n = n;
+        int32_t off_m = 0, off_0 = 0;
+        copy_out(&off_m, off + m, sizeof(int32_t), h->st);
+        copy_out(&off_0, off, sizeof(int32_t), h->st);
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        if (off_0 != 0 || off_m < 0) throw Error{SLG_EINVAL, "off[0] must be 0 and off[m] >= 0"};
+        g.nnz = off_m;
+        if (g.nnz > 0 && !idx) throw Error{SLG_EINVAL, "idx is NULL"};
+        g.off = slg::dalloc<int32_t>((size_t)m + 1, h->st);
+        g.idx = slg::dalloc<int32_t>((size_t)g.nnz + 4, h->st);
+        g.size = slg::dalloc<int32_t>((size_t)m, h->st);
+        g.rowid = slg::dalloc<int32_t>((size_t)g.nnz + 4, h->st);
+        g.offT = slg::dalloc<int32_t>((size_t)n + 1, h->st);
+        g.idxT = slg::dalloc<int32_t>((size_t)g.nnz + 4, h->st);
+        g.tpos = slg::dalloc<int32_t>((size_t)g.nnz + 4, h->st);
+        copy_out(g.off, off, sizeof(int32_t) * ((size_t)m + 1), h->st);
+        copy_out(g.idx, idx, sizeof(int32_t) * (size_t)g.nnz, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(g.rowid, 0, sizeof(int32_t) * ((size_t)g.nnz + 4), h->st));
+        SLG_CUDA_TRY(cudaMemsetAsync(g.idxT + g.nnz, 0, sizeof(int32_t) * 4, h->st));
+        int32_t* flag = slg::dalloc<int32_t>(3, h->st);
+        slg::launch_validate(g.off, g.idx, m, n, g.nnz, g.rowid, g.size, flag, h->st);
+        int32_t mm_init[2] = {INT32_MAX, 0};
+        SLG_CUDA_TRY(cudaMemcpyAsync(flag + 1, mm_init, sizeof(mm_init), cudaMemcpyHostToDevice,
+                                     h->st));
+        if (m) {
+            slg::k_size_range<<<152 * 4, 256, 0, h->st>>>(g.size, m, flag + 1);
+            SLG_LAUNCH_CHECK();
+        }
+        int32_t fl[3];
+        SLG_CUDA_TRY(cudaMemcpyAsync(fl, flag, sizeof(fl), cudaMemcpyDeviceToHost, h->st));
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        slg::dfree(flag, h->st);
+        if (fl[0]) {
+            char buf[160];
+            snprintf(buf, sizeof(buf), "invalid CSR:%s%s%s",
+                     (fl[0] & 1) ? " offsets not monotone or out of range;" : "",
+                     (fl[0] & 2) ? " vertex id outside [0, n);" : "",
+                     (fl[0] & 4) ? " row not strictly increasing (repeated or unsorted vertex);"
+                                 : "");
+            throw Error{SLG_EINVAL, buf};
+        }
+        g.min_size = fl[1] == INT32_MAX ? 0 : fl[1];
+        g.max_size = fl[2];
+        slg::build_transpose(g.idx, g.rowid, n, g.nnz, g.offT, g.idxT, g.tpos, h->st);
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        h->timer.init();
+    } catch (const Error& e) {
+        h->plan.release(h->st);
+        free_graph_dev(h->g, h->st);
+        cudaStreamSynchronize(h->st);
+        delete h;
+        return fail(e.code, e.msg);
+    }
+    *out = h;
+    slg::g_last_error.clear();
+    return SLG_OK;
+}
+
+void slg_free(slg_graph* h) {
+    if (!h) return;
+    try {
+        h->plan.release(h->st);
+    } catch (...) {
+    }
+    free_graph_dev(h->g, h->st);
+    cudaStreamSynchronize(h->st);
+    h->timer.destroy();
+    delete h;
+}
+
+slg_status slg_graph_info(const slg_graph* h, int32_t* m, int32_t* n, int64_t* nnz) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (m) *m = h->g.m;
+    if (n) *n = h->g.n;
+    if (nnz) *nnz = h->g.nnz;
+    return SLG_OK;
+}
+
+slg_status slg_transpose_copy(slg_graph* h, int32_t* offT, int32_t* idxT) {
+    if (!h || !offT || (!idxT && h->g.nnz)) return fail(SLG_EINVAL, "NULL argument");
+    API_BEGIN
+    copy_out(offT, h->g.offT, sizeof(int32_t) * ((size_t)h->g.n + 1), h->st);
+    copy_out(idxT, h->g.idxT, sizeof(int32_t) * (size_t)h->g.nnz, h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    API_END
+}
+
+slg_status slg_count(slg_graph* h, int32_t s, int64_t* pairs, int64_t* wedges) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    API_BEGIN
+    ensure_counted(h, s);
+    if (pairs) *pairs = h->plan.pairs;
+    if (wedges) *wedges = h->plan.wedges;
+    API_END
+}
+
+slg_status slg_bound(slg_graph* h, int32_t s, int64_t* pairs_ub) {
+    if (!h || !pairs_ub) return fail(SLG_EINVAL, "NULL argument");
+    if (s < 1) return fail(SLG_EINVAL, "s must be >= 1");
+    API_BEGIN
+    if (h->plan.s != s) slg::plan_build(h->g, s, h->bp, h->plan, h->st);
+    *pairs_ub = h->plan.wedges / s;
+    API_END
+}
+
+slg_status slg_row_offsets(slg_graph* h, int32_t s, int64_t* rowoff) {
+    if (!h || !rowoff) return fail(SLG_EINVAL, "NULL argument");
+    API_BEGIN
+    ensure_counted(h, s);
+    copy_out(rowoff, h->plan.rowoff, sizeof(int64_t) * ((size_t)h->g.m + 1), h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    API_END
+}
+
+slg_status slg_build_window(slg_graph* h, int32_t s, int32_t r0, int32_t r1, int32_t* I,
+                            int32_t* J, int32_t* O, int64_t cap, int64_t* pairs,
+                            uint64_t* digest, uint64_t* row_digests) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (r0 < 0 || r1 < r0 || r1 > h->g.m) return fail(SLG_EINVAL, "bad row range");
+    API_BEGIN
+    ensure_counted(h, s);
+    const WindowInfo w = window_info(h, r0, r1);
+    const int64_t P = w.end - w.base;
+    if (pairs) *pairs = P;
+    if (P > cap) throw Error{SLG_ECAPACITY, "output buffer too small for the window"};
+    if (P > 0 && (!I || !J || !O)) throw Error{SLG_EINVAL, "NULL output array"};
+    const bool dev = P == 0 || (slg::is_device_ptr(I) && slg::is_device_ptr(J) && slg::is_device_ptr(O));
+    int32_t *dI = I, *dJ = J, *dO = O;
+    if (!dev) {
+        dI = slg::dalloc<int32_t>(P, h->st);
+        dJ = slg::dalloc<int32_t>(P, h->st);
+        dO = slg::dalloc<int32_t>(P, h->st);
+    }
+    unsigned long long* dd = nullptr;
+    const int32_t nr = r1 - r0;
+    if (digest || row_digests) {
+        dd = slg::dalloc<unsigned long long>((size_t)nr + 1, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(unsigned long long) * ((size_t)nr + 1), h->st));
+    }
+    fill_window_dev(h, r0, r1, dI, dJ, dO, dd, row_digests ? dd + 1 : nullptr, w);
+    if (!dev) {
+        copy_out(I, dI, sizeof(int32_t) * P, h->st);
+        copy_out(J, dJ, sizeof(int32_t) * P, h->st);
+        copy_out(O, dO, sizeof(int32_t) * P, h->st);
+    }
+    if (digest) copy_out(digest, dd, sizeof(uint64_t), h->st);
+    if (row_digests) copy_out(row_digests, dd + 1, sizeof(uint64_t) * nr, h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    finish_timing(h, P);
+    if (!dev) {
+        slg::dfree(dI, h->st);
+        slg::dfree(dJ, h->st);
+        slg::dfree(dO, h->st);
+    }
+    slg::dfree(dd, h->st);
+    API_END
+}
+
+slg_status slg_build(slg_graph* h, int32_t s, int32_t* I, int32_t* J, int32_t* O, int64_t cap,
+                     int64_t* pairs) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    API_BEGIN
+    ensure_counted(h, s);
+    const int64_t P = h->plan.pairs;
+    if (pairs) *pairs = P;
+    if (P > cap) throw Error{SLG_ECAPACITY, "output buffer too small"};
+    if (P == 0) {
+        slg::g_last_error.clear();
+        return SLG_OK;
+    }
+    if (!I || !J || !O) throw Error{SLG_EINVAL, "NULL output array"};
+    const bool dev = slg::is_device_ptr(I) && slg::is_device_ptr(J) && slg::is_device_ptr(O);
+    if (dev) {
+        WindowInfo w{0, P, 0, (int32_t)h->plan.nitems};
+        fill_window_dev(h, 0, h->g.m, I, J, O, nullptr, nullptr, w);
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        finish_timing(h, P);
+    } else {
+        // host destination: produce bounded windows through a device staging buffer
+        const int64_t stage = (int64_t)1 << 27;  // pairs per window (1.5 GiB staging)
+        const int64_t maxrow = slg::plan_max_row(h->g, h->plan, h->st);
+        const int64_t cap_w = stage > maxrow ? stage : maxrow;
+        const int64_t C = cap_w - maxrow > 0 ? cap_w - maxrow : 1;
+        int32_t* splits_d = slg::dalloc<int32_t>((size_t)h->g.m + 1, h->st);
+        const int32_t nw = slg::plan_windows(h->g, h->plan, C, splits_d, h->st);
+        std::vector<int32_t> splits((size_t)nw + 1);
+        copy_out(splits.data(), splits_d, sizeof(int32_t) * nw, h->st);
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        slg::dfree(splits_d, h->st);
+        splits[nw] = h->g.m;
+        int32_t* dI = slg::dalloc<int32_t>(cap_w, h->st);
+        int32_t* dJ = slg::dalloc<int32_t>(cap_w, h->st);
+        int32_t* dO = slg::dalloc<int32_t>(cap_w, h->st);
+        for (int32_t k = 0; k < nw; ++k) {
+            const WindowInfo w = window_info(h, splits[k], splits[k + 1]);
+            const int64_t Pw = fill_window_dev(h, splits[k], splits[k + 1], dI, dJ, dO, nullptr,
+                                               nullptr, w);
+            copy_out(I + w.base, dI, sizeof(int32_t) * Pw, h->st);
+            copy_out(J + w.base, dJ, sizeof(int32_t) * Pw, h->st);
+            copy_out(O + w.base, dO, sizeof(int32_t) * Pw, h->st);
+        }
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        slg::dfree(dI, h->st);
+        slg::dfree(dJ, h->st);
+        slg::dfree(dO, h->st);
+    }
+    API_END
+}
+
+slg_status slg_plan_windows(slg_graph* h, int32_t s, int64_t cap, int32_t* row_splits,
+                            int32_t max_windows, int32_t* nwindows) {
+    if (!h || !row_splits || !nwindows) return fail(SLG_EINVAL, "NULL argument");
+    if (cap < 1) return fail(SLG_EINVAL, "cap must be >= 1");
+    API_BEGIN
+    *nwindows = 0;
+    ensure_counted(h, s);
+    const int64_t maxrow = slg::plan_max_row(h->g, h->plan, h->st);
+    if (maxrow > cap) throw Error{SLG_ECAPACITY, "a single row has more pairs than cap"};
+    const int64_t C = cap - maxrow > 0 ? cap - maxrow : 1;
+    const int32_t nw = slg::plan_windows(h->g, h->plan, C, nullptr, h->st);
+    *nwindows = nw;
+    if (nw > max_windows) throw Error{SLG_ECAPACITY, "more windows needed than max_windows"};
+    int32_t* splits_d = slg::dalloc<int32_t>((size_t)nw + 1, h->st);
+    slg::plan_windows(h->g, h->plan, C, splits_d, h->st);
+    copy_out(row_splits, splits_d, sizeof(int32_t) * nw, h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    slg::dfree(splits_d, h->st);
+    row_splits[nw] = h->g.m;
+    API_END
+}
+
+slg_status slg_set_timing(slg_graph* h, int32_t enable) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    h->timer.on = enable != 0;
+    return SLG_OK;
+}
+
+slg_status slg_last_timing(slg_graph* h, float* ms5) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (ms5) memcpy(ms5, h->ms, sizeof(h->ms));
+    return SLG_OK;
+}
+
+slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_item_wedges,
+                        int32_t dense_min_density, int32_t dense_item_tiles) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (warp_max_wedges < 0 || warp_max_wedges > slg::WARP_TABLE / 2 || block_item_wedges < 1 ||
+        dense_item_tiles < 1)
+        return fail(SLG_EINVAL, "bin parameter out of range");
+    API_BEGIN
+    h->bp.warp_max_wedges = warp_max_wedges;
+    h->bp.block_item_wedges = block_item_wedges;
+    h->bp.dense_min_density = dense_min_density;
+    h->bp.dense_item_tiles = dense_item_tiles;
+    h->plan.release(h->st);
+    API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,683 @@
+// Counting and filling: the inner loop of Algorithm 2 (Section III-C).
+//
+// For a row e_i and each of its vertices v_k, every later hyperedge e_j of
+// adj(v_k) gets overlap_count[e_j] += 1; afterwards every e_j with count >= s
+// is an s-incident partner. That is the "ikj" axpy order of Section III-B
+// (for k in H^T.Adj[i], for j in H.Adj[k]: L[i,j] += 1) with the Boolean
+// filter applied per row. The paper keeps the counts in a per-thread
+// std::unordered_map; here a work item (row i, partners j in [jlo, jhi))
+// keeps them on chip in one of three forms:
+//
+//   MODE_WARP   one warp, a 256-slot open-addressing table in shared memory
+//               (rows with at most 128 wedges, so the table never fills);
+//   MODE_BLOCK  one CTA, a 4096-slot open-addressing table in shared memory
+//               with atomicAdd counts; a slice with more than 2048 distinct
+//               partners is split in two j halves and redone, so no table
+//               overflows and nothing spills off chip;
+//   MODE_DENSE  one CTA, direct-addressed 16-bit counters for 32768
+//               consecutive j (a j tile); the item walks its tiles in order,
+//               advancing one cursor per wedge range (the adj_s lists are
+//               ascending), reading H^T with 16-byte vector loads.
+//
+// Both passes run the same code: the counting pass stores the number of
+// partners per item, a scan turns those into output offsets, and the fill
+// pass writes (i, j, overlap) in ascending j with warp-ballot compaction (the
+// per-thread output lists of Algorithm 2 are not needed).
+#include <cstdio>
+
+#include "plan.cuh"
+
+namespace slg {
+namespace {
+
+constexpr int32_t EMPTY = -1;
+constexpr int32_t ERR_BOUNDS = 1;  // a fill write fell outside the window
+constexpr int32_t ERR_TABLE = 2;   // a table had no free slot
+constexpr int32_t ERR_DIGEST = 4;  // a pair's row lay outside the window
+
+__device__ __forceinline__ int32_t lower_bound_dev(const int32_t* __restrict__ a, int32_t lo,
+                                                   int32_t hi, int32_t x) {
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Fibonacci hashing of a hyperedge id into a table of 2^(32-shift) slots.
+__device__ __forceinline__ uint32_t slot_of(int32_t j, int shift) {
+    return ((uint32_t)j * 2654435761u) >> shift;
+}
+
+// Insert-or-increment with linear probing. Keys go EMPTY -> j once and never
+// change again, so a plain read that sees a key is final; a read that sees
+// EMPTY is settled by the CAS. Returns 1 when this call created the key, 0
+// when it existed, -1 when every slot was probed without finding room (the
+// callers size their tables so that this cannot happen; the bound only
+// guarantees that the loop ends).
+__device__ __forceinline__ int table_add(int32_t* keys, int32_t* cnts, uint32_t mask, int shift,
+                                         int32_t j) {
+    uint32_t h = slot_of(j, shift);
+    volatile int32_t* vk = keys;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t k = vk[h];
+        if (k == j) {
+            atomicAdd(&cnts[h], 1);
+            return 0;
+        }
+        if (k == EMPTY) {
+            const int32_t old = atomicCAS(&keys[h], EMPTY, j);
+            if (old == EMPTY) {
+                atomicAdd(&cnts[h], 1);
+                return 1;
+            }
+            if (old == j) {
+                atomicAdd(&cnts[h], 1);
+                return 0;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+template <int NT>
+__device__ __forceinline__ int32_t block_excl_scan(int32_t x, int32_t* total, int32_t* tmp) {
+    // tmp: NT/32 + 1 ints of shared memory
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) tmp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int32_t v = lane < NT / 32 ? tmp[lane] : 0;
+        int32_t vi = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, vi, d);
+            if (lane >= d) vi += y;
+        }
+        if (lane < NT / 32) tmp[lane] = vi - v;
+        if (lane == NT / 32 - 1) tmp[NT / 32] = vi;
+    }
+    __syncthreads();
+    const int32_t r = tmp[w] + inc - x;
+    *total = tmp[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+// ============================================================ MODE_WARP
+
+template <bool FILL>
+__global__ void __launch_bounds__(WARP_CTA_WARPS * 32)
+k_warp_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+             const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+             const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+             const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
+             int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
+             int32_t* __restrict__ J, int32_t* __restrict__ O, int64_t limit,
+             int32_t* __restrict__ err) {
+    constexpr int SHIFT = 32 - 8;  // 256 slots
+    static_assert(WARP_TABLE == 256, "slot hash assumes 256 slots");
+    __shared__ int32_t keys[WARP_CTA_WARPS][WARP_TABLE];
+    __shared__ int32_t cnts[WARP_CTA_WARPS][WARP_TABLE];
+    __shared__ int32_t pre[WARP_CTA_WARPS][33];
+    __shared__ int32_t beg[WARP_CTA_WARPS][32];
+    __shared__ int32_t sj[WARP_CTA_WARPS][WARP_TABLE / 2];
+    __shared__ int32_t so[WARP_CTA_WARPS][WARP_TABLE / 2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+    for (int t = lane; t < WARP_TABLE; t += 32) {
+        keys[w][t] = EMPTY;
+        cnts[w][t] = 0;
+    }
+    __syncwarp();
+    const int64_t nw = (int64_t)gridDim.x * WARP_CTA_WARPS;
+    for (int64_t pos = lo + (int64_t)blockIdx.x * WARP_CTA_WARPS + w; pos < hi; pos += nw) {
+        const int32_t q = list[pos];
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const int32_t e1 = off[i + 1];
+        for (int32_t eb = off[i]; eb < e1; eb += 32) {
+            const int32_t e = eb + lane;
+            int32_t b = 0, len = 0;
+            if (e < e1) {
+                b = wbeg[e];
+                len = wend[e] - b;
+            }
+            int32_t inc = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += y;
+            }
+            pre[w][lane + 1] = inc;
+            if (lane == 0) pre[w][0] = 0;
+            beg[w][lane] = b;
+            __syncwarp();
+            const int32_t tot = pre[w][32];
+            for (int32_t t = lane; t < tot; t += 32) {
+                int32_t a = 0, z = 31;  // largest a with pre[a] <= t
+                while (a < z) {
+                    const int32_t mid = (a + z + 1) >> 1;
+                    if (pre[w][mid] <= t)
+                        a = mid;
+                    else
+                        z = mid - 1;
+                }
+                if (table_add(keys[w], cnts[w], WARP_TABLE - 1, SHIFT,
+                              idxTs[beg[w][a] + t - pre[w][a]]) < 0)
+                    atomicOr(err, ERR_TABLE);
+            }
+            __syncwarp();
+        }
+        // survivors, in slot order
+        int32_t count = 0;
+        for (int r = 0; r < WARP_TABLE / 32; ++r) {
+            const int slot = r * 32 + lane;
+            const int32_t k = keys[w][slot];
+            const int32_t c = cnts[w][slot];
+            const bool f = (k != EMPTY) && (c >= s);
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (FILL && f) {
+                sj[w][count + __popc(bal & lt)] = k;
+                so[w][count + __popc(bal & lt)] = c;
+            }
+            count += __popc(bal);
+        }
+        if (!FILL) {
+            if (lane == 0) icnt[q] = count;
+        } else {
+            __syncwarp();
+            const int64_t obase = ioff[q] - ioff[item_lo];
+            for (int32_t t = lane; t < count; t += 32) {
+                const int32_t jj = sj[w][t];
+                int32_t r = 0;
+                for (int32_t u = 0; u < count; ++u) r += (sj[w][u] < jj) ? 1 : 0;
+                if (obase + r < limit) {
+                    I[obase + r] = i;
+                    J[obase + r] = jj;
+                    O[obase + r] = so[w][t];
+                } else {
+                    atomicOr(err, ERR_BOUNDS);
+                }
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < WARP_TABLE; t += 32) {
+            keys[w][t] = EMPTY;
+            cnts[w][t] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+// =========================================================== MODE_BLOCK
+
+template <bool FILL>
+__global__ void __launch_bounds__(BLOCK_THREADS)
+k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+              const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+              const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
+              int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
+              int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
+              int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+    constexpr int NT = BLOCK_THREADS;
+    constexpr int SHIFT = 32 - 12;  // 4096 slots
+    static_assert(BLOCK_TABLE == 4096, "slot hash assumes 4096 slots");
+    constexpr int SLOTS_PER_THREAD = BLOCK_TABLE / NT;
+    __shared__ unsigned long long tab[BLOCK_TABLE];  // keys | counts, then the sort buffer
+    __shared__ int32_t pre[NT + 1];
+    __shared__ int32_t sub[NT];
+    __shared__ int32_t stk_a[64], stk_b[64];
+    __shared__ int32_t tmp[NT / 32 + 1];
+    __shared__ int32_t sh_pos, sh_n, sh_a, sh_b;
+    __shared__ volatile int32_t nkeys, ovf;
+    int32_t* keys = reinterpret_cast<int32_t*>(tab);
+    int32_t* cnts = keys + BLOCK_TABLE;
+    const int tid = threadIdx.x;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+
+    for (;;) {
+        if (tid == 0) sh_pos = lo + atomicAdd(queue, 1);
+        __syncthreads();
+        const int32_t pos = sh_pos;
+        if (pos >= hi) break;
+        const int32_t q = list[pos];
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const int32_t e0 = off[i], e1 = off[i + 1];
+        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
+        int64_t out_pos = 0;  // same value in every thread
+        if (tid == 0) {
+            sh_n = 1;
+            stk_a[0] = it.jlo;
+            stk_b[0] = it.jhi;
+        }
+        for (;;) {
+            __syncthreads();
+            const int32_t n_now = sh_n;
+            __syncthreads();  // every thread has read sh_n before thread 0 pops
+            if (n_now == 0) break;
+            if (tid == 0) {
+                sh_n = n_now - 1;
+                sh_a = stk_a[n_now - 1];
+                sh_b = stk_b[n_now - 1];
+                nkeys = 0;
+                ovf = 0;
+            }
+            for (int t = tid; t < BLOCK_TABLE; t += NT) {
+                keys[t] = EMPTY;
+                cnts[t] = 0;
+            }
+            __syncthreads();
+            const int32_t a = sh_a, b = sh_b;
+            for (int32_t eb = e0; eb < e1; eb += NT) {
+                const int32_t e = eb + tid;
+                int32_t lo_e = 0, len = 0;
+                if (e < e1) {
+                    const int32_t b0 = wbeg[e], t0 = wend[e];
+                    if (t0 > b0) {
+                        lo_e = lower_bound_dev(idxTs, b0, t0, a);
+                        len = lower_bound_dev(idxTs, lo_e, t0, b) - lo_e;
+                    }
+                }
+                int32_t total;
+                const int32_t ex = block_excl_scan<NT>(len, &total, tmp);
+                pre[tid] = ex;
+                sub[tid] = lo_e;
+                if (tid == 0) pre[NT] = total;
+                __syncthreads();
+                for (int32_t t = tid; t < total; t += NT) {
+                    if (ovf) break;
+                    int32_t x = 0, z = NT - 1;  // largest x with pre[x] <= t
+                    while (x < z) {
+                        const int32_t mid = (x + z + 1) >> 1;
+                        if (pre[mid] <= t)
+                            x = mid;
+                        else
+                            z = mid - 1;
+                    }
+                    const int32_t j = idxTs[sub[x] + t - pre[x]];
+                    const int r = table_add(keys, cnts, BLOCK_TABLE - 1, SHIFT, j);
+                    if (r > 0) {
+                        if (atomicAdd((int32_t*)&nkeys, 1) >= BLOCK_CAP) ovf = 1;
+                    } else if (r < 0) {
+                        ovf = 1;  // no room: split, as for too many distinct keys
+                    }
+                }
+                __syncthreads();
+                if (ovf) break;
+            }
+            if (ovf) {
+                // more distinct partners than the table may hold: redo as two halves
+                if (tid == 0) {
+                    const int32_t mid = a + (b - a) / 2;
+                    stk_a[sh_n] = mid;
+                    stk_b[sh_n] = b;
+                    stk_a[sh_n + 1] = a;
+                    stk_b[sh_n + 1] = mid;
+                    sh_n += 2;
+                }
+                __syncthreads();
+                continue;
+            }
+            int32_t kk[SLOTS_PER_THREAD], cc[SLOTS_PER_THREAD];
+            int32_t mine = 0;
+#pragma unroll
+            for (int r = 0; r < SLOTS_PER_THREAD; ++r) {
+                const int slot = r * NT + tid;
+                kk[r] = keys[slot];
+                cc[r] = cnts[slot];
+                mine += (kk[r] != EMPTY && cc[r] >= s) ? 1 : 0;
+            }
+            int32_t c;
+            const int32_t ex = block_excl_scan<NT>(mine, &c, tmp);
+            if (FILL && c > 0) {
+                // the table has been read into registers: reuse it as the sort buffer
+                int32_t p = ex;
+#pragma unroll
+                for (int r = 0; r < SLOTS_PER_THREAD; ++r)
+                    if (kk[r] != EMPTY && cc[r] >= s)
+                        tab[p++] = ((unsigned long long)(uint32_t)kk[r] << 32) | (uint32_t)cc[r];
+                int32_t P = 1;
+                while (P < c) P <<= 1;
+                for (int32_t t = c + tid; t < P; t += NT) tab[t] = ~0ull;
+                __syncthreads();
+                for (int32_t k = 2; k <= P; k <<= 1) {
+                    for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                        for (int32_t t = tid; t < P; t += NT) {
+                            const int32_t u = t ^ jj;
+                            if (u > t) {
+                                const unsigned long long x = tab[t], y = tab[u];
+                                const bool up = (t & k) == 0;
+                                if ((x > y) == up) {
+                                    tab[t] = y;
+                                    tab[u] = x;
+                                }
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+                for (int32_t t = tid; t < c; t += NT) {
+                    const unsigned long long v = tab[t];
+                    const int64_t p2 = obase + out_pos + t;
+                    if (p2 < limit) {
+                        I[p2] = i;
+                        J[p2] = (int32_t)(v >> 32);
+                        O[p2] = (int32_t)(v & 0xffffffffu);
+                    } else {
+                        atomicOr(err, ERR_BOUNDS);
+                    }
+                }
+            }
+            out_pos += c;
+            __syncthreads();
+        }
+        if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
+        __syncthreads();
+    }
+}
+
+// =========================================================== MODE_DENSE
+
+constexpr int HALF = DENSE_TILE / 2;  // 16-bit counters, two per word
+constexpr int LOG_HALF = 14;
+static_assert((1 << LOG_HALF) == HALF, "tile must be 2^15");
+constexpr size_t DENSE_SMEM = sizeof(uint32_t) * HALF + sizeof(int32_t) * 3 * DENSE_MAXE;
+
+template <bool FILL>
+__global__ void __launch_bounds__(DENSE_THREADS)
+k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+              const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+              const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
+              int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
+              int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
+              int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+    constexpr int NT = DENSE_THREADS;
+    extern __shared__ __align__(16) uint32_t dyn[];
+    uint32_t* ctr = dyn;                                        // HALF words
+    int32_t* cur = reinterpret_cast<int32_t*>(dyn + HALF);      // DENSE_MAXE
+    int32_t* endp = cur + DENSE_MAXE;
+    int32_t* hiv = endp + DENSE_MAXE;
+    __shared__ int32_t tmp[NT / 32 + 1];
+    __shared__ int32_t sh_pos;
+    const int tid = threadIdx.x;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+
+    for (;;) {
+        if (tid == 0) sh_pos = lo + atomicAdd(queue, 1);
+        __syncthreads();
+        const int32_t pos = sh_pos;
+        if (pos >= hi) break;
+        const int32_t q = list[pos];
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const int32_t e0 = off[i];
+        const int32_t ne = off[i + 1] - e0;
+        for (int32_t k = tid; k < ne; k += NT) {
+            const int32_t b0 = wbeg[e0 + k], t0 = wend[e0 + k];
+            if (t0 > b0) {
+                cur[k] = lower_bound_dev(idxTs, b0, t0, it.jlo);
+                endp[k] = t0;
+            } else {
+                cur[k] = 0;
+                endp[k] = 0;
+            }
+        }
+        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
+        int64_t out_pos = 0;
+        __syncthreads();
+        for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += DENSE_TILE) {
+            const int32_t span = min(DENSE_TILE, it.jhi - t0);
+            const int32_t t1 = t0 + span;
+            // clear the words this tile uses
+            const int32_t nz = span > HALF ? HALF : ((span + 3) & ~3);
+            for (int32_t w = 4 * tid; w < nz; w += 4 * NT)
+                *reinterpret_cast<uint4*>(ctr + w) = make_uint4(0, 0, 0, 0);
+            for (int32_t k = tid; k < ne; k += NT) {
+                const int32_t c0 = cur[k], e = endp[k];
+                hiv[k] = (c0 < e) ? lower_bound_dev(idxTs, c0, min(e, c0 + span), t1) : c0;
+            }
+            __syncthreads();
+            for (int32_t k = 0; k < ne; ++k) {
+                const int32_t a = cur[k], z = hiv[k];
+                if (a >= z) continue;
+                for (int32_t p = (a & ~3) + 4 * tid; p < z; p += 4 * NT) {
+                    const int4 v = *reinterpret_cast<const int4*>(idxTs + p);
+                    const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int32_t pp = p + c;
+                        if (pp >= a && pp < z) {
+                            const int32_t ci = vv[c] - t0;
+                            atomicAdd(&ctr[ci & (HALF - 1)], 1u << ((ci >> LOG_HALF) << 4));
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            for (int32_t k = tid; k < ne; k += NT) cur[k] = hiv[k];
+            if (!FILL) {
+                int32_t mine = 0;
+                for (int32_t w = 4 * tid; w < HALF; w += 4 * NT) {
+                    const uint4 x = *reinterpret_cast<const uint4*>(ctr + w);
+                    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (w + c < span && (int32_t)(xs[c] & 0xffffu) >= s) ++mine;
+                        if (w + c + HALF < span && (int32_t)(xs[c] >> 16) >= s) ++mine;
+                    }
+                }
+                int32_t tot;
+                block_excl_scan<NT>(mine, &tot, tmp);
+                out_pos += tot;
+            } else {
+                for (int32_t chunk = 0; chunk < span; chunk += 4 * NT) {
+                    const int32_t c0 = chunk + 4 * tid;  // four consecutive counters
+                    int32_t cnt[4] = {0, 0, 0, 0};
+                    int32_t mine = 0;
+                    if (c0 < span) {
+                        const uint4 x = *reinterpret_cast<const uint4*>(ctr + (c0 & (HALF - 1)));
+                        const int sh = (c0 >> LOG_HALF) << 4;
+                        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int32_t v = (int32_t)((xs[c] >> sh) & 0xffffu);
+                            cnt[c] = (c0 + c < span && v >= s) ? v : 0;
+                            mine += cnt[c] ? 1 : 0;
+                        }
+                    }
+                    int32_t tot;
+                    int32_t p = block_excl_scan<NT>(mine, &tot, tmp);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (cnt[c]) {
+                            const int64_t p2 = obase + out_pos + p;
+                            if (p2 < limit) {
+                                I[p2] = i;
+                                J[p2] = t0 + c0 + c;
+                                O[p2] = cnt[c];
+                            } else {
+                                atomicOr(err, ERR_BOUNDS);
+                            }
+                            ++p;
+                        }
+                    }
+                    out_pos += tot;
+                }
+            }
+            __syncthreads();
+        }
+        if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
+        __syncthreads();
+    }
+}
+
+// =============================================================== digest
+
+__global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restrict__ J,
+                         const int32_t* __restrict__ O, int64_t P, int64_t base,
+                         const int64_t* __restrict__ rowoff, int32_t r0, int32_t r1,
+                         unsigned long long* __restrict__ total,
+                         unsigned long long* __restrict__ rows, int32_t* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < P; b += stride) {
+        const int64_t p = b + threadIdx.x;
+        bool ok = p < P;
+        int32_t i = -1;
+        unsigned long long h = 0;
+        if (ok) {
+            i = I[p];
+            if (i < r0 || i >= r1) {
+                atomicOr(err, ERR_DIGEST);
+                ok = false;
+                i = -1;
+            } else {
+                h = pair_digest(i, base + p - rowoff[i], J[p], O[p]);
+                acc += h;
+            }
+        }
+        if (rows) {
+            const unsigned peers = __match_any_sync(0xffffffffu, i);
+            unsigned long long sum = 0;
+            // sum of h over the peers, by shuffling each peer's value to the leader
+            for (unsigned m2 = peers; m2; m2 &= m2 - 1) {
+                const int src = __ffs(m2) - 1;
+                sum += __shfl_sync(peers, h, src);
+            }
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&rows[i - r0], sum);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if (lane == 0 && acc) atomicAdd(total, acc);
+}
+
+struct Occupancy {
+    int sms = 0;
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0;
+};
+
+Occupancy& occupancy() {
+    static Occupancy o;
+    if (o.sms == 0) {
+        int dev = 0;
+        SLG_CUDA_TRY(cudaGetDevice(&dev));
+        SLG_CUDA_TRY(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev));
+        SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)DENSE_SMEM));
+        SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)DENSE_SMEM));
+        int a = 0, b = 0, c = 0;
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
+                                                                   WARP_CTA_WARPS * 32, 0));
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_block_items<true>,
+                                                                   BLOCK_THREADS, 0));
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_dense_items<true>,
+                                                                   DENSE_THREADS, DENSE_SMEM));
+        o.warp_ctas = o.sms * (a > 0 ? a : 1);
+        o.block_ctas = o.sms * (b > 0 ? b : 1);
+        o.dense_ctas = o.sms * (c > 0 ? c : 1);
+    }
+    return o;
+}
+
+template <bool FILL>
+void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
+                  int32_t* icnt, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
+                  int32_t* scratch, cudaStream_t st) {
+    // scratch: NMODES queue heads, then the error flag
+    Occupancy& oc = occupancy();
+    int32_t* queue = scratch;
+    int32_t* err = scratch + NMODES;
+    if (p.mode_count[MODE_WARP]) {
+        k_warp_items<FILL><<<oc.warp_ctas, WARP_CTA_WARPS * 32, 0, st>>>(
+            p.items, p.mode_list[MODE_WARP], p.mode_rank[MODE_WARP], item_lo, item_hi, g.off,
+            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, limit, err);
+        SLG_LAUNCH_CHECK();
+    }
+    if (p.mode_count[MODE_BLOCK]) {
+        k_block_items<FILL><<<oc.block_ctas, BLOCK_THREADS, 0, st>>>(
+            p.items, p.mode_list[MODE_BLOCK], p.mode_rank[MODE_BLOCK], item_lo, item_hi, g.off,
+            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_BLOCK, limit, err);
+        SLG_LAUNCH_CHECK();
+    }
+    if (p.mode_count[MODE_DENSE]) {
+        k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
+            p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
+            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_DENSE, limit, err);
+        SLG_LAUNCH_CHECK();
+    }
+}
+
+int32_t* new_scratch(cudaStream_t st) {
+    int32_t* s = nullptr;
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&s, sizeof(int32_t) * (NMODES + 1), st));
+    SLG_CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(int32_t) * (NMODES + 1), st));
+    return s;
+}
+
+// Reads the error flag (synchronises) and frees the scratch.
+void check_scratch(int32_t* s, cudaStream_t st, const char* what) {
+    int32_t e = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&e, s + NMODES, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    SLG_CUDA_TRY(cudaFreeAsync(s, st));
+    if (e) {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "%s: device consistency check failed (flags %d)", what, e);
+        throw Error{SLG_EINTERNAL, buf};
+    }
+}
+
+}  // namespace
+
+void run_count(const GraphDev& g, Plan& p, cudaStream_t st) {
+    int32_t* sc = new_scratch(st);
+    launch_items<false>(g, p, 0, (int32_t)p.nitems, p.icnt, nullptr, nullptr, nullptr, 0, sc, st);
+    check_scratch(sc, st, "counting pass");
+}
+
+void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
+              int32_t* J, int32_t* O, int64_t limit, cudaStream_t st) {
+    if (item_hi <= item_lo) return;
+    int32_t* sc = new_scratch(st);
+    launch_items<true>(g, p, item_lo, item_hi, nullptr, I, J, O, limit, sc, st);
+    check_scratch(sc, st, "fill pass");
+}
+
+void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const int32_t* I,
+                const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,
+                unsigned long long* rows_dev, cudaStream_t st) {
+    (void)g;
+    if (P <= 0) return;
+    int64_t base = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&base, p.rowoff + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int32_t* sc = new_scratch(st);
+    int64_t blocks = (P + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    k_digest<<<(int)blocks, 256, 0, st>>>(I, J, O, P, base, p.rowoff, r0, r1, total_dev, rows_dev,
+                                          sc + NMODES);
+    SLG_LAUNCH_CHECK();
+    check_scratch(sc, st, "digest");
+}
+
+}  // namespace slg

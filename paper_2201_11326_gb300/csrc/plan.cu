@@ -1,0 +1,402 @@
+// Per-s planning: pruning to E_s, wedge ranges, per-row work, binning.
+//
+// Algorithm 2 (Section III-C) skips every e_i with |e_i| < s ("degree-based
+// pruning") and, for each kept e_i, visits the wedges (e_i, v_k, e_j) with
+// i < j. Pruning e_j as well changes no result (|e_i ∩ e_j| <= |e_j|), so the
+// wedge set used here is W_s = { (i, v, j) : i < j, v in e_i ∩ e_j,
+// |e_i|, |e_j| >= s }, of size sum_v C(d_s(v), 2) (Section III-E's work).
+//
+// Instead of relabelling hyperedges by degree and splitting rows into blocked
+// or cyclic ranges (Sections III-F and IV), rows are binned by their exact
+// wedge count W_{s,i} and candidate span into work items (see slg_internal.cuh),
+// so that output ids stay the caller's ids and no un-relabel sort is needed.
+#include "slg_internal.cuh"
+#include "plan.cuh"
+
+namespace slg {
+namespace {
+
+int grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+#define GRID_STRIDE(k, n)                                                            \
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < (n);       \
+         k += (int64_t)gridDim.x * blockDim.x)
+
+// keep[k] = |e_{idxT[k]}| >= s, for every position k of H^T
+__global__ void k_keep_flags(const int32_t* __restrict__ idxT, const int32_t* __restrict__ size,
+                             int64_t nnz, int32_t s, int32_t* __restrict__ keep) {
+    GRID_STRIDE(k, nnz) keep[k] = size[idxT[k]] >= s ? 1 : 0;
+}
+
+// pruned transpose: idxTs[ks[k]] = idxT[k] for kept k (ks = exclusive scan of keep)
+__global__ void k_compact(const int32_t* __restrict__ idxT, const int32_t* __restrict__ ks,
+                          int64_t nnz, int32_t* __restrict__ idxTs) {
+    GRID_STRIDE(k, nnz) {
+        const int32_t p = ks[k];
+        if (ks[k + 1] != p) idxTs[p] = idxT[k];
+    }
+}
+
+// Wedge range of incidence e = (i, v): positions of adj_s(v) after i.
+__global__ void k_wedge_ranges(const int32_t* __restrict__ idx, const int32_t* __restrict__ rowid,
+                               const int32_t* __restrict__ size, const int32_t* __restrict__ tpos,
+                               const int32_t* __restrict__ offT, const int32_t* __restrict__ ks,
+                               int64_t nnz, int32_t s, int32_t* __restrict__ wbeg,
+                               int32_t* __restrict__ wend) {
+    GRID_STRIDE(e, nnz) {
+        const int32_t i = rowid[e];
+        int32_t b = 0, t = 0;
+        if (size[i] >= s) {
+            const int32_t v = idx[e];
+            const int32_t p = tpos[e];
+            b = (ks ? ks[p] : p) + 1;
+            t = ks ? ks[offT[v + 1]] : offT[v + 1];
+        }
+        wbeg[e] = b;
+        wend[e] = t;
+    }
+}
+
+// One warp per row: W_{s,i} = sum of wedge-range lengths, and the first and
+// last candidate j (adj_s lists are ascending, so these are range ends).
+__global__ void k_row_work(const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+                           const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs,
+                           int32_t m, int64_t* __restrict__ W, int32_t* __restrict__ jmin,
+                           int32_t* __restrict__ jmax, unsigned long long* __restrict__ wtotal) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc_total = 0;
+    for (int64_t i = warp; i < m; i += nwarps) {
+        int64_t w = 0;
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int32_t e = off[i] + lane; e < off[i + 1]; e += 32) {
+            const int32_t b = wbeg[e], t = wend[e];
+            if (t > b) {
+                w += t - b;
+                lo = min(lo, idxTs[b]);
+                hi = max(hi, idxTs[t - 1]);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, d);
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+        }
+        if (lane == 0) {
+            W[i] = w;
+            jmin[i] = lo;
+            jmax[i] = hi;
+            acc_total += (unsigned long long)w;
+        }
+    }
+    if (lane == 0 && acc_total) atomicAdd(wtotal, acc_total);
+}
+
+struct RowItems {
+    int32_t mode;
+    int32_t count;
+    int64_t step;  // j width of each item (dense) or 0 (uniform split)
+};
+
+__device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, BinParams bp) {
+    RowItems r{MODE_WARP, 0, 0};
+    if (w <= 0) return r;
+    const int64_t span = (int64_t)hi - lo + 1;
+    if (w <= bp.warp_max_wedges) {
+        r.mode = MODE_WARP;
+        r.count = 1;
+        return r;
+    }
+    const bool dense_ok = size <= DENSE_MAX_SIZE && size <= DENSE_MAXE;
+    if (bp.dense_min_density >= 0 && dense_ok &&
+        (span <= 4096 || 256 * w >= (int64_t)bp.dense_min_density * span)) {
+        r.mode = MODE_DENSE;
+        r.step = (int64_t)DENSE_TILE * bp.dense_item_tiles;
+        r.count = (int32_t)((span + r.step - 1) / r.step);
+        return r;
+    }
+    r.mode = MODE_BLOCK;
+    int64_t k = (w + bp.block_item_wedges - 1) / bp.block_item_wedges;
+    if (k > span) k = span;
+    if (k < 1) k = 1;
+    r.count = (int32_t)k;
+    return r;
+}
+
+__global__ void k_item_count(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
+                             const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
+                             int32_t m, BinParams bp, int32_t* __restrict__ nitem) {
+    GRID_STRIDE(i, m) nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], bp).count;
+}
+
+__global__ void k_item_emit(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
+                            const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
+                            int32_t m, BinParams bp, const int32_t* __restrict__ row_item,
+                            Item* __restrict__ items) {
+    GRID_STRIDE(i, m) {
+        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], bp);
+        if (r.count == 0) continue;
+        const int64_t lo = jmin[i], end = (int64_t)jmax[i] + 1, span = end - lo;
+        Item* out = items + row_item[i];
+        for (int32_t q = 0; q < r.count; ++q) {
+            int64_t a, b;
+            if (r.step) {
+                a = lo + (int64_t)q * r.step;
+                b = min(end, a + r.step);
+            } else {
+                a = lo + span * q / r.count;
+                b = lo + span * (q + 1) / r.count;
+            }
+            out[q] = Item{(int32_t)i, (int32_t)a, (int32_t)b, r.mode};
+        }
+    }
+}
+
+__global__ void k_mode_flags(const Item* __restrict__ items, int64_t nitems, int32_t mode,
+                             int32_t* __restrict__ flags) {
+    GRID_STRIDE(q, nitems) flags[q] = items[q].mode == mode ? 1 : 0;
+}
+
+__global__ void k_mode_list(const int32_t* __restrict__ rank, int64_t nitems,
+                            int32_t* __restrict__ list) {
+    GRID_STRIDE(q, nitems) {
+        const int32_t p = rank[q];
+        if (rank[q + 1] != p) list[p] = (int32_t)q;
+    }
+}
+
+__global__ void k_rowoff(const int32_t* __restrict__ row_item, const int64_t* __restrict__ ioff,
+                         int32_t m, int64_t* __restrict__ rowoff) {
+    GRID_STRIDE(i, (int64_t)m + 1) rowoff[i] = ioff[row_item[i]];
+}
+
+// Window boundaries: row r starts a new window when floor(rowoff[r] / C)
+// exceeds floor(rowoff[r-1] / C); with C = cap - (largest row), every window
+// then holds at most cap pairs.
+__global__ void k_window_flags(const int64_t* __restrict__ rowoff, int32_t m, int64_t C,
+                               int32_t* __restrict__ flags) {
+    GRID_STRIDE(r, m) flags[r] = (r == 0) ? 1 : ((rowoff[r] / C) != (rowoff[r - 1] / C) ? 1 : 0);
+}
+
+__global__ void k_window_list(const int32_t* __restrict__ rank, int32_t m,
+                              int32_t* __restrict__ splits) {
+    GRID_STRIDE(r, m) {
+        const int32_t p = rank[r];
+        if (rank[r + 1] != p) splits[p] = (int32_t)r;
+    }
+}
+
+__global__ void k_max_row(const int64_t* __restrict__ rowoff, int32_t m,
+                          unsigned long long* __restrict__ out) {
+    unsigned long long best = 0;
+    GRID_STRIDE(r, m) {
+        const unsigned long long c = (unsigned long long)(rowoff[r + 1] - rowoff[r]);
+        best = c > best ? c : best;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+        best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+template <typename T>
+T* dalloc(size_t count, cudaStream_t st) {
+    T* p = nullptr;
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st));
+    return p;
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t st) {
+    if (p) SLG_CUDA_TRY(cudaFreeAsync(p, st));
+    p = nullptr;
+}
+
+}  // namespace
+
+void Plan::release(cudaStream_t st) {
+    if (idxTs_owned) dfree(idxTs, st);
+    idxTs = nullptr;
+    dfree(ks, st);
+    dfree(wbeg, st);
+    dfree(wend, st);
+    dfree(W, st);
+    dfree(jmin, st);
+    dfree(jmax, st);
+    dfree(row_item, st);
+    dfree(items, st);
+    for (int k = 0; k < NMODES; ++k) {
+        dfree(mode_rank[k], st);
+        dfree(mode_list[k], st);
+        mode_count[k] = 0;
+    }
+    dfree(icnt, st);
+    dfree(ioff, st);
+    dfree(rowoff, st);
+    s = 0;
+    nitems = 0;
+    counted = false;
+    pairs = wedges = 0;
+}
+
+void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st) {
+    p.release(st);
+    p.s = s;
+    const int64_t nnz = g.nnz;
+    const int32_t m = g.m;
+    const int T = 256;
+
+    // pruned transpose
+    if (s <= g.min_size) {
+        p.idxTs = g.idxT;
+        p.idxTs_owned = false;
+        p.ks = nullptr;
+    } else {
+        int32_t* keep = dalloc<int32_t>(nnz, st);
+        p.ks = dalloc<int32_t>(nnz + 1, st);
+        if (nnz) {
+            k_keep_flags<<<grid_for(nnz, T), T, 0, st>>>(g.idxT, g.size, nnz, s, keep);
+            SLG_LAUNCH_CHECK();
+        }
+        scan_i32_to_i32(keep, p.ks, nnz, st);
+        dfree(keep, st);
+        // +4: the dense handler reads H^T with 16-byte vector loads that may
+        // reach up to three entries past the last kept position
+        p.idxTs = dalloc<int32_t>(nnz + 4, st);
+        SLG_CUDA_TRY(cudaMemsetAsync(p.idxTs, 0, sizeof(int32_t) * (nnz + 4), st));
+        p.idxTs_owned = true;
+        if (nnz) {
+            k_compact<<<grid_for(nnz, T), T, 0, st>>>(g.idxT, p.ks, nnz, p.idxTs);
+            SLG_LAUNCH_CHECK();
+        }
+    }
+    p.wbeg = dalloc<int32_t>(nnz, st);
+    p.wend = dalloc<int32_t>(nnz, st);
+    if (nnz) {
+        k_wedge_ranges<<<grid_for(nnz, T), T, 0, st>>>(g.idx, g.rowid, g.size, g.tpos, g.offT, p.ks,
+                                                       nnz, s, p.wbeg, p.wend);
+        SLG_LAUNCH_CHECK();
+    }
+    // per-row work
+    p.W = dalloc<int64_t>(m, st);
+    p.jmin = dalloc<int32_t>(m, st);
+    p.jmax = dalloc<int32_t>(m, st);
+    unsigned long long* wtot = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(wtot, 0, sizeof(unsigned long long), st));
+    if (m) {
+        k_row_work<<<grid_for((int64_t)m * 32, T), T, 0, st>>>(g.off, p.wbeg, p.wend, p.idxTs, m,
+                                                               p.W, p.jmin, p.jmax, wtot);
+        SLG_LAUNCH_CHECK();
+    }
+    // items
+    int32_t* nitem = dalloc<int32_t>(m, st);
+    p.row_item = dalloc<int32_t>((size_t)m + 1, st);
+    if (m) {
+        k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, m, bp, nitem);
+        SLG_LAUNCH_CHECK();
+    }
+    scan_i32_to_i32(nitem, p.row_item, m, st);
+    dfree(nitem, st);
+    int32_t nitems32 = 0;
+    unsigned long long wtot_h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&nitems32, p.row_item + m, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&wtot_h, wtot, sizeof(wtot_h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(wtot, st);
+    p.nitems = nitems32;
+    p.wedges = (int64_t)wtot_h;
+    p.items = dalloc<Item>(p.nitems, st);
+    if (m) {
+        k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, m, bp, p.row_item,
+                                                  p.items);
+        SLG_LAUNCH_CHECK();
+    }
+    int32_t* flags = dalloc<int32_t>(p.nitems, st);
+    for (int k = 0; k < NMODES; ++k) {
+        p.mode_rank[k] = dalloc<int32_t>(p.nitems + 1, st);
+        if (p.nitems) {
+            k_mode_flags<<<grid_for(p.nitems, T), T, 0, st>>>(p.items, p.nitems, k, flags);
+            SLG_LAUNCH_CHECK();
+        }
+        scan_i32_to_i32(flags, p.mode_rank[k], p.nitems, st);
+    }
+    dfree(flags, st);
+    int32_t counts[NMODES];
+    for (int k = 0; k < NMODES; ++k)
+        SLG_CUDA_TRY(cudaMemcpyAsync(&counts[k], p.mode_rank[k] + p.nitems, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < NMODES; ++k) {
+        p.mode_count[k] = counts[k];
+        p.mode_list[k] = dalloc<int32_t>(counts[k], st);
+        if (p.nitems) {
+            k_mode_list<<<grid_for(p.nitems, T), T, 0, st>>>(p.mode_rank[k], p.nitems,
+                                                             p.mode_list[k]);
+            SLG_LAUNCH_CHECK();
+        }
+    }
+    p.icnt = dalloc<int32_t>(p.nitems, st);
+    p.ioff = dalloc<int64_t>(p.nitems + 1, st);
+    p.rowoff = dalloc<int64_t>((size_t)m + 1, st);
+    p.counted = false;
+}
+
+void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st) {
+    const int T = 256;
+    scan_i32_to_i64(p.icnt, p.ioff, p.nitems, st);
+    k_rowoff<<<grid_for((int64_t)g.m + 1, T), T, 0, st>>>(p.row_item, p.ioff, g.m, p.rowoff);
+    SLG_LAUNCH_CHECK();
+    SLG_CUDA_TRY(cudaMemcpyAsync(&p.pairs, p.ioff + p.nitems, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    p.counted = true;
+}
+
+int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st) {
+    unsigned long long* d = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    if (g.m) {
+        k_max_row<<<grid_for(g.m, 256), 256, 0, st>>>(p.rowoff, g.m, d);
+        SLG_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    return (int64_t)h;
+}
+
+int32_t plan_windows(const GraphDev& g, const Plan& p, int64_t C, int32_t* splits_dev,
+                     cudaStream_t st) {
+    const int T = 256;
+    const int32_t m = g.m;
+    int32_t* flags = dalloc<int32_t>(m, st);
+    int32_t* rank = dalloc<int32_t>((size_t)m + 1, st);
+    if (m) {
+        k_window_flags<<<grid_for(m, T), T, 0, st>>>(p.rowoff, m, C, flags);
+        SLG_LAUNCH_CHECK();
+    }
+    scan_i32_to_i32(flags, rank, m, st);
+    int32_t nw = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&nw, rank + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (splits_dev && m) {
+        k_window_list<<<grid_for(m, T), T, 0, st>>>(rank, m, splits_dev);
+        SLG_LAUNCH_CHECK();
+    }
+    dfree(flags, st);
+    dfree(rank, st);
+    return nw;
+}
+
+}  // namespace slg

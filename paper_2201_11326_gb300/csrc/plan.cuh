@@ -1,0 +1,67 @@
+// Device-resident graph and per-s plan (internal).
+#pragma once
+
+#include "slg_internal.cuh"
+
+namespace slg {
+
+// A loaded hypergraph: the caller's CSR, its dual, and per-incidence tables.
+struct GraphDev {
+    int32_t m = 0, n = 0;
+    int64_t nnz = 0;
+    int32_t min_size = 0;   // smallest |e_i| over non-empty rows (0 if none)
+    int32_t max_size = 0;   // largest |e_i|
+    int32_t* off = nullptr;    // [m+1]
+    int32_t* idx = nullptr;    // [nnz]
+    int32_t* size = nullptr;   // [m]   |e_i|
+    int32_t* rowid = nullptr;  // [nnz] row of incidence e
+    int32_t* offT = nullptr;   // [n+1] H^T offsets
+    int32_t* idxT = nullptr;   // [nnz] adj(v) ascending
+    int32_t* tpos = nullptr;   // [nnz] position of incidence e inside H^T
+};
+
+// Everything derived for one s. Items and offsets are valid once built;
+// icnt/ioff/rowoff once `counted`.
+struct Plan {
+    int32_t s = 0;
+    int32_t* ks = nullptr;      // [nnz+1] kept-prefix over H^T positions (null when nothing is pruned)
+    int32_t* idxTs = nullptr;   // pruned H^T (aliases idxT when nothing is pruned)
+    bool idxTs_owned = false;
+    int32_t* wbeg = nullptr;    // [nnz] wedge range of incidence e in idxTs
+    int32_t* wend = nullptr;
+    int64_t* W = nullptr;       // [m] wedges of row i
+    int32_t* jmin = nullptr;    // [m] first / last candidate partner of row i
+    int32_t* jmax = nullptr;
+    int32_t* row_item = nullptr;  // [m+1] first item of row i
+    int64_t nitems = 0;
+    Item* items = nullptr;
+    int32_t* mode_rank[NMODES] = {nullptr, nullptr, nullptr};  // [nitems+1]
+    int32_t* mode_list[NMODES] = {nullptr, nullptr, nullptr};  // item ids per mode, ascending
+    int64_t mode_count[NMODES] = {0, 0, 0};
+    int32_t* icnt = nullptr;    // [nitems] pairs per item
+    int64_t* ioff = nullptr;    // [nitems+1] output offset per item
+    int64_t* rowoff = nullptr;  // [m+1] output offset per row
+    bool counted = false;
+    int64_t pairs = 0;
+    int64_t wedges = 0;
+
+    void release(cudaStream_t st);
+};
+
+void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st);
+void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st);
+int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st);
+int32_t plan_windows(const GraphDev& g, const Plan& p, int64_t C, int32_t* splits_dev,
+                     cudaStream_t st);
+
+// Counting and filling (count_fill.cu). Items [item_lo, item_hi) are filled
+// into I/J/O at position ioff[q] - ioff[item_lo].
+void run_count(const GraphDev& g, Plan& p, cudaStream_t st);
+void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
+              int32_t* J, int32_t* O, int64_t limit, cudaStream_t st);
+// Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
+void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const int32_t* I,
+                const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,
+                unsigned long long* rows_dev, cudaStream_t st);
+
+}  // namespace slg

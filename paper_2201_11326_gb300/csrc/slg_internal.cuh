@@ -1,0 +1,116 @@
+// Internal declarations of libslg (not part of the C ABI).
+//
+// Terms used throughout (Liu et al., arXiv 2201.11326):
+//   row i        hyperedge e_i; its CSR row lists its vertices (Section II-A)
+//   adj(v)       hyperedges containing vertex v, ascending (the dual, H^T)
+//   E_s          hyperedges with |e| >= s (Section II-B)
+//   wedge        (i, v, j) with i < j, v in e_i ∩ e_j, |e_i|, |e_j| >= s: one
+//                increment of Algorithm 2's overlap counter (Section III-C)
+//   adj_s(v)     adj(v) restricted to E_s ("pruned transpose")
+//   wedge range  for incidence (i, v): the suffix of adj_s(v) after i, i.e.
+//                the j of every wedge (i, v, j)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "slg.h"
+
+namespace slg {
+
+// ---------------------------------------------------------------- status
+
+struct Error {
+    slg_status code;
+    std::string msg;
+};
+
+void set_error(slg_status code, const std::string& msg);
+
+#define SLG_CUDA_TRY(expr)                                                         \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            throw ::slg::Error{e_ == cudaErrorMemoryAllocation ? SLG_ENOMEM        \
+                                                                : SLG_ECUDA,       \
+                               std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+        }                                                                          \
+    } while (0)
+
+#define SLG_LAUNCH_CHECK() SLG_CUDA_TRY(cudaGetLastError())
+
+// ------------------------------------------------------------ work items
+//
+// A work item is one row i restricted to candidate partners j in [jlo, jhi).
+// Items of a row are contiguous, in increasing j, and cover every wedge of
+// the row; items of different rows follow row order. The canonical output is
+// therefore the concatenation of the items' outputs in item order.
+
+enum ItemMode : int32_t {
+    MODE_WARP = 0,   // whole row, few wedges: one warp, small hash table
+    MODE_BLOCK = 1,  // sparse slice: one CTA, shared-memory hash table
+    MODE_DENSE = 2,  // dense slice: one CTA, direct j-tiled counters
+    NMODES = 3
+};
+
+struct Item {
+    int32_t row;
+    int32_t jlo;
+    int32_t jhi;
+    int32_t mode;
+};
+
+// Tunables of the binning (chosen per graph; defaults in plan.cu).
+struct BinParams {
+    int32_t warp_max_wedges;   // rows with W_i <= this go to MODE_WARP
+    int32_t block_item_wedges; // target wedges per MODE_BLOCK item
+    int32_t dense_min_density; // dense when 256*W_i >= density*span (density/256)
+    int32_t dense_item_tiles;  // tiles per MODE_DENSE item
+};
+
+// ---------------------------------------------------------- kernel sizes
+
+constexpr int WARP_TABLE = 256;           // slots per warp table (MODE_WARP)
+constexpr int WARP_CTA_WARPS = 8;         // warps per CTA in MODE_WARP
+constexpr int BLOCK_THREADS = 512;        // MODE_BLOCK CTA
+constexpr int BLOCK_TABLE = 4096;         // slots per CTA table (MODE_BLOCK)
+constexpr int BLOCK_CAP = BLOCK_TABLE / 2;// distinct keys before a slice splits
+constexpr int DENSE_THREADS = 512;        // MODE_DENSE CTA
+constexpr int DENSE_TILE = 32768;         // j per tile (16-bit counters)
+constexpr int DENSE_MAXE = 2048;          // incidences a dense row may have
+constexpr int DENSE_MAX_SIZE = 65535;     // |e_i| bound for 16-bit counters
+
+// --------------------------------------------------------- device helpers
+
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+    // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t pair_digest(int32_t i, int64_t k, int32_t j, int32_t o) {
+    uint64_t a = splitmix64(((uint64_t)(uint32_t)i << 32) | (uint64_t)(uint32_t)k);
+    return splitmix64(a ^ (((uint64_t)(uint32_t)j << 32) | (uint64_t)(uint32_t)o));
+}
+
+// ------------------------------------------------------ host-side launches
+//
+// Each returns after enqueueing on `st`; scratch comes from stream-ordered
+// allocation (cudaMallocAsync) and is released in stream order.
+
+// exclusive scan: out[0..n] with out[n] = total (out has n+1 entries)
+void scan_i32_to_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+void scan_i64_to_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// load-time kernels (transpose.cu)
+void launch_validate(const int32_t* off, const int32_t* idx, int32_t m, int32_t n, int64_t nnz,
+                     int32_t* rowid, int32_t* size, int32_t* flag, cudaStream_t st);
+void build_transpose(const int32_t* idx, const int32_t* rowid, int32_t n, int64_t nnz,
+                     int32_t* offT, int32_t* idxT, int32_t* tpos, cudaStream_t st);
+
+}  // namespace slg

@@ -250,6 +250,27 @@ def uniform_random(seed: int, m: int, n: int, lo: int, hi: int) -> Hypergraph:
     return Hypergraph(off.astype(np.int32), idx.astype(np.int32), int(n), f"uniform{seed}")
 
 
+def striped_hub(seed: int, m: int, n: int, period: int, lo: int = 1, hi: int = 4) -> Hypergraph:
+    """A sparse graph whose hub rows span many j tiles.
+
+    Every row draws a uniform size in [lo, hi] of distinct vertices from
+    [1, n); rows i with i % period == 0 also contain vertex 0, so the hub list
+    adj(0) covers the whole id range with density 1/period.
+    """
+    rng = np.random.default_rng([seed, 78])
+    sizes = rng.integers(lo, hi + 1, size=m)
+    rows = []
+    for i, k in enumerate(sizes):
+        r = rng.choice(np.arange(1, n), size=int(min(k, n - 1)), replace=False)
+        if i % period == 0:
+            r = np.append(r, 0)
+        rows.append(np.sort(r))
+    off = np.zeros(m + 1, np.int64)
+    np.cumsum([len(r) for r in rows], out=off[1:])
+    idx = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    return Hypergraph(off.astype(np.int32), idx.astype(np.int32), int(n), f"striped{seed}")
+
+
 # ----------------------------------------------------------------------------
 # file cache (int32 CSR binaries)
 # ----------------------------------------------------------------------------

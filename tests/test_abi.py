@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/slg.h declares.
+
+No GPU work is launched here: only symbol lookup and calls that touch no device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2201_11326_gb300 as slg
+from paper_2201_11326_gb300 import build as slg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\*]+\s+\**(slg_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    slg_build.build()
+    return slg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("slg_load", "slg_count", "slg_build", "slg_build_window", "slg_bound",
+                     "slg_plan_windows", "slg_free", "slg_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_symbol():
+    for n in declared_symbols():
+        assert n in slg._SIGS, f"{n} has no Python binding"
+
+
+def test_version_and_error_string(lib):
+    assert lib.slg_version() >= 100
+    assert isinstance(lib.slg_last_error(), bytes)
+
+
+def test_null_arguments_rejected_without_device(lib):
+    # argument checks that happen before any CUDA call
+    out = ctypes.c_void_p()
+    assert lib.slg_load(None, None, 0, 0, None, ctypes.byref(out)) == slg.SLG_EINVAL
+    assert lib.slg_load(None, None, -1, 0, None, None) == slg.SLG_EINVAL
+    assert lib.slg_count(None, 1, None, None) == slg.SLG_EINVAL
+    assert b"NULL" in lib.slg_last_error() or len(lib.slg_last_error()) > 0
+
+
+def test_library_links_no_oracle():
+    # the product library shares nothing with the oracle
+    import subprocess
+    out = subprocess.run(["nm", "-D", slg.library_path()], capture_output=True, text=True).stdout
+    assert "oracle_" not in out

@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle, bit-exact.
+
+Every case compares the full canonical list (I, J, O) element by element, or,
+at full size, per-row counts and digests of sampled rows plus totals fixed by
+closed forms.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2201_11326_gb300 as slg
+from tests.test_oracle_pins import csr_from_rows, parse_golden
+
+pytestmark = pytest.mark.gpu
+
+# bin settings that force one handler onto every row (results must not change)
+FORCED = {
+    "default": (128, 1024, 64, 4),
+    "block_only": (0, 1024, -1, 4),
+    "block_one_item_per_row": (0, 1 << 30, -1, 4),  # big items: exercises the split path
+    "block_tiny_items": (0, 1, -1, 4),
+    "dense_only": (0, 1024, 0, 1),
+    "warp_and_block": (128, 256, -1, 4),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    slg.build.build()
+    torch.cuda.init()
+
+
+def gpu_list(h, s, bins=None):
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        if bins is not None:
+            slg.slg_set_bins(g, *bins)
+        return slg.slg_build(g, s)
+    finally:
+        g.free()
+
+
+def assert_same(got, want, ctx=""):
+    gI, gJ, gO = got
+    wI, wJ, wO = want
+    assert gI.size == wI.size, f"{ctx}: {gI.size} pairs vs oracle {wI.size}"
+    for name, a, b in (("I", gI, wI), ("J", gJ, wJ), ("O", gO, wO)):
+        if not np.array_equal(a, b):
+            k = int(np.flatnonzero(a != b)[0])
+            raise AssertionError(f"{ctx}: {name} differs first at {k}: "
+                                 f"gpu ({gI[k]},{gJ[k]},{gO[k]}) oracle ({wI[k]},{wJ[k]},{wO[k]})")
+
+
+def test_worked_example(golden_dir):
+    n, rows, pairs, *_ = parse_golden(os.path.join(golden_dir, "worked_example.txt"))
+    off, idx = csr_from_rows(rows)
+    h = synth.Hypergraph(off, idx, n)
+    for s in range(1, 6):
+        I, J, O = gpu_list(h, s)
+        assert list(zip(I.tolist(), J.tolist(), O.tolist())) == sorted(pairs.get(s, []))
+
+
+def test_transpose_matches_oracle():
+    for h in (synth.tiny(), synth.medium(m=20000), synth.uniform_random(1, 500, 300, 0, 9)):
+        g = slg.slg_load(h.off, h.idx, h.m, h.n)
+        offT, idxT = slg.slg_transpose_copy(g)
+        g.free()
+        wo, wi = oracle.transpose(h.off, h.idx, h.n)
+        assert np.array_equal(offT, wo) and np.array_equal(idxT, wi)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_tiny_workload(s):
+    h = synth.tiny()
+    assert_same(gpu_list(h, s), oracle.slg(h.off, h.idx, s), f"tiny s={s}")
+
+
+@pytest.mark.parametrize("mode", sorted(FORCED))
+def test_forced_handlers_tiny(mode):
+    h = synth.tiny()
+    for s in (1, 2, 3):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle.slg(h.off, h.idx, s), f"{mode} s={s}")
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_list(key, h, s):
+    if (key, s) not in _ORACLE_CACHE:
+        _ORACLE_CACHE[(key, s)] = oracle.slg_par(h.off, h.idx, s)
+    return _ORACLE_CACHE[(key, s)]
+
+
+@pytest.mark.parametrize("mode", sorted(FORCED))
+def test_forced_handlers_medium_recipe(mode):
+    # the medium workload's recipe (Zipf hubs in most rows), scaled down
+    h = synth.medium(seed=2, m=6000)
+    for s in (1, 3, 8):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("med6000", h, s), f"{mode} s={s}")
+
+
+@pytest.mark.parametrize("mode", sorted(FORCED))
+def test_forced_handlers_multitile(mode):
+    # hub rows whose partners span three 32768-wide j tiles and a ragged tail
+    h = synth.striped_hub(3, 70001, 3000, 40)
+    for s in (1, 2):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("striped", h, s), f"{mode} s={s}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small(seed):
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(1, 400))
+    n = int(rng.integers(1, 300))
+    h = synth.uniform_random(seed, m, n, 0, min(n, 40))
+    for s in (1, 2, 4, 7):
+        assert_same(gpu_list(h, s), oracle.slg(h.off, h.idx, s), f"seed={seed} s={s}")
+
+
+def test_count_and_wedges():
+    h = synth.medium(seed=4, m=30000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    sizes = h.sizes()
+    row = np.repeat(np.arange(h.m), sizes)
+    s_list = list(range(1, 9))
+    counts, _, _ = oracle.rows(h.off, h.idx, None, s_list)
+    for t, s in enumerate(s_list):
+        pairs, wedges = slg.slg_count(g, s)
+        ds = np.bincount(h.idx[sizes[row] >= s], minlength=h.n).astype(np.int64)
+        assert wedges == int((ds * (ds - 1) // 2).sum())
+        assert pairs == int(counts[:, t].sum())
+        assert slg.slg_bound(g, s) >= pairs
+        rowoff = slg.slg_row_offsets(g, s)
+        assert np.array_equal(np.diff(rowoff), counts[:, t])
+    g.free()
+
+
+def test_edge_cases():
+    cases = {
+        "empty_graph": ([], 5),
+        "all_empty_rows": ([[], [], []], 4),
+        "one_row": ([[0, 1, 2]], 3),
+        "duplicates": ([[1, 2, 3]] * 5 + [[2, 3]] * 3, 4),
+        "hub_row": ([list(range(300))] + [[v] for v in range(300)] + [list(range(0, 300, 2))], 300),
+        "singletons": ([[v % 7] for v in range(50)], 7),
+    }
+    for name, (rows, n) in cases.items():
+        off, idx = csr_from_rows(rows)
+        h = synth.Hypergraph(off, idx, n)
+        for s in (1, 2, 3, 200):
+            assert_same(gpu_list(h, s), oracle.slg(off, idx, s), f"{name} s={s}")
+
+
+def test_invalid_input_rejected():
+    bad = {
+        "unsorted": (np.array([0, 2], np.int32), np.array([3, 1], np.int32), 1, 4),
+        "repeat": (np.array([0, 2], np.int32), np.array([1, 1], np.int32), 1, 4),
+        "range": (np.array([0, 1], np.int32), np.array([4], np.int32), 1, 4),
+        "negative": (np.array([0, 1], np.int32), np.array([-1], np.int32), 1, 4),
+        "offsets": (np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32), 2, 4),
+        "off0": (np.array([1, 2], np.int32), np.array([0, 1], np.int32), 1, 4),
+    }
+    for name, (off, idx, m, n) in bad.items():
+        with pytest.raises(slg.SlgError) as ei:
+            slg.slg_load(off, idx, m, n)
+        assert ei.value.code == slg.SLG_EINVAL, name
+    h = synth.tiny()
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    with pytest.raises(slg.SlgError) as ei:
+        slg.slg_count(g, 0)
+    assert ei.value.code == slg.SLG_EINVAL
+    I = np.zeros(3, np.int32)
+    with pytest.raises(slg.SlgError) as ei:
+        slg.slg_build(g, 1, I, I.copy(), I.copy(), cap=3)
+    assert ei.value.code == slg.SLG_ECAPACITY
+    g.free()
+
+
+def test_windows_and_digests():
+    h = synth.medium(seed=6, m=5000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    for s in (1, 4):
+        wI, wJ, wO = oracle.slg_par(h.off, h.idx, s)
+        counts, digs, _ = oracle.rows(h.off, h.idx, None, [s])
+        cap = max(int(counts.max()), wI.size // 7 + 1)
+        splits = slg.slg_plan_windows(g, s, cap)
+        assert splits[0] == 0 and splits[-1] == h.m and np.all(np.diff(splits) > 0)
+        I = np.zeros(cap, np.int32)
+        J = np.zeros(cap, np.int32)
+        O = np.zeros(cap, np.int32)
+        parts, total = [], 0
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            rd = np.zeros(r1 - r0, np.uint64)
+            P, d = slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, digest=True,
+                                        row_digests=rd)
+            assert P <= cap
+            parts.append((I[:P].copy(), J[:P].copy(), O[:P].copy()))
+            total = (total + d) % 2**64
+            assert np.array_equal(rd, digs[r0:r1, 0])
+        got = tuple(np.concatenate([p[k] for p in parts]) for k in range(3))
+        assert_same(got, (wI, wJ, wO), f"windows s={s}")
+        assert total == oracle.list_digest(wI, wJ, wO)
+    g.free()
+
+
+def test_device_buffers_and_stream():
+    import torch
+    h = synth.medium(seed=7, m=5000)
+    st = torch.cuda.Stream()
+    off = torch.from_numpy(h.off).cuda()
+    idx = torch.from_numpy(h.idx).cuda()
+    g = slg.slg_load(off, idx, h.m, h.n, stream=st)
+    pairs, _ = slg.slg_count(g, 2)
+    I = torch.empty(pairs, dtype=torch.int32, device="cuda")
+    J = torch.empty_like(I)
+    O = torch.empty_like(I)
+    slg.slg_build(g, 2, I, J, O)
+    st.synchronize()
+    want = oracle.slg_par(h.off, h.idx, 2)
+    assert_same((I.cpu().numpy(), J.cpu().numpy(), O.cpu().numpy()), want, "device buffers")
+    g.free()
+
+
+def test_repeated_calls_are_identical():
+    h = synth.medium(seed=8, m=8000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    a = slg.slg_build(g, 2)
+    slg.slg_count(g, 5)
+    b = slg.slg_build(g, 2)
+    assert_same(a, b, "rebuild")
+    g.free()

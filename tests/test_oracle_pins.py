@@ -189,6 +189,16 @@ def test_medium_recipe_small_vs_scipy(seed):
         assert as_triples(*oracle.slg(h.off, h.idx, s)) == sparse_upper(h.off, h.idx, h.n, s)
 
 
+def test_threaded_list_equals_single_thread():
+    h = synth.medium(seed=9, m=2500)
+    for s in (1, 3, 6):
+        a = oracle.slg(h.off, h.idx, s)
+        b = oracle.slg_par(h.off, h.idx, s, nthreads=3)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    e = synth.uniform_random(5, 0, 10, 0, 3)
+    assert oracle.slg_par(e.off, e.idx, 1)[0].size == 0
+
+
 def test_transpose_vs_scipy():
     h = synth.medium(seed=5, m=5000)
     offT, idxT = oracle.transpose(h.off, h.idx, h.n)
