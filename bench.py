@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of s-line graph construction on one GB300 (or N replicas).
+
+Workload: the medium synthetic hypergraph (m = 1,000,000 hyperedges over
+n = 500,000 vertices, log-normal(1.8, 1.0) sizes clipped to [2, 5000],
+Zipf(1.7) vertex popularity, seed 0) with the sweep s = 1..8.
+
+One step = the whole hot path on that input, resident in HBM:
+  slg_load from device memory (validate, transpose), then for every s:
+  counting pass (prune, per-row work, binning, count, scan), window plan and
+  the fill of every window of at most 2^31 pairs into a reused device window.
+Metric: wedges per second, W = sum_s W_s with W_s = sum_v C(d_s(v), 2);
+s-edges per second (sum_s |L_s| / time) is reported beside it.
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on a
+bounded row sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = ("medium: m=1,000,000 hyperedges, n=500,000 vertices, sizes log-normal(1.8,1.0) "
+            "clipped [2,5000], vertex popularity Zipf(1.7), seed 0; s=1..8 sweep")
+METRIC = "s-line wedges/s (medium hypergraph, s=1..8, bit-exact)"
+WINDOW = 1 << 31          # pairs per output window (24 GiB of I/J/O)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--s", default="1-8", help="s values, e.g. 1-8 or 2,4")
+    ap.add_argument("--m", type=int, default=1_000_000, help="hyperedges (default: full size)")
+    ap.add_argument("--cpu-rows", type=int, default=600, help="rows in the CPU-oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def s_values(spec: str):
+    out = []
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            out.extend(range(int(a), int(b) + 1))
+        else:
+            out.append(int(part))
+    return out
+
+
+def workload(m: int):
+    key = f"medium_m{m}_seed0"
+    return synth.cached(key, lambda: synth.medium(seed=0, m=m))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample(h, s_list, rows: int, seed: int):
+    """Time the CPU oracle on `rows` random rows (all s at once)."""
+    import oracle
+    rng = np.random.default_rng([seed, 5])
+    sample = np.sort(rng.choice(h.m, size=min(rows, h.m), replace=False)).astype(np.int32)
+    cores = host_cores()
+    t0 = time.perf_counter()
+    _, _, osum = oracle.rows(h.off, h.idx, sample, s_list, nthreads=cores)
+    dt = time.perf_counter() - t0
+    wedges = int(osum.sum())
+    return wedges, dt, cores, f"{sample.size} random rows (seed {seed}) x s={s_list[0]}..{s_list[-1]}"
+
+
+# ------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.path = os.path.join(tempfile.gettempdir(), f"slg_clocks_{os.getpid()}.csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half by clock (idle gaps between kernels read low)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- GPU step
+
+def run_sweep(slg, g, s_list, bufs, stream, per_s):
+    """Counting pass + windowed fill for every s on a loaded graph."""
+    import torch
+    I, J, O = bufs
+    for s in s_list:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pairs, wedges = slg.slg_count(g, s)
+        splits = slg.slg_plan_windows(g, s, WINDOW)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW)
+        e1.record(stream)
+        e1.synchronize()
+        d = per_s.setdefault(s, {"s": s, "wedges": wedges, "pairs": pairs, "ms": []})
+        d["ms"].append(e0.elapsed_time(e1))
+
+
+def bench_ours(args):
+    import torch
+    import paper_2201_11326_gb300 as slg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    s_list = s_values(args.s)
+    h = workload(args.m)
+    # inputs resident in HBM before the timed region
+    off_d = torch.from_numpy(h.off).to(dev)
+    idx_d = torch.from_numpy(h.idx).to(dev)
+    stream = torch.cuda.Stream(dev)
+    I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+    J = torch.empty_like(I)
+    O = torch.empty_like(I)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(per_s, timing=False):
+        with torch.cuda.stream(stream):
+            flush.fill_(0)  # L2 flush: a 512 MiB write
+            g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+            if timing:
+                slg.slg_set_timing(g, True)
+            run_sweep(slg, g, s_list, (I, J, O), stream, per_s)
+            ks = slg.slg_kernel_stats(g) if timing else None
+            g.free()
+        return ks
+
+    for _ in range(args.warmup):
+        step({})
+    # per-handler work of the sweep (for the roofline's algorithmic bytes)
+    g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+    mode_work = {s: slg.slg_mode_stats(g, s) for s in s_list}
+    g.free()
+
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(dev)
+    launches0 = slg.slg_kernel_launches()
+    per_s = {}
+    kstats = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        kstats.append(step(per_s, timing=True))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = slg.slg_kernel_launches() - launches0
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    W = sum(d["wedges"] for d in per_s.values())
+    P = sum(d["pairs"] for d in per_s.values())
+    sec = elapsed_ms / 1e3
+    value = world * W * args.steps / sec
+    edges = world * P * args.steps / sec
+
+    # roofline of the dominant kernel (dense-tile handler, counting or fill)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ms_tot = [[0.0] * 3, [0.0] * 3]
+    ln_tot = [[0] * 3, [0] * 3]
+    for ms, ln in kstats:
+        for p in range(2):
+            for k in range(3):
+                ms_tot[p][k] += ms[p][k]
+                ln_tot[p][k] += ln[p][k]
+    w_mode = [sum(mode_work[s][k][1] for s in s_list) for k in range(3)]
+    inc_mode = [sum(mode_work[s][k][2] for s in s_list) for k in range(3)]
+    pairs_mode = [sum(mode_work[s][k][3] for s in s_list) for k in range(3)]
+    # candidates: (pass, mode) -> bytes per step
+    cands = []
+    names = ["warp", "block", "dense"]
+    for k in range(3):
+        cb = 4 * w_mode[k] + 8 * inc_mode[k]
+        cands.append(("count", k, cb, ms_tot[0][k] / args.steps, ln_tot[0][k] / args.steps))
+        cands.append(("fill", k, cb + 12 * pairs_mode[k], ms_tot[1][k] / args.steps,
+                      ln_tot[1][k] / args.steps))
+    dom = max(cands, key=lambda c: c[3])
+    kname = f"k_{names[dom[1]]}_items<{'true' if dom[0] == 'fill' else 'false'}>"
+    achieved = dom[2] / (dom[3] / 1e3) / 1e9 if dom[3] > 0 else 0.0
+    traffic = profiled_traffic(kname, dom[2] / max(dom[4], 1))
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
+                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                "bytes_per_launch": int(dom[2] / max(dom[4], 1)),
+                "launches_per_step": dom[4],
+                "ms_per_launch": round(dom[3] / max(dom[4], 1), 3),
+                "kernel_share_of_step": round(dom[3] / (elapsed_ms / args.steps), 4)}
+
+    per_s_out = []
+    for s in s_list:
+        d = per_s[s]
+        ms = statistics.mean(d["ms"])
+        pw = mode_work[s]
+        alg = sum(4 * pw[k][1] + 8 * pw[k][2] for k in range(3)) * 2 + 12 * d["pairs"]
+        per_s_out.append({"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
+                          "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
+                          "s_edges_per_s": d["pairs"] / (ms / 1e3),
+                          "alg_GBps": round(alg / (ms / 1e3) / 1e9, 1)})
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.m == 1_000_000 else f"{WORKLOAD} (m={args.m})",
+                   "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": WINDOW,
+                   "l2": "flushed before each step (512 MiB device write); inputs resident",
+                   "parallelism": f"replicas x{world}"},
+        "s_edges_per_s": edges,
+        "per_s": per_s_out,
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        wedges, dt, cores, sample = oracle_sample(h, s_list, args.cpu_rows, seed=1)
+        out["cpu_baseline"] = {"value": wedges / dt, "unit": "wedges/s", "cores": cores,
+                               "kind": "oracle", "sample": sample, "seconds": round(dt, 2)}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def e2e(args, slg, h, s_list, stream, bufs):
+    """Same sweep through the public API from pinned host memory.
+
+    Timed (wall clock): host->device copy of the CSR (inside slg_load), the
+    transpose, every counting pass and window fill, and the device->host read
+    of each s-line graph's row offsets (rowoff[m+1], int64) -- the lists stay in
+    the device window.
+    """
+    import torch
+    off_h = torch.from_numpy(h.off).pin_memory()
+    idx_h = torch.from_numpy(h.idx).pin_memory()
+    rowoff = torch.empty(h.m + 1, dtype=torch.int64).pin_memory()
+    I, J, O = bufs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    W = 0
+    with torch.cuda.stream(stream):
+        g = slg.slg_load(off_h, idx_h, h.m, h.n, stream=stream)
+        for s in s_list:
+            _, w = slg.slg_count(g, s)
+            W += w
+            splits = slg.slg_plan_windows(g, s, WINDOW)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW)
+            slg.slg_row_offsets(g, s, rowoff)
+        g.free()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": W / dt, "unit": "wedges/s", "h2d_bytes_per_step": int(h.off.nbytes + h.idx.nbytes),
+            "d2h_bytes_per_step": int(8 * (h.m + 1) * len(s_list)), "seconds": round(dt, 3),
+            "note": "lists stay in the device window; host reads |L_s| and row offsets"}
+
+
+def profiled_traffic(kname: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it matches.
+
+    profiles/traffic.json maps kernel name -> {"dram_over_alg": r,
+    "source_sha": sha of count_fill.cu when captured}. The ratio of measured
+    DRAM bytes to algorithmic bytes on the captured case is scaled to this
+    launch; null when no capture exists or the kernel source has changed.
+    """
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kname)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2201_11326_gb300", "csrc", "count_fill.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha") != sha:
+        return None
+    return int(rec["dram_over_alg"] * alg_bytes_per_launch)
+
+
+# ----------------------------------------------------------- reference arm
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s_list = s_values(args.s)
+    h = workload(args.m)
+    rows = max(16, args.cpu_rows // 4)
+    for k in range(args.warmup):
+        oracle_sample(h, s_list, rows, seed=100 + k)
+    W = 0
+    T = 0.0
+    for k in range(args.steps):
+        w, dt, cores, sample = oracle_sample(h, s_list, rows, seed=200 + k)
+        W += w
+        T += dt
+    value = W / T
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": T / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list,
+                   "parallelism": "cpu oracle, host threads"},
+        "cpu_baseline": {"value": value, "unit": "wedges/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows} random rows per step x s={s_list[0]}..{s_list[-1]}"},
+        "e2e": {"value": value, "unit": "wedges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,24 @@ slg_status slg_set_timing(slg_graph* g, int32_t enable);
 slg_status slg_last_timing(slg_graph* g, float* ms5);
 
 /*
+ * Per-handler kernel time accumulated while timing is enabled: ms6[pass*3 +
+ * mode] and launches6[pass*3 + mode], pass 0 = counting, 1 = fill, mode 0 =
+ * warp table, 1 = CTA table, 2 = dense tiles. reset != 0 zeroes the totals
+ * after reading. Either output may be NULL.
+ */
+slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms6, int64_t* launches6);
+
+/*
+ * Work per handler for s (runs the counting pass if needed): out12[mode*4 +
+ * c] with c = 0 rows, 1 wedges, 2 incidences (sum of |e_i| over the rows),
+ * 3 output pairs. The wedge total over the three handlers is W_s.
+ */
+slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out12);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t slg_kernel_launches(void);
+
+/*
  * Binning of rows into work items (replaces the relabel-by-degree and the
  * blocked/cyclic ranges of Sections III-F and IV). A row with W_i wedges and
  * candidate span S_i (last minus first partner id, plus one) is handled

@@ -20,7 +20,8 @@ from . import build as _build
 __all__ = [
     "SlgError", "Graph", "slg_load", "slg_free", "slg_count", "slg_bound", "slg_build",
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
-    "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "library_path",
+    "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
+    "slg_mode_stats", "slg_kernel_launches", "library_path",
     "lib",
 ]
 
@@ -67,6 +68,9 @@ _SIGS = {
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
+    "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
+    "slg_kernel_launches": (_i64, []),
 }
 
 
@@ -258,6 +262,25 @@ def slg_last_timing(g: Graph):
     ms = (ctypes.c_float * 5)()
     _check(lib().slg_last_timing(g.handle, ms))
     return list(ms)
+
+
+def slg_kernel_stats(g: Graph, reset: bool = False):
+    """(ms[2][3], launches[2][3]) per pass (count, fill) and handler (warp, block, dense)."""
+    ms = (ctypes.c_float * 6)()
+    ln = (ctypes.c_int64 * 6)()
+    _check(lib().slg_kernel_stats(g.handle, 1 if reset else 0, ms, ln))
+    return ([list(ms[0:3]), list(ms[3:6])], [list(ln[0:3]), list(ln[3:6])])
+
+
+def slg_mode_stats(g: Graph, s: int):
+    """[[rows, wedges, incidences, pairs] for warp, block, dense]."""
+    out = (ctypes.c_int64 * 12)()
+    _check(lib().slg_mode_stats(g.handle, s, out))
+    return [list(out[4 * k:4 * k + 4]) for k in range(3)]
+
+
+def slg_kernel_launches() -> int:
+    return int(lib().slg_kernel_launches())
 
 
 def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,

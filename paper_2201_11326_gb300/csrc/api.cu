@@ -4,6 +4,7 @@
 // of transpose.cu, plan.cu, count_fill.cu and scan.cu. There is no CPU path.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <vector>
 
 #include "plan.cuh"
@@ -11,6 +12,9 @@
 namespace slg {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(slg_status code, const std::string& msg) {
     (void)code;
@@ -88,6 +92,11 @@ struct Timer {
     }
 };
 
+void mtimer_init(ModeTimer& t) {
+    for (auto& e : t.ev)
+        if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
+}
+
 }  // namespace
 }  // namespace slg
 
@@ -98,6 +107,7 @@ struct slg_graph {
     int device = 0;
     slg::BinParams bp = slg::default_bins();
     slg::Timer timer;
+    slg::ModeTimer mtimer;
     float ms[5] = {0, 0, 0, 0, 0};
 };
 
@@ -140,7 +150,7 @@ void ensure_counted(slg_graph* h, int32_t s) {
     h->timer.mark(0, h->st);
     slg::plan_build(h->g, s, h->bp, p, h->st);
     h->timer.mark(1, h->st);
-    slg::run_count(h->g, p, h->st);
+    slg::run_count(h->g, p, &h->mtimer, h->st);
     h->timer.mark(2, h->st);
     slg::plan_offsets(h->g, p, h->st);  // synchronises
     h->timer.mark(3, h->st);
@@ -180,7 +190,7 @@ int64_t fill_window_dev(slg_graph* h, int32_t r0, int32_t r1, int32_t* I, int32_
                         const WindowInfo& w) {
     const int64_t P = w.end - w.base;
     h->timer.mark(3, h->st);
-    slg::run_fill(h->g, h->plan, w.q0, w.q1, I, J, O, P, h->st);
+    slg::run_fill(h->g, h->plan, w.q0, w.q1, I, J, O, P, &h->mtimer, h->st);
     h->timer.mark(4, h->st);
     if (dtot || drows) slg::run_digest(h->g, h->plan, r0, r1, I, J, O, P, dtot, drows, h->st);
     h->timer.mark(5, h->st);
@@ -261,6 +271,7 @@ slg_status slg_load(const int32_t* off, const int32_t* idx, int32_t m, int32_t n
         slg::build_transpose(g.idx, g.rowid, n, g.nnz, g.offT, g.idxT, g.tpos, h->st);
         SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
         h->timer.init();
+        slg::mtimer_init(h->mtimer);
     } catch (const Error& e) {
         h->plan.release(h->st);
         free_graph_dev(h->g, h->st);
@@ -282,6 +293,8 @@ void slg_free(slg_graph* h) {
     free_graph_dev(h->g, h->st);
     cudaStreamSynchronize(h->st);
     h->timer.destroy();
+    for (auto& e : h->mtimer.ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -449,8 +462,36 @@ slg_status slg_plan_windows(slg_graph* h, int32_t s, int64_t cap, int32_t* row_s
 slg_status slg_set_timing(slg_graph* h, int32_t enable) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     h->timer.on = enable != 0;
+    h->mtimer.on = enable != 0;
     return SLG_OK;
 }
+
+slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms6, int64_t* launches6) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < slg::NMODES; ++k) {
+            if (ms6) ms6[pass * slg::NMODES + k] = h->mtimer.ms[pass][k];
+            if (launches6) launches6[pass * slg::NMODES + k] = h->mtimer.launches[pass][k];
+            if (reset) {
+                h->mtimer.ms[pass][k] = 0;
+                h->mtimer.launches[pass][k] = 0;
+            }
+        }
+    return SLG_OK;
+}
+
+slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out12) {
+    if (!h || !out12) return fail(SLG_EINVAL, "NULL argument");
+    API_BEGIN
+    ensure_counted(h, s);
+    int64_t st[slg::NMODES][4];
+    slg::plan_mode_stats(h->g, h->plan, st, h->st);
+    for (int k = 0; k < slg::NMODES; ++k)
+        for (int c = 0; c < 4; ++c) out12[k * 4 + c] = st[k][c];
+    API_END
+}
+
+int64_t slg_kernel_launches(void) { return (int64_t)slg::g_launches.load(); }
 
 slg_status slg_last_timing(slg_graph* h, float* ms5) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");

@@ -602,28 +602,52 @@ Occupancy& occupancy() {
 template <bool FILL>
 void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
                   int32_t* icnt, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
-                  int32_t* scratch, cudaStream_t st) {
+                  int32_t* scratch, ModeTimer* mt, cudaStream_t st) {
     // scratch: NMODES queue heads, then the error flag
     Occupancy& oc = occupancy();
     int32_t* queue = scratch;
     int32_t* err = scratch + NMODES;
+    const bool timed = mt && mt->on;
+    auto tick = [&](int mode, int edge) {
+        if (timed) SLG_CUDA_TRY(cudaEventRecord(mt->ev[2 * mode + edge], st));
+    };
+    bool ran[NMODES] = {false, false, false};
     if (p.mode_count[MODE_WARP]) {
+        ran[MODE_WARP] = true;
+        tick(MODE_WARP, 0);
         k_warp_items<FILL><<<oc.warp_ctas, WARP_CTA_WARPS * 32, 0, st>>>(
             p.items, p.mode_list[MODE_WARP], p.mode_rank[MODE_WARP], item_lo, item_hi, g.off,
             p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, limit, err);
         SLG_LAUNCH_CHECK();
+        tick(MODE_WARP, 1);
     }
     if (p.mode_count[MODE_BLOCK]) {
+        ran[MODE_BLOCK] = true;
+        tick(MODE_BLOCK, 0);
         k_block_items<FILL><<<oc.block_ctas, BLOCK_THREADS, 0, st>>>(
             p.items, p.mode_list[MODE_BLOCK], p.mode_rank[MODE_BLOCK], item_lo, item_hi, g.off,
             p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_BLOCK, limit, err);
         SLG_LAUNCH_CHECK();
+        tick(MODE_BLOCK, 1);
     }
     if (p.mode_count[MODE_DENSE]) {
+        ran[MODE_DENSE] = true;
+        tick(MODE_DENSE, 0);
         k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
             p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
             p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_DENSE, limit, err);
         SLG_LAUNCH_CHECK();
+        tick(MODE_DENSE, 1);
+    }
+    if (timed) {
+        for (int k = 0; k < NMODES; ++k) {
+            if (!ran[k]) continue;
+            float ms = 0;
+            SLG_CUDA_TRY(cudaEventSynchronize(mt->ev[2 * k + 1]));
+            SLG_CUDA_TRY(cudaEventElapsedTime(&ms, mt->ev[2 * k], mt->ev[2 * k + 1]));
+            mt->ms[FILL ? 1 : 0][k] += ms;
+            mt->launches[FILL ? 1 : 0][k] += 1;
+        }
     }
 }
 
@@ -649,17 +673,18 @@ void check_scratch(int32_t* s, cudaStream_t st, const char* what) {
 
 }  // namespace
 
-void run_count(const GraphDev& g, Plan& p, cudaStream_t st) {
+void run_count(const GraphDev& g, Plan& p, ModeTimer* mt, cudaStream_t st) {
     int32_t* sc = new_scratch(st);
-    launch_items<false>(g, p, 0, (int32_t)p.nitems, p.icnt, nullptr, nullptr, nullptr, 0, sc, st);
+    launch_items<false>(g, p, 0, (int32_t)p.nitems, p.icnt, nullptr, nullptr, nullptr, 0, sc, mt,
+                        st);
     check_scratch(sc, st, "counting pass");
 }
 
 void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
-              int32_t* J, int32_t* O, int64_t limit, cudaStream_t st) {
+              int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt, cudaStream_t st) {
     if (item_hi <= item_lo) return;
     int32_t* sc = new_scratch(st);
-    launch_items<true>(g, p, item_lo, item_hi, nullptr, I, J, O, limit, sc, st);
+    launch_items<true>(g, p, item_lo, item_hi, nullptr, I, J, O, limit, sc, mt, st);
     check_scratch(sc, st, "fill pass");
 }
 

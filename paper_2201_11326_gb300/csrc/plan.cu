@@ -208,6 +208,22 @@ __global__ void k_max_row(const int64_t* __restrict__ rowoff, int32_t m,
     if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
 
+// Per-handler totals: a row's items all share one mode.
+__global__ void k_mode_stats(const int32_t* __restrict__ row_item, const Item* __restrict__ items,
+                             const int64_t* __restrict__ W, const int32_t* __restrict__ size,
+                             const int64_t* __restrict__ rowoff, int32_t m,
+                             unsigned long long* __restrict__ out) {
+    GRID_STRIDE(i, m) {
+        const int32_t q = row_item[i];
+        if (row_item[i + 1] == q) continue;
+        const int mode = items[q].mode;
+        atomicAdd(&out[mode * 4 + 0], 1ull);
+        atomicAdd(&out[mode * 4 + 1], (unsigned long long)W[i]);
+        atomicAdd(&out[mode * 4 + 2], (unsigned long long)size[i]);
+        atomicAdd(&out[mode * 4 + 3], (unsigned long long)(rowoff[i + 1] - rowoff[i]));
+    }
+}
+
 template <typename T>
 T* dalloc(size_t count, cudaStream_t st) {
     T* p = nullptr;
@@ -360,6 +376,22 @@ void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st) {
                                  cudaMemcpyDeviceToHost, st));
     SLG_CUDA_TRY(cudaStreamSynchronize(st));
     p.counted = true;
+}
+
+void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st) {
+    unsigned long long* d = dalloc<unsigned long long>(NMODES * 4, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NMODES * 4, st));
+    if (g.m) {
+        k_mode_stats<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.size,
+                                                         p.rowoff, g.m, d);
+        SLG_LAUNCH_CHECK();
+    }
+    unsigned long long h[NMODES * 4];
+    SLG_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    for (int k = 0; k < NMODES; ++k)
+        for (int c = 0; c < 4; ++c) out[k][c] = (int64_t)h[k * 4 + c];
 }
 
 int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st) {

@@ -56,9 +56,11 @@ int32_t plan_windows(const GraphDev& g, const Plan& p, int64_t C, int32_t* split
 
 // Counting and filling (count_fill.cu). Items [item_lo, item_hi) are filled
 // into I/J/O at position ioff[q] - ioff[item_lo].
-void run_count(const GraphDev& g, Plan& p, cudaStream_t st);
+void run_count(const GraphDev& g, Plan& p, ModeTimer* mt, cudaStream_t st);
 void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
-              int32_t* J, int32_t* O, int64_t limit, cudaStream_t st);
+              int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt, cudaStream_t st);
+// Per-handler totals over rows: rows, wedges, incidences, pairs (needs counts).
+void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
 void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,

@@ -39,7 +39,14 @@ void set_error(slg_status code, const std::string& msg);
         }                                                                          \
     } while (0)
 
-#define SLG_LAUNCH_CHECK() SLG_CUDA_TRY(cudaGetLastError())
+// Every kernel launch of the library is followed by SLG_LAUNCH_CHECK(), which
+// also counts it (reported by slg_kernel_launches()).
+void count_launch();
+#define SLG_LAUNCH_CHECK()                    \
+    do {                                      \
+        ::slg::count_launch();                \
+        SLG_CUDA_TRY(cudaGetLastError());     \
+    } while (0)
 
 // ------------------------------------------------------------ work items
 //
@@ -60,6 +67,15 @@ struct Item {
     int32_t jlo;
     int32_t jhi;
     int32_t mode;
+};
+
+// Per-handler kernel timing (CUDA events on the graph's stream), for the
+// counting pass [0] and the fill pass [1].
+struct ModeTimer {
+    bool on = false;
+    cudaEvent_t ev[2 * NMODES] = {};
+    float ms[2][NMODES] = {};
+    int64_t launches[2][NMODES] = {};
 };
 
 // Tunables of the binning (chosen per graph; defaults in plan.cu).
