@@ -194,6 +194,41 @@ slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out12);
 int64_t slg_kernel_launches(void);
 
 /*
+ * slg_scan_counts_noalloc -- exclusive prefix sum of per-row pair counts
+ * into int64 output offsets (offsets[0] = 0, offsets[n] = total), the step
+ * that places each row's pairs in a count-then-fill list, for callers that
+ * cannot allocate device memory. The paper has no counterpart: its output
+ * lists are merged host-side containers.
+ *
+ * Who needs it: a caller whose process has handed all device memory to
+ * another allocator (a serving runtime or framework that reserves HBM up
+ * front, so a further cudaMalloc fails or steals its budget), or a caller
+ * on a latency-critical path that cannot afford cudaMalloc/cudaFree, which
+ * may synchronise the whole device. This call performs no device
+ * allocation of any kind: its scratch (the per-tile sums) is a fixed
+ * 264 KiB array compiled into the library, present on every GPU that loads
+ * it until the process exits.
+ *
+ *   counts  : n int32 per-row counts, device memory.
+ *   offsets : n+1 int64 outputs, device memory (caller-owned).
+ *   n       : 0 <= n <= 67,108,864; larger n fails with SLG_EINVAL and
+ *             launches nothing.
+ *   stream  : cudaStream_t (as void*) for the kernels; the call returns
+ *             after enqueueing them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture begins. All calls on a device share the one
+ * array: every call writes each tile sum before reading it, so nothing needs
+ * clearing, but calls whose kernels overlap on the GPU (e.g. on two
+ * streams) race on it and must be serialised by the caller.
+ * Errors: SLG_EINVAL (size above the limit, NULL or host pointers),
+ * SLG_ECUDA.
+ */
+slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int64_t n,
+                                   void* stream);
+
+/*
  * Binning of rows into work items (replaces the relabel-by-degree and the
  * blocked/cyclic ranges of Sections III-F and IV). A row with W_i wedges and
  * candidate span S_i (last minus first partner id, plus one) is handled

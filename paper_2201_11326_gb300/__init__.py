@@ -21,7 +21,7 @@ __all__ = [
     "SlgError", "Graph", "slg_load", "slg_free", "slg_count", "slg_bound", "slg_build",
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
-    "slg_mode_stats", "slg_kernel_launches", "library_path",
+    "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "library_path",
     "lib",
 ]
 
@@ -71,6 +71,7 @@ _SIGS = {
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
     "slg_kernel_launches": (_i64, []),
+    "slg_scan_counts_noalloc": (_i32, [_vp, _vp, _i64, _vp]),
 }
 
 
@@ -281,6 +282,18 @@ def slg_mode_stats(g: Graph, s: int):
 
 def slg_kernel_launches() -> int:
     return int(lib().slg_kernel_launches())
+
+
+def slg_scan_counts_noalloc(counts, offsets, stream=None):
+    """Exclusive scan of int32 device counts into int64 device offsets (n+1).
+
+    Performs no device allocation (see include/slg.h); both tensors must be
+    on the GPU.
+    """
+    n = len(counts)
+    _check(lib().slg_scan_counts_noalloc(_ptr(counts), _ptr(offsets), n,
+                                         _stream_handle(stream)))
+    return offsets
 
 
 def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,

@@ -4,6 +4,8 @@
 // into pruned-transpose positions, and per-item pair counts into output
 // offsets (the count-then-fill scheme that replaces the per-thread output
 // lists merged at the end of Algorithm 2, Section III-C).
+#include <mutex>
+
 #include "slg_internal.cuh"
 
 namespace slg {
@@ -143,3 +145,113 @@ void scan_i64_to_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st
 }
 
 }  // namespace slg
+
+// ------------------------------------------------------------------------
+// Scan of per-row counts that allocates nothing.
+//
+// The same tile kernels as above, but the tile sums live in a fixed device
+// array compiled into the library instead of stream-ordered allocations.
+// Capacity: 32768 level-1 tile sums of 2048 counts each, i.e. at most
+// 67,108,864 counts per call; 264 KiB of device memory per GPU that loads the
+// library, held until the process exits.
+
+namespace {
+
+constexpr int64_t NOALLOC_TILES = 32768;
+constexpr int64_t NOALLOC_MAX_N = NOALLOC_TILES * slg::SCAN_TILE;
+constexpr int64_t NOALLOC_TILES2 = (NOALLOC_TILES + slg::SCAN_TILE - 1) / slg::SCAN_TILE;
+constexpr int64_t NOALLOC_ELEMS = (NOALLOC_TILES + 1) + (NOALLOC_TILES2 + 1);
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+std::mutex g_noalloc_mutex;
+long long* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+}  // namespace
+
+// Tile sums of every call, on every device (host code must not use this name
+// as an address: it resolves it with cudaGetSymbolAddress below).
+static __device__ __align__(256) long long g_noalloc_scan_sums[NOALLOC_ELEMS];
+
+namespace {
+
+// Device address of the array on the current device, looked up once per
+// device (the first call on each device does it).
+long long* noalloc_sums_on(int dev) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        throw slg::Error{SLG_EINVAL, "device ordinal beyond the no-allocation table"};
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scan_sums);
+        if (e != cudaSuccess)
+            throw slg::Error{SLG_ECUDA,
+                             std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
+        g_noalloc_addr[dev] = static_cast<long long*>(p);
+    }
+    return g_noalloc_addr[dev];
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int64_t n,
+                                              void* stream) {
+    using slg::Error;
+    try {
+        if (n < 0 || n > NOALLOC_MAX_N)
+            throw Error{SLG_EINVAL, "n must be in [0, 67108864] for the no-allocation scan"};
+        if (!offsets || (n > 0 && !counts)) throw Error{SLG_EINVAL, "NULL argument"};
+        if (!on_device(offsets) || (n > 0 && !on_device(counts)))
+            throw Error{SLG_EINVAL, "counts and offsets must be device memory"};
+        int dev = 0;
+        SLG_CUDA_TRY(cudaGetDevice(&dev));
+        long long* sums1 = noalloc_sums_on(dev);
+        long long* sums2 = sums1 + NOALLOC_TILES + 1;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        using slg::k_tile_reduce;
+        using slg::k_tile_scan;
+        constexpr int T = slg::SCAN_THREADS;
+        if (n == 0) {
+            SLG_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), st));
+        } else {
+            const int64_t nb1 = (n + slg::SCAN_TILE - 1) / slg::SCAN_TILE;
+            int64_t* out = reinterpret_cast<int64_t*>(offsets);
+            int64_t* s1 = reinterpret_cast<int64_t*>(sums1);
+            int64_t* s2 = reinterpret_cast<int64_t*>(sums2);
+            if (nb1 == 1) {
+                k_tile_scan<int32_t, int64_t><<<1, T, 0, st>>>(counts, n, nullptr, out);
+                SLG_LAUNCH_CHECK();
+            } else {
+                k_tile_reduce<int32_t, int64_t><<<(unsigned)nb1, T, 0, st>>>(counts, n, s1);
+                SLG_LAUNCH_CHECK();
+                const int64_t nb2 = (nb1 + slg::SCAN_TILE - 1) / slg::SCAN_TILE;
+                if (nb2 == 1) {
+                    k_tile_scan<int64_t, int64_t><<<1, T, 0, st>>>(s1, nb1, nullptr, s1);
+                    SLG_LAUNCH_CHECK();
+                } else {
+                    k_tile_reduce<int64_t, int64_t><<<(unsigned)nb2, T, 0, st>>>(s1, nb1, s2);
+                    SLG_LAUNCH_CHECK();
+                    k_tile_scan<int64_t, int64_t><<<1, T, 0, st>>>(s2, nb2, nullptr, s2);
+                    SLG_LAUNCH_CHECK();
+                    k_tile_scan<int64_t, int64_t><<<(unsigned)nb2, T, 0, st>>>(s1, nb1, s2, s1);
+                    SLG_LAUNCH_CHECK();
+                }
+                k_tile_scan<int32_t, int64_t><<<(unsigned)nb1, T, 0, st>>>(counts, n, s1, out);
+                SLG_LAUNCH_CHECK();
+            }
+        }
+    } catch (const Error& e) {
+        slg::set_error(e.code, e.msg);
+        return e.code;
+    }
+    return SLG_OK;
+}
+
