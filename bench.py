@@ -38,7 +38,7 @@ import synth  # noqa: E402
 WORKLOAD = ("medium: m=1,000,000 hyperedges, n=500,000 vertices, sizes log-normal(1.8,1.0) "
             "clipped [2,5000], vertex popularity Zipf(1.7), seed 0; s=1..8 sweep")
 METRIC = "s-line wedges/s (medium hypergraph, s=1..8, bit-exact)"
-WINDOW = 1 << 31          # pairs per output window (24 GiB of I/J/O)
+WINDOW = 1 << 31          # default pairs per output window (24 GiB of I/J/O)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--cpu-rows", type=int, default=600, help="rows in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--window", type=int, default=1 << 31, help="pairs per output window")
     return ap.parse_args()
 
 
@@ -145,6 +146,7 @@ def run_sweep(slg, g, s_list, bufs, stream, per_s):
     """Counting pass + windowed fill for every s on a loaded graph."""
     import torch
     I, J, O = bufs
+    WINDOW = I.numel()
     for s in s_list:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -178,7 +180,7 @@ def bench_ours(args):
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)
     stream = torch.cuda.Stream(dev)
-    I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+    I = torch.empty(args.window, dtype=torch.int32, device=dev)
     J = torch.empty_like(I)
     O = torch.empty_like(I)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -241,20 +243,21 @@ def bench_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    ms_tot = [[0.0] * 3, [0.0] * 3]
-    ln_tot = [[0] * 3, [0] * 3]
+    NM = slg.NMODES
+    ms_tot = [[0.0] * NM, [0.0] * NM]
+    ln_tot = [[0] * NM, [0] * NM]
     for ms, ln in kstats:
         for p in range(2):
-            for k in range(3):
+            for k in range(NM):
                 ms_tot[p][k] += ms[p][k]
                 ln_tot[p][k] += ln[p][k]
-    w_mode = [sum(mode_work[s][k][1] for s in s_list) for k in range(3)]
-    inc_mode = [sum(mode_work[s][k][2] for s in s_list) for k in range(3)]
-    pairs_mode = [sum(mode_work[s][k][3] for s in s_list) for k in range(3)]
+    w_mode = [sum(mode_work[s][k][1] for s in s_list) for k in range(NM)]
+    inc_mode = [sum(mode_work[s][k][2] for s in s_list) for k in range(NM)]
+    pairs_mode = [sum(mode_work[s][k][3] for s in s_list) for k in range(NM)]
     # candidates: (pass, mode) -> bytes per step
     cands = []
-    names = ["warp", "block", "dense"]
-    for k in range(3):
+    names = list(slg.MODE_NAMES)
+    for k in range(NM):
         cb = 4 * w_mode[k] + 8 * inc_mode[k]
         cands.append(("count", k, cb, ms_tot[0][k] / args.steps, ln_tot[0][k] / args.steps))
         cands.append(("fill", k, cb + 12 * pairs_mode[k], ms_tot[1][k] / args.steps,
@@ -263,20 +266,28 @@ def bench_ours(args):
     kname = f"k_{names[dom[1]]}_items<{'true' if dom[0] == 'fill' else 'false'}>"
     achieved = dom[2] / (dom[3] / 1e3) / 1e9 if dom[3] > 0 else 0.0
     traffic = profiled_traffic(kname, dom[2] / max(dom[4], 1))
+    # the output writes alone: 12 B per pair of the dominant kernel's handler
+    write_gbs = (12 * pairs_mode[dom[1]] / (dom[3] / 1e3) / 1e9
+                 if dom[0] == "fill" and dom[3] > 0 else None)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                 "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                 "bytes_per_launch": int(dom[2] / max(dom[4], 1)),
                 "launches_per_step": dom[4],
                 "ms_per_launch": round(dom[3] / max(dom[4], 1), 3),
-                "kernel_share_of_step": round(dom[3] / (elapsed_ms / args.steps), 4)}
+                "kernel_share_of_step": round(dom[3] / (elapsed_ms / args.steps), 4),
+                "output_write_GBps": round(write_gbs, 1) if write_gbs else None,
+                "output_write_frac": round(write_gbs / hbm_peak, 4) if write_gbs else None,
+                "model": "algorithmic bytes = 4 B/wedge + 8 B/incidence + 12 B/pair written"}
+    kernels_ms = {f"{ps}_{names[k]}": round(ms_tot[pi][k] / args.steps, 1)
+                  for pi, ps in enumerate(("count", "fill")) for k in range(NM)}
 
     per_s_out = []
     for s in s_list:
         d = per_s[s]
         ms = statistics.mean(d["ms"])
         pw = mode_work[s]
-        alg = sum(4 * pw[k][1] + 8 * pw[k][2] for k in range(3)) * 2 + 12 * d["pairs"]
+        alg = sum(4 * pw[k][1] + 8 * pw[k][2] for k in range(NM)) * 2 + 12 * d["pairs"]
         per_s_out.append({"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
                           "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
                           "s_edges_per_s": d["pairs"] / (ms / 1e3),
@@ -288,11 +299,12 @@ def bench_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.m == 1_000_000 else f"{WORKLOAD} (m={args.m})",
-                   "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": WINDOW,
+                   "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": args.window,
                    "l2": "flushed before each step (512 MiB device write); inputs resident",
                    "parallelism": f"replicas x{world}"},
         "s_edges_per_s": edges,
         "per_s": per_s_out,
+        "kernel_ms_per_step": kernels_ms,
         "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -322,6 +334,7 @@ def e2e(args, slg, h, s_list, stream, bufs):
     idx_h = torch.from_numpy(h.idx).pin_memory()
     rowoff = torch.empty(h.m + 1, dtype=torch.int64).pin_memory()
     I, J, O = bufs
+    WINDOW = I.numel()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     W = 0

@@ -176,19 +176,19 @@ slg_status slg_set_timing(slg_graph* g, int32_t enable);
 slg_status slg_last_timing(slg_graph* g, float* ms5);
 
 /*
- * Per-handler kernel time accumulated while timing is enabled: ms6[pass*3 +
- * mode] and launches6[pass*3 + mode], pass 0 = counting, 1 = fill, mode 0 =
- * warp table, 1 = CTA table, 2 = dense tiles. reset != 0 zeroes the totals
- * after reading. Either output may be NULL.
+ * Per-handler kernel time accumulated while timing is enabled: ms8[pass*4 +
+ * mode] and launches8[pass*4 + mode], pass 0 = counting, 1 = fill, mode 0 =
+ * warp table, 1 = CTA table, 2 = CTA dense tiles, 3 = warp dense tiles.
+ * reset != 0 zeroes the totals after reading. Either output may be NULL.
  */
-slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms6, int64_t* launches6);
+slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms8, int64_t* launches8);
 
 /*
- * Work per handler for s (runs the counting pass if needed): out12[mode*4 +
+ * Work per handler for s (runs the counting pass if needed): out16[mode*4 +
  * c] with c = 0 rows, 1 wedges, 2 incidences (sum of |e_i| over the rows),
- * 3 output pairs. The wedge total over the three handlers is W_s.
+ * 3 output pairs. The wedge total over the four handlers is W_s.
  */
-slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out12);
+slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out16);
 
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t slg_kernel_launches(void);
@@ -233,14 +233,18 @@ slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int6
  * blocked/cyclic ranges of Sections III-F and IV). A row with W_i wedges and
  * candidate span S_i (last minus first partner id, plus one) is handled
  *   - by one warp with a 256-slot table when W_i <= warp_max_wedges (<= 128);
- *   - by direct j-tiled counters when 256 * W_i >= dense_min_density * S_i
- *     (or S_i <= 4096), dense_item_tiles tiles of 32768 ids per item;
- *     dense_min_density < 0 disables this handler;
+ *   - by a dense j-tiled handler when 256 * W_i >= dense_min_density * S_i
+ *     (or S_i <= 4096); dense_min_density < 0 disables it. A dense row with
+ *     at most wdense_max_ranges (<= 32; 0 disables) wedge ranges through
+ *     non-hub vertices goes to the warp-level dense handler (items of
+ *     4096 * dense_item_tiles ids), other dense rows to the CTA-level one
+ *     (items of 32768 * dense_item_tiles ids);
  *   - otherwise by CTA hash tables, about block_item_wedges wedges per item.
  * Results do not depend on these values; only speed does. Resets the plan.
  */
 slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_item_wedges,
-                        int32_t dense_min_density, int32_t dense_item_tiles);
+                        int32_t dense_min_density, int32_t dense_item_tiles,
+                        int32_t wdense_max_ranges);
 
 #ifdef __cplusplus
 }

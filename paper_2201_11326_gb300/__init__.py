@@ -67,7 +67,7 @@ _SIGS = {
     "slg_plan_windows": (_i32, [_vp, _i32, _i64, _i32p, _i32, _i32p]),
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
-    "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
     "slg_kernel_launches": (_i64, []),
@@ -265,19 +265,23 @@ def slg_last_timing(g: Graph):
     return list(ms)
 
 
+NMODES = 4
+MODE_NAMES = ("warp", "block", "dense", "wdense")
+
+
 def slg_kernel_stats(g: Graph, reset: bool = False):
-    """(ms[2][3], launches[2][3]) per pass (count, fill) and handler (warp, block, dense)."""
-    ms = (ctypes.c_float * 6)()
-    ln = (ctypes.c_int64 * 6)()
+    """(ms[2][4], launches[2][4]) per pass (count, fill) and handler (MODE_NAMES)."""
+    ms = (ctypes.c_float * (2 * NMODES))()
+    ln = (ctypes.c_int64 * (2 * NMODES))()
     _check(lib().slg_kernel_stats(g.handle, 1 if reset else 0, ms, ln))
-    return ([list(ms[0:3]), list(ms[3:6])], [list(ln[0:3]), list(ln[3:6])])
+    return ([list(ms[0:NMODES]), list(ms[NMODES:])], [list(ln[0:NMODES]), list(ln[NMODES:])])
 
 
 def slg_mode_stats(g: Graph, s: int):
-    """[[rows, wedges, incidences, pairs] for warp, block, dense]."""
-    out = (ctypes.c_int64 * 12)()
+    """[[rows, wedges, incidences, pairs] per handler (MODE_NAMES)]."""
+    out = (ctypes.c_int64 * (4 * NMODES))()
     _check(lib().slg_mode_stats(g.handle, s, out))
-    return [list(out[4 * k:4 * k + 4]) for k in range(3)]
+    return [list(out[4 * k:4 * k + 4]) for k in range(NMODES)]
 
 
 def slg_kernel_launches() -> int:
@@ -297,6 +301,7 @@ def slg_scan_counts_noalloc(counts, offsets, stream=None):
 
 
 def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,
-                 dense_min_density: int = 64, dense_item_tiles: int = 4):
+                 dense_min_density: int = 64, dense_item_tiles: int = 16,
+                 wdense_max_ranges: int = 32):
     _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
-                              dense_item_tiles))
+                              dense_item_tiles, wdense_max_ranges))

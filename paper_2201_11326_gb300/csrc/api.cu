@@ -72,7 +72,8 @@ BinParams default_bins() {
     b.warp_max_wedges = 128;
     b.block_item_wedges = 1024;
     b.dense_min_density = 64;  // dense when W_i >= span / 4
-    b.dense_item_tiles = 4;
+    b.dense_item_tiles = 16;
+    b.wdense_max_ranges = WD_MAXR;
     return b;
 }
 
@@ -140,6 +141,8 @@ void free_graph_dev(slg::GraphDev& g, cudaStream_t st) {
     slg::dfree(g.offT, st);
     slg::dfree(g.idxT, st);
     slg::dfree(g.tpos, st);
+    slg::dfree(g.hubidx, st);
+    slg::dfree(g.hubmask, st);
 }
 
 // Count pass for s (cached per handle): plan, count, offsets.
@@ -269,6 +272,11 @@ slg_status slg_load(const int32_t* off, const int32_t* idx, int32_t m, int32_t n
         g.min_size = fl[1] == INT32_MAX ? 0 : fl[1];
         g.max_size = fl[2];
         slg::build_transpose(g.idx, g.rowid, n, g.nnz, g.offT, g.idxT, g.tpos, h->st);
+        g.hubidx = slg::dalloc<int32_t>((size_t)n + 1, h->st);
+        // +64: the warp dense handler reads hub masks 4 at a time from 32-aligned tiles
+        g.hubmask = slg::dalloc<uint32_t>((size_t)m + 64, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(g.hubmask, 0, sizeof(uint32_t) * ((size_t)m + 64), h->st));
+        g.nhubs = slg::build_hubs(g.off, g.idx, g.offT, m, n, g.hubidx, g.hubmask, h->st);
         SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
         h->timer.init();
         slg::mtimer_init(h->mtimer);
@@ -466,12 +474,12 @@ slg_status slg_set_timing(slg_graph* h, int32_t enable) {
     return SLG_OK;
 }
 
-slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms6, int64_t* launches6) {
+slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms8, int64_t* launches8) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < slg::NMODES; ++k) {
-            if (ms6) ms6[pass * slg::NMODES + k] = h->mtimer.ms[pass][k];
-            if (launches6) launches6[pass * slg::NMODES + k] = h->mtimer.launches[pass][k];
+            if (ms8) ms8[pass * slg::NMODES + k] = h->mtimer.ms[pass][k];
+            if (launches8) launches8[pass * slg::NMODES + k] = h->mtimer.launches[pass][k];
             if (reset) {
                 h->mtimer.ms[pass][k] = 0;
                 h->mtimer.launches[pass][k] = 0;
@@ -480,14 +488,14 @@ slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms6, int64_t* la
     return SLG_OK;
 }
 
-slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out12) {
-    if (!h || !out12) return fail(SLG_EINVAL, "NULL argument");
+slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out16) {
+    if (!h || !out16) return fail(SLG_EINVAL, "NULL argument");
     API_BEGIN
     ensure_counted(h, s);
     int64_t st[slg::NMODES][4];
     slg::plan_mode_stats(h->g, h->plan, st, h->st);
     for (int k = 0; k < slg::NMODES; ++k)
-        for (int c = 0; c < 4; ++c) out12[k * 4 + c] = st[k][c];
+        for (int c = 0; c < 4; ++c) out16[k * 4 + c] = st[k][c];
     API_END
 }
 
@@ -500,16 +508,19 @@ slg_status slg_last_timing(slg_graph* h, float* ms5) {
 }
 
 slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_item_wedges,
-                        int32_t dense_min_density, int32_t dense_item_tiles) {
+                        int32_t dense_min_density, int32_t dense_item_tiles,
+                        int32_t wdense_max_ranges) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     if (warp_max_wedges < 0 || warp_max_wedges > slg::WARP_TABLE / 2 || block_item_wedges < 1 ||
-        dense_item_tiles < 1)
+        dense_item_tiles < 1 || dense_item_tiles > 4096 || wdense_max_ranges < 0 ||
+        wdense_max_ranges > slg::WD_MAXR)
         return fail(SLG_EINVAL, "bin parameter out of range");
     API_BEGIN
     h->bp.warp_max_wedges = warp_max_wedges;
     h->bp.block_item_wedges = block_item_wedges;
     h->bp.dense_min_density = dense_min_density;
     h->bp.dense_item_tiles = dense_item_tiles;
+    h->bp.wdense_max_ranges = wdense_max_ranges;
     h->plan.release(h->st);
     API_END
 }

@@ -14,10 +14,9 @@
 //               with atomicAdd counts; a slice with more than 2048 distinct
 //               partners is split in two j halves and redone, so no table
 //               overflows and nothing spills off chip;
-//   MODE_DENSE  one CTA, direct-addressed 16-bit counters for 32768
-//               consecutive j (a j tile); the item walks its tiles in order,
-//               advancing one cursor per wedge range (the adj_s lists are
-//               ascending), reading H^T with 16-byte vector loads.
+//   MODE_DENSE  one CTA per slice walking 32768-wide j tiles in order: the
+//               hub part of each overlap is a popcount of two 32-bit hub
+//               masks, the rest direct-addressed 16-bit counters (see below).
 //
 // Both passes run the same code: the counting pass stores the number of
 // partners per item, a scan turns those into output offsets, and the fill
@@ -391,138 +390,383 @@ k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 }
 
 // =========================================================== MODE_DENSE
+//
+// Overlap of row i with partner j, split by vertex class:
+//   |e_i ∩ e_j| = popc(hubmask[i] & hubmask[j])            (hub vertices)
+//               + #{non-hub v in e_i ∩ e_j, wedge (i,v,j)} (counted here)
+// Hubs are the (at most 32) highest-degree vertices, fixed at load time;
+// hubmask[r] has bit b set when hub b is in e_r. Pruning needs no mask
+// change: a partner with |e_j| < s has overlap <= |e_j| < s whatever is
+// added. Only non-hub wedges touch shared memory: 16-bit counters for one
+// 32768-wide j tile, incremented by atomicAdd with lane-contiguous reads of
+// adj_s (consecutive lanes -> consecutive partners -> distinct banks). Each
+// non-hub wedge range keeps a cursor that advances tile by tile (the lists are
+// ascending), so no per-tile search is needed.
 
 constexpr int HALF = DENSE_TILE / 2;  // 16-bit counters, two per word
 constexpr int LOG_HALF = 14;
 static_assert((1 << LOG_HALF) == HALF, "tile must be 2^15");
-constexpr size_t DENSE_SMEM = sizeof(uint32_t) * HALF + sizeof(int32_t) * 3 * DENSE_MAXE;
+constexpr int DENSE_WARPS = DENSE_THREADS / 32;
+constexpr int DENSE_SEG = DENSE_TILE / DENSE_WARPS;  // partners per warp per tile
+static_assert(DENSE_SEG == 2048, "extraction keeps 64 ballots per warp");
+constexpr size_t DENSE_SMEM = sizeof(uint32_t) * HALF + sizeof(int32_t) * 2 * DENSE_MAXE;
+
+__device__ __forceinline__ int32_t dense_count(uint32_t hmi, const uint32_t* __restrict__ hubmask,
+                                               const uint32_t* ctr, int32_t t0, int32_t ci) {
+    const uint32_t w = ctr[ci & (HALF - 1)];
+    return __popc(hmi & __ldg(&hubmask[t0 + ci])) +
+           (int32_t)((w >> ((ci >> LOG_HALF) << 4)) & 0xffffu);
+}
 
 template <bool FILL>
 __global__ void __launch_bounds__(DENSE_THREADS)
 k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
-              const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
-              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
-              int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
-              int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
-              int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+              const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+              const int32_t* __restrict__ hubidx, const uint32_t* __restrict__ hubmask,
+              const int32_t* __restrict__ wbeg, const int32_t* __restrict__ wend,
+              const int32_t* __restrict__ idxTs, int32_t s, int32_t* __restrict__ icnt,
+              const int64_t* __restrict__ ioff, int32_t* __restrict__ I, int32_t* __restrict__ J,
+              int32_t* __restrict__ O, int32_t* __restrict__ queue, int64_t limit,
+              int32_t* __restrict__ err) {
     constexpr int NT = DENSE_THREADS;
+    constexpr int NW = DENSE_WARPS;
     extern __shared__ __align__(16) uint32_t dyn[];
-    uint32_t* ctr = dyn;                                        // HALF words
-    int32_t* cur = reinterpret_cast<int32_t*>(dyn + HALF);      // DENSE_MAXE
+    uint32_t* ctr = dyn;                                    // HALF words
+    int32_t* cur = reinterpret_cast<int32_t*>(dyn + HALF);  // non-hub cursors
     int32_t* endp = cur + DENSE_MAXE;
-    int32_t* hiv = endp + DENSE_MAXE;
-    __shared__ int32_t tmp[NT / 32 + 1];
-    __shared__ int32_t sh_pos;
-    const int tid = threadIdx.x;
+    __shared__ int32_t wtot[NW];
+    __shared__ int32_t sh_pos, sh_nnh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
 
     for (;;) {
-        if (tid == 0) sh_pos = lo + atomicAdd(queue, 1);
+        if (tid == 0) {
+            sh_pos = lo + atomicAdd(queue, 1);
+            sh_nnh = 0;
+        }
         __syncthreads();
         const int32_t pos = sh_pos;
         if (pos >= hi) break;
         const int32_t q = list[pos];
         const Item it = items[q];
         const int32_t i = it.row;
+        const uint32_t hmi = hubmask[i];
         const int32_t e0 = off[i];
         const int32_t ne = off[i + 1] - e0;
+        // non-hub wedge ranges of the row, cursors at the item's first partner
         for (int32_t k = tid; k < ne; k += NT) {
-            const int32_t b0 = wbeg[e0 + k], t0 = wend[e0 + k];
-            if (t0 > b0) {
-                cur[k] = lower_bound_dev(idxTs, b0, t0, it.jlo);
-                endp[k] = t0;
-            } else {
-                cur[k] = 0;
-                endp[k] = 0;
+            const int32_t e = e0 + k;
+            const int32_t b0 = wbeg[e], t0 = wend[e];
+            if (t0 > b0 && hubidx[idx[e]] < 0) {
+                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo)
+                                      ? b0 : lower_bound_dev(idxTs, b0, t0, it.jlo);
+                if (c < t0) {
+                    const int32_t slot = atomicAdd(&sh_nnh, 1);
+                    cur[slot] = c;
+                    endp[slot] = t0;
+                }
             }
         }
         const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
         int64_t out_pos = 0;
         __syncthreads();
+        const int32_t nnh = sh_nnh;
         for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += DENSE_TILE) {
             const int32_t span = min(DENSE_TILE, it.jhi - t0);
             const int32_t t1 = t0 + span;
-            // clear the words this tile uses
             const int32_t nz = span > HALF ? HALF : ((span + 3) & ~3);
             for (int32_t w = 4 * tid; w < nz; w += 4 * NT)
                 *reinterpret_cast<uint4*>(ctr + w) = make_uint4(0, 0, 0, 0);
-            for (int32_t k = tid; k < ne; k += NT) {
-                const int32_t c0 = cur[k], e = endp[k];
-                hiv[k] = (c0 < e) ? lower_bound_dev(idxTs, c0, min(e, c0 + span), t1) : c0;
+            __syncthreads();
+            // non-hub wedges of this tile: one warp per wedge range, 32
+            // consecutive entries per step, until a partner reaches t1
+            for (int32_t k = warp; k < nnh; k += NW) {
+                int32_t c = cur[k];
+                const int32_t e = endp[k];
+                for (;;) {
+                    const int32_t p = c + lane;
+                    const int32_t j = p < e ? __ldg(&idxTs[p]) : INT32_MAX;
+                    const bool valid = j < t1;
+                    if (valid) {
+                        const int32_t ci = j - t0;
+                        atomicAdd(&ctr[ci & (HALF - 1)], 1u << ((ci >> LOG_HALF) << 4));
+                    }
+                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
+                    c += n;
+                    if (n < 32) break;
+                }
+                if (lane == 0) cur[k] = c;
             }
             __syncthreads();
-            for (int32_t k = 0; k < ne; ++k) {
-                const int32_t a = cur[k], z = hiv[k];
-                if (a >= z) continue;
-                for (int32_t p = (a & ~3) + 4 * tid; p < z; p += 4 * NT) {
-                    const int4 v = *reinterpret_cast<const int4*>(idxTs + p);
-                    const int32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int32_t pp = p + c;
-                        if (pp >= a && pp < z) {
-                            const int32_t ci = vv[c] - t0;
-                            atomicAdd(&ctr[ci & (HALF - 1)], 1u << ((ci >> LOG_HALF) << 4));
-                        }
-                    }
+            // extraction, pass 1: survivors per 32 partners, in j order per warp segment
+            const int32_t seg0 = warp * DENSE_SEG;
+            uint32_t bs0 = 0, bs1 = 0;
+            int32_t cnt = 0;
+            for (int32_t r = 0; r < DENSE_SEG / 32; ++r) {
+                const int32_t ci = seg0 + r * 32 + lane;
+                bool f = false;
+                if (ci < span) f = dense_count(hmi, hubmask, ctr, t0, ci) >= s;
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (FILL && lane == (r & 31)) {
+                    if (r < 32)
+                        bs0 = bal;
+                    else
+                        bs1 = bal;
                 }
+                cnt += __popc(bal);
             }
+            if (lane == 0) wtot[warp] = cnt;
             __syncthreads();
-            for (int32_t k = tid; k < ne; k += NT) cur[k] = hiv[k];
-            if (!FILL) {
-                int32_t mine = 0;
-                for (int32_t w = 4 * tid; w < HALF; w += 4 * NT) {
-                    const uint4 x = *reinterpret_cast<const uint4*>(ctr + w);
-                    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+            int32_t before = 0, tile_total = 0;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (w + c < span && (int32_t)(xs[c] & 0xffffu) >= s) ++mine;
-                        if (w + c + HALF < span && (int32_t)(xs[c] >> 16) >= s) ++mine;
-                    }
-                }
-                int32_t tot;
-                block_excl_scan<NT>(mine, &tot, tmp);
-                out_pos += tot;
-            } else {
-                for (int32_t chunk = 0; chunk < span; chunk += 4 * NT) {
-                    const int32_t c0 = chunk + 4 * tid;  // four consecutive counters
-                    int32_t cnt[4] = {0, 0, 0, 0};
-                    int32_t mine = 0;
-                    if (c0 < span) {
-                        const uint4 x = *reinterpret_cast<const uint4*>(ctr + (c0 & (HALF - 1)));
-                        const int sh = (c0 >> LOG_HALF) << 4;
-                        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int32_t v = (int32_t)((xs[c] >> sh) & 0xffffu);
-                            cnt[c] = (c0 + c < span && v >= s) ? v : 0;
-                            mine += cnt[c] ? 1 : 0;
+            for (int w = 0; w < NW; ++w) {
+                const int32_t v = wtot[w];
+                before += (w < warp) ? v : 0;
+                tile_total += v;
+            }
+            if (FILL) {
+                // pass 2: write survivors at their ordered positions
+                int64_t base = obase + out_pos + before;
+                for (int32_t r = 0; r < DENSE_SEG / 32; ++r) {
+                    const unsigned bal = __shfl_sync(0xffffffffu, r < 32 ? bs0 : bs1, r & 31);
+                    if (bal == 0) continue;
+                    if ((bal >> lane) & 1u) {
+                        const int32_t ci = seg0 + r * 32 + lane;
+                        const int64_t p2 = base + __popc(bal & lt);
+                        if (p2 < limit) {
+                            I[p2] = i;
+                            J[p2] = t0 + ci;
+                            O[p2] = dense_count(hmi, hubmask, ctr, t0, ci);
+                        } else {
+                            atomicOr(err, ERR_BOUNDS);
                         }
                     }
-                    int32_t tot;
-                    int32_t p = block_excl_scan<NT>(mine, &tot, tmp);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (cnt[c]) {
-                            const int64_t p2 = obase + out_pos + p;
-                            if (p2 < limit) {
-                                I[p2] = i;
-                                J[p2] = t0 + c0 + c;
-                                O[p2] = cnt[c];
-                            } else {
-                                atomicOr(err, ERR_BOUNDS);
-                            }
-                            ++p;
-                        }
-                    }
-                    out_pos += tot;
+                    base += __popc(bal);
                 }
             }
+            out_pos += tile_total;
             __syncthreads();
         }
         if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
         __syncthreads();
+    }
+}
+
+// ========================================================== MODE_WDENSE
+//
+// The dense handler at warp granularity, for rows with at most 32 non-hub
+// wedge ranges (almost every dense row): one warp owns a slice, a 4096-wide j
+// tile of 8-bit counters (4 KB of shared memory; a row has at most 32 non-hub
+// ranges, so a non-hub count is at most 32) and one non-hub cursor per lane,
+// so no CTA barrier is ever needed. Counter of partner t0 + c: byte c % 4 of
+// word c / 4, so a lane's four consecutive partners share one word. Tiles
+// start at multiples of 32 ids. Per tile:
+//   1. clear the counters;
+//   2. add the non-hub wedges: ranges with a partner inside the tile take
+//      part in rounds; a round loads the next 32 entries of up to four ranges
+//      at once, then counts the ones below the tile end;
+//   3. extraction. Counting pass: four consecutive partners per lane, hub
+//      masks by 16-byte loads, overlaps summed and compared four at a time
+//      inside one 32-bit word (each byte stays below 128, so no carry crosses
+//      bytes). Fill pass: one partner per lane so that the survivors are
+//      written with coalesced stores in ascending j, eight blocks of loads in
+//      flight.
+
+constexpr int WD_WORDS = WD_TILE / 4;                  // counter words per warp
+constexpr size_t WD_WARP_SMEM_WORDS = WD_WORDS + 2 * 32;  // + staging of 32 ranges
+constexpr size_t WD_SMEM = sizeof(uint32_t) * WD_WARP_SMEM_WORDS * WD_WARPS;
+constexpr int WD_CBLK = 4;    // counting: 128-partner blocks whose loads are issued together
+constexpr int WD_FBLK = 8;    // fill: 32-partner blocks whose loads are issued together
+constexpr int WD_GROUP = 4;   // non-hub ranges loaded together per round
+static_assert(WD_TILE % (128 * WD_CBLK) == 0 && WD_TILE % (32 * WD_FBLK) == 0, "tile blocks");
+static_assert(MAX_HUBS + WD_MAXR < 128, "byte-wise overlap sums must stay below 128");
+
+template <bool FILL>
+__global__ void __launch_bounds__(WD_WARPS * 32, 3)
+k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+               const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+               const int32_t* __restrict__ hubidx, const uint32_t* __restrict__ hubmask,
+               const int32_t* __restrict__ wbeg, const int32_t* __restrict__ wend,
+               const int32_t* __restrict__ idxTs, int32_t s, int32_t* __restrict__ icnt,
+               const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
+               int32_t* __restrict__ J, int32_t* __restrict__ O, int32_t* __restrict__ queue,
+               int64_t limit, int32_t* __restrict__ err) {
+    extern __shared__ __align__(16) uint32_t dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* ctr = dyn + (size_t)warp * WD_WARP_SMEM_WORDS;
+    const uint8_t* ctr8 = reinterpret_cast<const uint8_t*>(ctr);
+    int32_t* stage = reinterpret_cast<int32_t*>(ctr + WD_WORDS);  // [0..31] cursor, [32..63] end
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+    // byte-wise threshold: x >= s  <=>  bit 7 of x + (128 - s), for x < 128
+    const uint32_t bias4 = 0x01010101u * (uint32_t)(128 - min(s, 128));
+
+    for (;;) {
+        int32_t pos = 0;
+        if (lane == 0) pos = lo + atomicAdd(queue, 1);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (pos >= hi) break;
+        const int32_t q = list[pos];
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const uint32_t hmi = hubmask[i];
+        const int32_t e0 = off[i];
+        const int32_t ne = off[i + 1] - e0;
+        // gather the non-hub wedge ranges, cursor at the slice's first partner
+        int32_t nr = 0;
+        for (int32_t kb = 0; kb < ne; kb += 32) {
+            const int32_t k = kb + lane;
+            bool ok = false;
+            int32_t c = 0, t = 0;
+            if (k < ne) {
+                const int32_t e = e0 + k;
+                const int32_t b0 = wbeg[e];
+                t = wend[e];
+                if (t > b0 && hubidx[idx[e]] < 0) {
+                    c = (__ldg(&idxTs[b0]) >= it.jlo) ? b0 : lower_bound_dev(idxTs, b0, t, it.jlo);
+                    ok = c < t;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            const int32_t slot = nr + __popc(bal & lt);
+            if (ok) {
+                if (slot < WD_MAXR) {
+                    stage[slot] = c;
+                    stage[32 + slot] = t;
+                } else {
+                    atomicOr(err, ERR_TABLE);  // binning guarantees <= 32 ranges
+                }
+            }
+            nr += __popc(bal);
+        }
+        nr = min(nr, WD_MAXR);
+        __syncwarp();
+        int32_t my_cur = lane < nr ? stage[lane] : 0;
+        const int32_t my_end = lane < nr ? stage[32 + lane] : 0;
+        // partner at the cursor (INT32_MAX once the range is used up)
+        int32_t my_next = (lane < nr && my_cur < my_end) ? __ldg(&idxTs[my_cur]) : INT32_MAX;
+        __syncwarp();
+
+        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
+        int64_t out_pos = 0;
+        int32_t my_count = 0;
+        for (int32_t t0 = it.jlo & ~31; t0 < it.jhi; t0 += WD_TILE) {
+            const int32_t t1 = min(t0 + WD_TILE, it.jhi);  // partners j in [max(t0, jlo), t1)
+            const int32_t jfirst = max(t0, it.jlo);
+            const int32_t span = t1 - t0;
+            // 1. clear (only the words this tile uses)
+            const int32_t nzw = (((span + 3) >> 2) + 3) & ~3;  // words, whole uint4s
+            for (int32_t w = 4 * lane; w < nzw; w += 128)
+                *reinterpret_cast<uint4*>(ctr + w) = make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            // 2. non-hub wedges
+            unsigned active = __ballot_sync(0xffffffffu, my_next < t1);
+            while (active) {
+                int32_t kk[WD_GROUP], vv[WD_GROUP];
+                unsigned a = active;
+#pragma unroll
+                for (int g = 0; g < WD_GROUP; ++g) {
+                    const int32_t k = a ? __ffs(a) - 1 : -1;
+                    a &= a - 1u;
+                    kk[g] = k;
+                    const int32_t c = __shfl_sync(0xffffffffu, my_cur, k & 31);
+                    const int32_t e = __shfl_sync(0xffffffffu, my_end, k & 31);
+                    const int32_t p = c + lane;
+                    vv[g] = (k >= 0 && p < e) ? __ldg(&idxTs[p]) : INT32_MAX;
+                }
+#pragma unroll
+                for (int g = 0; g < WD_GROUP; ++g) {
+                    const int32_t k = kk[g];
+                    if (k < 0) break;
+                    const bool valid = vv[g] < t1;
+                    if (valid) {
+                        const int32_t ci = vv[g] - t0;
+                        atomicAdd(&ctr[ci >> 2], 1u << ((ci & 3) << 3));
+                    }
+                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
+                    // the first entry not taken is the range's next partner
+                    const int32_t nxt = __shfl_sync(0xffffffffu, vv[g], n & 31);
+                    if (lane == k) {
+                        my_cur += n;
+                        if (n < 32) my_next = nxt;
+                    }
+                    if (n < 32) active &= ~(1u << k);
+                }
+            }
+            __syncwarp();
+            // 3. extraction
+            if (!FILL) {
+                for (int32_t g = 0; g < span; g += 128 * WD_CBLK) {
+                    uint4 hv[WD_CBLK];
+                    uint32_t cw[WD_CBLK];
+#pragma unroll
+                    for (int b = 0; b < WD_CBLK; ++b) {
+                        const int32_t ci = g + b * 128 + 4 * lane;
+                        if (ci < span) {
+                            hv[b] = __ldg(reinterpret_cast<const uint4*>(hubmask + t0 + ci));
+                            cw[b] = ctr[ci >> 2];
+                        } else {
+                            hv[b] = make_uint4(0, 0, 0, 0);
+                            cw[b] = 0;
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < WD_CBLK; ++b) {
+                        const int32_t ci = g + b * 128 + 4 * lane;
+                        const uint32_t p4 = (uint32_t)__popc(hmi & hv[b].x) |
+                                            ((uint32_t)__popc(hmi & hv[b].y) << 8) |
+                                            ((uint32_t)__popc(hmi & hv[b].z) << 16) |
+                                            ((uint32_t)__popc(hmi & hv[b].w) << 24);
+                        uint32_t f4 = (p4 + cw[b] + bias4) & 0x80808080u;
+                        const int32_t j0 = t0 + ci;
+                        if (j0 < jfirst || j0 + 4 > t1) {  // partial block at a tile edge
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+                                if (j0 + r < jfirst || j0 + r >= t1) f4 &= ~(0x80u << (8 * r));
+                        }
+                        my_count += __popc(f4);
+                    }
+                }
+            } else {
+                for (int32_t g = 0; g < span; g += 32 * WD_FBLK) {
+                    uint32_t hm[WD_FBLK], cb[WD_FBLK];
+#pragma unroll
+                    for (int b = 0; b < WD_FBLK; ++b) {
+                        const int32_t ci = g + b * 32 + lane;
+                        hm[b] = ci < span ? __ldg(&hubmask[t0 + ci]) : 0u;
+                        cb[b] = ci < span ? ctr8[ci] : 0u;
+                    }
+#pragma unroll
+                    for (int b = 0; b < WD_FBLK; ++b) {
+                        const int32_t ci = g + b * 32 + lane;
+                        const int32_t j = t0 + ci;
+                        const int32_t c = __popc(hmi & hm[b]) + (int32_t)cb[b];
+                        const bool f = j >= jfirst && j < t1 && c >= s;
+                        const unsigned bal = __ballot_sync(0xffffffffu, f);
+                        if (f) {
+                            const int64_t p2 = obase + out_pos + __popc(bal & lt);
+                            if (p2 < limit) {
+                                I[p2] = i;
+                                J[p2] = j;
+                                O[p2] = c;
+                            } else {
+                                atomicOr(err, ERR_BOUNDS);
+                            }
+                        }
+                        out_pos += __popc(bal);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (!FILL) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) my_count += __shfl_xor_sync(0xffffffffu, my_count, d);
+            if (lane == 0) icnt[q] = my_count;
+        }
     }
 }
 
@@ -570,7 +814,7 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 
 struct Occupancy {
     int sms = 0;
-    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0;
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, wdense_ctas = 0;
 };
 
 Occupancy& occupancy() {
@@ -585,7 +829,16 @@ Occupancy& occupancy() {
         SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)DENSE_SMEM));
-        int a = 0, b = 0, c = 0;
+        SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)WD_SMEM));
+        SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)WD_SMEM));
+        int a = 0, b = 0, c = 0, d = 0;
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_wdense_items<true>,
+                                                                   WD_WARPS * 32, WD_SMEM));
+        o.wdense_ctas = o.sms * (d > 0 ? d : 1);
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
                                                                    WARP_CTA_WARPS * 32, 0));
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_block_items<true>,
@@ -611,7 +864,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
     auto tick = [&](int mode, int edge) {
         if (timed) SLG_CUDA_TRY(cudaEventRecord(mt->ev[2 * mode + edge], st));
     };
-    bool ran[NMODES] = {false, false, false};
+    bool ran[NMODES] = {};
     if (p.mode_count[MODE_WARP]) {
         ran[MODE_WARP] = true;
         tick(MODE_WARP, 0);
@@ -635,9 +888,20 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_DENSE, 0);
         k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
             p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_DENSE, limit, err);
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O,
+            queue + MODE_DENSE, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_DENSE, 1);
+    }
+    if (p.mode_count[MODE_WDENSE]) {
+        ran[MODE_WDENSE] = true;
+        tick(MODE_WDENSE, 0);
+        k_wdense_items<FILL><<<oc.wdense_ctas, WD_WARPS * 32, WD_SMEM, st>>>(
+            p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi, g.off,
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O,
+            queue + MODE_WDENSE, limit, err);
+        SLG_LAUNCH_CHECK();
+        tick(MODE_WDENSE, 1);
     }
     if (timed) {
         for (int k = 0; k < NMODES; ++k) {

@@ -64,23 +64,26 @@ __global__ void k_wedge_ranges(const int32_t* __restrict__ idx, const int32_t* _
 
 // One warp per row: W_{s,i} = sum of wedge-range lengths, and the first and
 // last candidate j (adj_s lists are ascending, so these are range ends).
-__global__ void k_row_work(const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+__global__ void k_row_work(const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                           const int32_t* __restrict__ hubidx, const int32_t* __restrict__ wbeg,
                            const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs,
                            int32_t m, int64_t* __restrict__ W, int32_t* __restrict__ jmin,
-                           int32_t* __restrict__ jmax, unsigned long long* __restrict__ wtotal) {
+                           int32_t* __restrict__ jmax, int32_t* __restrict__ nnh,
+                           unsigned long long* __restrict__ wtotal) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long acc_total = 0;
     for (int64_t i = warp; i < m; i += nwarps) {
         int64_t w = 0;
-        int32_t lo = INT32_MAX, hi = -1;
+        int32_t lo = INT32_MAX, hi = -1, r = 0;
         for (int32_t e = off[i] + lane; e < off[i + 1]; e += 32) {
             const int32_t b = wbeg[e], t = wend[e];
             if (t > b) {
                 w += t - b;
                 lo = min(lo, idxTs[b]);
                 hi = max(hi, idxTs[t - 1]);
+                r += hubidx[idx[e]] < 0 ? 1 : 0;
             }
         }
 #pragma unroll
@@ -88,11 +91,13 @@ __global__ void k_row_work(const int32_t* __restrict__ off, const int32_t* __res
             w += __shfl_xor_sync(0xffffffffu, w, d);
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+            r += __shfl_xor_sync(0xffffffffu, r, d);
         }
         if (lane == 0) {
             W[i] = w;
             jmin[i] = lo;
             jmax[i] = hi;
+            nnh[i] = r;
             acc_total += (unsigned long long)w;
         }
     }
@@ -105,7 +110,8 @@ struct RowItems {
     int64_t step;  // j width of each item (dense) or 0 (uniform split)
 };
 
-__device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, BinParams bp) {
+__device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, int32_t nnh,
+                             BinParams bp) {
     RowItems r{MODE_WARP, 0, 0};
     if (w <= 0) return r;
     const int64_t span = (int64_t)hi - lo + 1;
@@ -114,9 +120,16 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, Bi
         r.count = 1;
         return r;
     }
-    const bool dense_ok = size <= DENSE_MAX_SIZE && size <= DENSE_MAXE;
-    if (bp.dense_min_density >= 0 && dense_ok &&
-        (span <= 4096 || 256 * w >= (int64_t)bp.dense_min_density * span)) {
+    const bool dense_wanted = bp.dense_min_density >= 0 &&
+                              (span <= 4096 || 256 * w >= (int64_t)bp.dense_min_density * span);
+    if (dense_wanted && nnh <= bp.wdense_max_ranges) {
+        // warp tiles: non-hub counts <= 32, so any row size fits 16-bit counters
+        r.mode = MODE_WDENSE;
+        r.step = (int64_t)WD_ITEM * bp.dense_item_tiles;
+        r.count = (int32_t)((span + r.step - 1) / r.step);
+        return r;
+    }
+    if (dense_wanted && size <= DENSE_MAX_SIZE && size <= DENSE_MAXE) {
         r.mode = MODE_DENSE;
         r.step = (int64_t)DENSE_TILE * bp.dense_item_tiles;
         r.count = (int32_t)((span + r.step - 1) / r.step);
@@ -132,16 +145,17 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, Bi
 
 __global__ void k_item_count(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                              const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
-                             int32_t m, BinParams bp, int32_t* __restrict__ nitem) {
-    GRID_STRIDE(i, m) nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], bp).count;
+                             const int32_t* __restrict__ nnh, int32_t m, BinParams bp,
+                             int32_t* __restrict__ nitem) {
+    GRID_STRIDE(i, m) nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], bp).count;
 }
 
 __global__ void k_item_emit(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                             const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
-                            int32_t m, BinParams bp, const int32_t* __restrict__ row_item,
-                            Item* __restrict__ items) {
+                            const int32_t* __restrict__ nnh, int32_t m, BinParams bp,
+                            const int32_t* __restrict__ row_item, Item* __restrict__ items) {
     GRID_STRIDE(i, m) {
-        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], bp);
+        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], bp);
         if (r.count == 0) continue;
         const int64_t lo = jmin[i], end = (int64_t)jmax[i] + 1, span = end - lo;
         Item* out = items + row_item[i];
@@ -248,6 +262,7 @@ void Plan::release(cudaStream_t st) {
     dfree(W, st);
     dfree(jmin, st);
     dfree(jmax, st);
+    dfree(nnh, st);
     dfree(row_item, st);
     dfree(items, st);
     for (int k = 0; k < NMODES; ++k) {
@@ -306,18 +321,21 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.W = dalloc<int64_t>(m, st);
     p.jmin = dalloc<int32_t>(m, st);
     p.jmax = dalloc<int32_t>(m, st);
+    p.nnh = dalloc<int32_t>(m, st);
     unsigned long long* wtot = dalloc<unsigned long long>(1, st);
     SLG_CUDA_TRY(cudaMemsetAsync(wtot, 0, sizeof(unsigned long long), st));
     if (m) {
-        k_row_work<<<grid_for((int64_t)m * 32, T), T, 0, st>>>(g.off, p.wbeg, p.wend, p.idxTs, m,
-                                                               p.W, p.jmin, p.jmax, wtot);
+        k_row_work<<<grid_for((int64_t)m * 32, T), T, 0, st>>>(g.off, g.idx, g.hubidx, p.wbeg,
+                                                               p.wend, p.idxTs, m, p.W, p.jmin,
+                                                               p.jmax, p.nnh, wtot);
         SLG_LAUNCH_CHECK();
     }
     // items
     int32_t* nitem = dalloc<int32_t>(m, st);
     p.row_item = dalloc<int32_t>((size_t)m + 1, st);
     if (m) {
-        k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, m, bp, nitem);
+        k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, bp,
+                                                   nitem);
         SLG_LAUNCH_CHECK();
     }
     scan_i32_to_i32(nitem, p.row_item, m, st);
@@ -333,8 +351,8 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.wedges = (int64_t)wtot_h;
     p.items = dalloc<Item>(p.nitems, st);
     if (m) {
-        k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, m, bp, p.row_item,
-                                                  p.items);
+        k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, bp,
+                                                  p.row_item, p.items);
         SLG_LAUNCH_CHECK();
     }
     int32_t* flags = dalloc<int32_t>(p.nitems, st);

@@ -18,6 +18,9 @@ struct GraphDev {
     int32_t* offT = nullptr;   // [n+1] H^T offsets
     int32_t* idxT = nullptr;   // [nnz] adj(v) ascending
     int32_t* tpos = nullptr;   // [nnz] position of incidence e inside H^T
+    int32_t nhubs = 0;
+    int32_t* hubidx = nullptr;     // [n]  hub number of vertex v, -1 if none
+    uint32_t* hubmask = nullptr;   // [m]  bit b set when hub b is in e_i
 };
 
 // Everything derived for one s. Items and offsets are valid once built;
@@ -32,12 +35,13 @@ struct Plan {
     int64_t* W = nullptr;       // [m] wedges of row i
     int32_t* jmin = nullptr;    // [m] first / last candidate partner of row i
     int32_t* jmax = nullptr;
+    int32_t* nnh = nullptr;     // [m] non-hub incidences of row i with a non-empty wedge range
     int32_t* row_item = nullptr;  // [m+1] first item of row i
     int64_t nitems = 0;
     Item* items = nullptr;
-    int32_t* mode_rank[NMODES] = {nullptr, nullptr, nullptr};  // [nitems+1]
-    int32_t* mode_list[NMODES] = {nullptr, nullptr, nullptr};  // item ids per mode, ascending
-    int64_t mode_count[NMODES] = {0, 0, 0};
+    int32_t* mode_rank[NMODES] = {};  // [nitems+1]
+    int32_t* mode_list[NMODES] = {};  // item ids per mode, ascending
+    int64_t mode_count[NMODES] = {};
     int32_t* icnt = nullptr;    // [nitems] pairs per item
     int64_t* ioff = nullptr;    // [nitems+1] output offset per item
     int64_t* rowoff = nullptr;  // [m+1] output offset per row

@@ -58,8 +58,9 @@ void count_launch();
 enum ItemMode : int32_t {
     MODE_WARP = 0,   // whole row, few wedges: one warp, small hash table
     MODE_BLOCK = 1,  // sparse slice: one CTA, shared-memory hash table
-    MODE_DENSE = 2,  // dense slice: one CTA, direct j-tiled counters
-    NMODES = 3
+    MODE_DENSE = 2,  // dense slice, many non-hub ranges: one CTA, j tiles of 32768
+    MODE_WDENSE = 3, // dense slice, <= 32 non-hub ranges: one warp, j tiles of 2048
+    NMODES = 4
 };
 
 struct Item {
@@ -83,7 +84,9 @@ struct BinParams {
     int32_t warp_max_wedges;   // rows with W_i <= this go to MODE_WARP
     int32_t block_item_wedges; // target wedges per MODE_BLOCK item
     int32_t dense_min_density; // dense when 256*W_i >= density*span (density/256)
-    int32_t dense_item_tiles;  // tiles per MODE_DENSE item
+    int32_t dense_item_tiles;  // tiles per MODE_DENSE item (x4096 ids per MODE_WDENSE item)
+    int32_t wdense_max_ranges; // rows with at most this many non-hub wedge ranges (<= 32)
+                               // use the warp-level dense handler; 0 disables it
 };
 
 // ---------------------------------------------------------- kernel sizes
@@ -95,7 +98,12 @@ constexpr int BLOCK_TABLE = 4096;         // slots per CTA table (MODE_BLOCK)
 constexpr int BLOCK_CAP = BLOCK_TABLE / 2;// distinct keys before a slice splits
 constexpr int DENSE_THREADS = 512;        // MODE_DENSE CTA
 constexpr int DENSE_TILE = 32768;         // j per tile (16-bit counters)
-constexpr int DENSE_MAXE = 2048;          // incidences a dense row may have
+constexpr int DENSE_MAXE = 1024;          // incidences a dense row may have
+constexpr int MAX_HUBS = 32;              // vertices summarised by per-row bit masks
+constexpr int WD_WARPS = 16;              // warps per CTA in MODE_WDENSE
+constexpr int WD_TILE = 4096;             // j per warp tile (8-bit counters, 4 KB)
+constexpr int WD_ITEM = 8192;             // j per MODE_WDENSE item = WD_ITEM * dense_item_tiles
+constexpr int WD_MAXR = 32;               // non-hub wedge ranges a MODE_WDENSE row may have
 constexpr int DENSE_MAX_SIZE = 65535;     // |e_i| bound for 16-bit counters
 
 // --------------------------------------------------------- device helpers
@@ -128,5 +136,9 @@ void launch_validate(const int32_t* off, const int32_t* idx, int32_t m, int32_t 
                      int32_t* rowid, int32_t* size, int32_t* flag, cudaStream_t st);
 void build_transpose(const int32_t* idx, const int32_t* rowid, int32_t n, int64_t nnz,
                      int32_t* offT, int32_t* idxT, int32_t* tpos, cudaStream_t st);
+// Hub vertices (at most MAX_HUBS, highest degree first) and per-row masks.
+// Returns the number of hubs.
+int32_t build_hubs(const int32_t* off, const int32_t* idx, const int32_t* offT, int32_t m,
+                   int32_t n, int32_t* hubidx, uint32_t* hubmask, cudaStream_t st);
 
 }  // namespace slg

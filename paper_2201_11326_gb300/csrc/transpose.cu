@@ -181,6 +181,88 @@ __global__ void k_finish_transpose(const int32_t* __restrict__ sorted_e,
     }
 }
 
+// ------------------------------------------------------------------ hubs
+//
+// The highest-degree vertices ("hubs", at most MAX_HUBS) are summarised by a
+// 32-bit mask per hyperedge, so that the dense handler gets their share of an
+// overlap as one popcount. Which vertices are hubs never changes a result;
+// the pick below is deterministic (degree descending, then id).
+
+constexpr int HUB_CAND = 4096;
+
+__global__ void k_deg_buckets(const int32_t* __restrict__ offT, int32_t n,
+                              int32_t* __restrict__ hist) {
+    __shared__ int32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = offT[v + 1] - offT[v];
+        if (d >= 2) atomicAdd(&h[31 - __clz(d)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_hub_candidates(const int32_t* __restrict__ offT, int32_t n, int32_t dmin,
+                                 unsigned long long* __restrict__ cand,
+                                 int32_t* __restrict__ ncand) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = offT[v + 1] - offT[v];
+        if (d >= dmin && d >= 2) {
+            const int32_t slot = atomicAdd(ncand, 1);
+            if (slot < HUB_CAND)
+                cand[slot] = ((unsigned long long)(uint32_t)(INT32_MAX - d) << 32) | (uint32_t)v;
+        }
+    }
+}
+
+// One CTA: sort the candidates by (degree desc, id asc), number the first
+// MAX_HUBS of them.
+__global__ void __launch_bounds__(1024)
+k_hub_pick(const unsigned long long* __restrict__ cand, const int32_t* __restrict__ ncand,
+           int32_t* __restrict__ hubidx, int32_t* __restrict__ nhubs) {
+    __shared__ unsigned long long buf[HUB_CAND];
+    const int32_t c = min(*ncand, HUB_CAND);
+    int32_t P = 1;
+    while (P < c) P <<= 1;
+    for (int32_t t = threadIdx.x; t < P; t += blockDim.x) buf[t] = t < c ? cand[t] : ~0ull;
+    __syncthreads();
+    for (int32_t k = 2; k <= P; k <<= 1) {
+        for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int32_t t = threadIdx.x; t < P; t += blockDim.x) {
+                const int32_t u = t ^ jj;
+                if (u > t) {
+                    const unsigned long long x = buf[t], y = buf[u];
+                    if ((x > y) == ((t & k) == 0)) {
+                        buf[t] = y;
+                        buf[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int32_t h = min(c, MAX_HUBS);
+    if (threadIdx.x < h) hubidx[(int32_t)(buf[threadIdx.x] & 0xffffffffu)] = threadIdx.x;
+    if (threadIdx.x == 0) *nhubs = h;
+}
+
+__global__ void k_hub_masks(const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                            const int32_t* __restrict__ hubidx, int32_t m,
+                            uint32_t* __restrict__ hubmask) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t mask = 0;
+        for (int32_t e = off[i]; e < off[i + 1]; ++e) {
+            const int32_t b = hubidx[idx[e]];
+            if (b >= 0) mask |= 1u << b;
+        }
+        hubmask[i] = mask;
+    }
+}
+
 int grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -254,6 +336,48 @@ void build_transpose(const int32_t* idx, const int32_t* rowid, int32_t n, int64_
     SLG_CUDA_TRY(cudaFreeAsync(k1, st));
     SLG_CUDA_TRY(cudaFreeAsync(v1, st));
     SLG_CUDA_TRY(cudaFreeAsync(hist, st));
+}
+
+int32_t build_hubs(const int32_t* off, const int32_t* idx, const int32_t* offT, int32_t m,
+                   int32_t n, int32_t* hubidx, uint32_t* hubmask, cudaStream_t st) {
+    SLG_CUDA_TRY(cudaMemsetAsync(hubidx, 0xff, sizeof(int32_t) * ((size_t)n + 1), st));
+    int32_t* work = nullptr;  // [0..31] degree buckets, [32] candidates, [33] hubs
+    unsigned long long* cand = nullptr;
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(int32_t) * 34, st));
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&cand, sizeof(unsigned long long) * HUB_CAND, st));
+    SLG_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int32_t) * 34, st));
+    int32_t nh = 0;
+    if (n > 0) {
+        k_deg_buckets<<<grid_for(n, 256), 256, 0, st>>>(offT, n, work);
+        SLG_LAUNCH_CHECK();
+        int32_t hist[32];
+        SLG_CUDA_TRY(cudaMemcpyAsync(hist, work, sizeof(hist), cudaMemcpyDeviceToHost, st));
+        SLG_CUDA_TRY(cudaStreamSynchronize(st));
+        // smallest power-of-two degree bound keeping at most HUB_CAND candidates
+        int b = 31;
+        int64_t cum = hist[31];
+        while (b > 1 && cum + hist[b - 1] <= HUB_CAND) {
+            --b;
+            cum += hist[b];
+        }
+        if (cum > 0) {
+            const int32_t dmin = b >= 31 ? INT32_MAX : (int32_t)(1u << b);
+            k_hub_candidates<<<grid_for(n, 256), 256, 0, st>>>(offT, n, dmin, cand, work + 32);
+            SLG_LAUNCH_CHECK();
+            k_hub_pick<<<1, 1024, 0, st>>>(cand, work + 32, hubidx, work + 33);
+            SLG_LAUNCH_CHECK();
+            SLG_CUDA_TRY(cudaMemcpyAsync(&nh, work + 33, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                         st));
+        }
+    }
+    if (m > 0) {
+        k_hub_masks<<<grid_for(m, 256), 256, 0, st>>>(off, idx, hubidx, m, hubmask);
+        SLG_LAUNCH_CHECK();
+    }
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    SLG_CUDA_TRY(cudaFreeAsync(work, st));
+    SLG_CUDA_TRY(cudaFreeAsync(cand, st));
+    return nh;
 }
 
 }  // namespace slg

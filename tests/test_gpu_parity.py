@@ -18,12 +18,14 @@ pytestmark = pytest.mark.gpu
 
 # bin settings that force one handler onto every row (results must not change)
 FORCED = {
-    "default": (128, 1024, 64, 4),
-    "block_only": (0, 1024, -1, 4),
-    "block_one_item_per_row": (0, 1 << 30, -1, 4),  # big items: exercises the split path
-    "block_tiny_items": (0, 1, -1, 4),
-    "dense_only": (0, 1024, 0, 1),
-    "warp_and_block": (128, 256, -1, 4),
+    "default": (128, 1024, 64, 16, 32),
+    "block_only": (0, 1024, -1, 4, 32),
+    "block_one_item_per_row": (0, 1 << 30, -1, 4, 32),  # big items: exercises the split path
+    "block_tiny_items": (0, 1, -1, 4, 32),
+    "dense_only": (0, 1024, 0, 1, 32),           # warp-level dense where possible
+    "dense_cta_only": (0, 1024, 0, 1, 0),        # CTA-level dense for every dense row
+    "dense_warp_few_ranges": (0, 1024, 0, 3, 2),  # warp dense only for rows with <= 2 ranges
+    "warp_and_block": (128, 256, -1, 4, 32),
 }
 
 
@@ -155,6 +157,25 @@ def test_edge_cases():
         h = synth.Hypergraph(off, idx, n)
         for s in (1, 2, 3, 200):
             assert_same(gpu_list(h, s), oracle.slg(off, idx, s), f"{name} s={s}")
+
+
+def test_hub_masks_many_hubs():
+    # more than 32 high-degree vertices, rows holding every hub, hub-only rows
+    rng = np.random.default_rng(21)
+    n = 400
+    rows = []
+    for i in range(3000):
+        k = int(rng.integers(1, 12))
+        r = set(rng.choice(60, size=min(k, 60), replace=False).tolist())  # 60 popular vertices
+        r |= set(rng.choice(np.arange(60, n), size=int(rng.integers(0, 4)), replace=False).tolist())
+        rows.append(sorted(r))
+    rows += [list(range(64))] * 3 + [list(range(0, 64, 2))]
+    off, idx = csr_from_rows(rows)
+    h = synth.Hypergraph(off, idx, n)
+    for s in (1, 2, 5, 9):
+        want = oracle.slg(off, idx, s)
+        for mode in ("default", "dense_only", "dense_cta_only", "block_only"):
+            assert_same(gpu_list(h, s, FORCED[mode]), want, f"{mode} s={s}")
 
 
 def test_invalid_input_rejected():
