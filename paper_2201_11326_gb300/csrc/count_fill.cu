@@ -556,35 +556,43 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 
 // ========================================================== MODE_WDENSE
 //
-// The dense handler at warp granularity, for rows with at most 32 non-hub
-// wedge ranges (almost every dense row): one warp owns a slice, a 4096-wide j
-// tile of 8-bit counters (4 KB of shared memory; a row has at most 32 non-hub
-// ranges, so a non-hub count is at most 32) and one non-hub cursor per lane,
-// so no CTA barrier is ever needed. Counter of partner t0 + c: byte c % 4 of
-// word c / 4, so a lane's four consecutive partners share one word. Tiles
-// start at multiples of 32 ids. Per tile:
+// The dense handler at warp granularity, for rows with at most 64 non-hub
+// wedge ranges (almost every dense row): one warp owns a slice, a j tile of
+// 8-bit counters (4096 ids when counting, 2048 when filling, so that the fill
+// keeps three CTAs per SM) and two non-hub cursors per lane, so no CTA
+// barrier is ever needed. A non-hub count is at most 64 and a hub count at
+// most 32, so every overlap fits a byte below 128. Counter of partner t0 + c:
+// byte c % 4 of word c / 4, so a lane's four consecutive partners share one
+// word. Tiles start at multiples of 32 ids. Per tile:
 //   1. clear the counters;
 //   2. add the non-hub wedges: ranges with a partner inside the tile take
 //      part in rounds; a round loads the next 32 entries of up to four ranges
 //      at once, then counts the ones below the tile end;
-//   3. extraction. Counting pass: four consecutive partners per lane, hub
-//      masks by 16-byte loads, overlaps summed and compared four at a time
-//      inside one 32-bit word (each byte stays below 128, so no carry crosses
-//      bytes). Fill pass: one partner per lane so that the survivors are
-//      written with coalesced stores in ascending j, eight blocks of loads in
-//      flight.
+//   3. extraction, four consecutive partners per lane: hub masks by 16-byte
+//      loads, overlaps summed and compared four at a time inside one 32-bit
+//      word (each byte stays below 128, so no carry crosses bytes). The
+//      counting pass adds up the survivors. The fill pass appends them in j
+//      order to a per-warp ring in shared memory and stores them in chunks of
+//      32 that start on 128-byte boundaries of I (only the first chunk of a
+//      slice is shorter), so every store is a full, aligned line.
 
-constexpr int WD_WORDS = WD_TILE / 4;                  // counter words per warp
-constexpr size_t WD_WARP_SMEM_WORDS = WD_WORDS + 2 * 32;  // + staging of 32 ranges
-constexpr size_t WD_SMEM = sizeof(uint32_t) * WD_WARP_SMEM_WORDS * WD_WARPS;
-constexpr int WD_CBLK = 4;    // counting: 128-partner blocks whose loads are issued together
-constexpr int WD_FBLK = 8;    // fill: 32-partner blocks whose loads are issued together
+constexpr int WD_TILE_FILL = 4096;
+constexpr int WD_SLOTS = WD_MAXR / 32;  // non-hub cursors per lane
+constexpr int WD_RING = 256;  // fill: survivors waiting for an aligned store
+constexpr int WD_CBLK = 4;    // 128-partner blocks whose loads are issued together
 constexpr int WD_GROUP = 4;   // non-hub ranges loaded together per round
-static_assert(WD_TILE % (128 * WD_CBLK) == 0 && WD_TILE % (32 * WD_FBLK) == 0, "tile blocks");
+constexpr size_t WD_STAGE_WORDS = 2 * WD_MAXR;  // cursor and end of each range
+constexpr size_t wd_warp_words(bool fill) {
+    return (fill ? WD_TILE_FILL / 4 + 2 * WD_RING : WD_TILE / 4) + WD_STAGE_WORDS;
+}
+constexpr size_t WD_SMEM = sizeof(uint32_t) * wd_warp_words(false) * WD_WARPS;
+constexpr size_t WD_SMEM_FILL = sizeof(uint32_t) * wd_warp_words(true) * WD_WARPS;
+static_assert(WD_TILE % (128 * WD_CBLK) == 0 && WD_TILE_FILL % (128 * WD_CBLK) == 0, "tiles");
 static_assert(MAX_HUBS + WD_MAXR < 128, "byte-wise overlap sums must stay below 128");
+static_assert(WD_MAXR % 32 == 0 && WD_SLOTS >= 1 && WD_SLOTS <= 2, "cursors per lane");
 
 template <bool FILL>
-__global__ void __launch_bounds__(WD_WARPS * 32, 3)
+__global__ void __launch_bounds__(WD_WARPS * 32, FILL ? 2 : 3)
 k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
                const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
@@ -594,11 +602,13 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
                int32_t* __restrict__ J, int32_t* __restrict__ O, int32_t* __restrict__ queue,
                int64_t limit, int32_t* __restrict__ err) {
+    constexpr int TILE = FILL ? WD_TILE_FILL : WD_TILE;
+    constexpr int WORDS = TILE / 4;
     extern __shared__ __align__(16) uint32_t dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* ctr = dyn + (size_t)warp * WD_WARP_SMEM_WORDS;
-    const uint8_t* ctr8 = reinterpret_cast<const uint8_t*>(ctr);
-    int32_t* stage = reinterpret_cast<int32_t*>(ctr + WD_WORDS);  // [0..31] cursor, [32..63] end
+    uint32_t* ctr = dyn + (size_t)warp * wd_warp_words(FILL);
+    int32_t* stage = reinterpret_cast<int32_t*>(ctr + WORDS);  // [0..63] cursor, [64..127] end
+    int2* ring = reinterpret_cast<int2*>(stage + WD_STAGE_WORDS);  // fill only
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
     // byte-wise threshold: x >= s  <=>  bit 7 of x + (128 - s), for x < 128
@@ -635,26 +645,35 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             if (ok) {
                 if (slot < WD_MAXR) {
                     stage[slot] = c;
-                    stage[32 + slot] = t;
+                    stage[WD_MAXR + slot] = t;
                 } else {
-                    atomicOr(err, ERR_TABLE);  // binning guarantees <= 32 ranges
+                    atomicOr(err, ERR_TABLE);  // binning guarantees <= 64 ranges
                 }
             }
             nr += __popc(bal);
         }
         nr = min(nr, WD_MAXR);
         __syncwarp();
-        int32_t my_cur = lane < nr ? stage[lane] : 0;
-        const int32_t my_end = lane < nr ? stage[32 + lane] : 0;
-        // partner at the cursor (INT32_MAX once the range is used up)
-        int32_t my_next = (lane < nr && my_cur < my_end) ? __ldg(&idxTs[my_cur]) : INT32_MAX;
+        // ranges lane, 32 + lane, ... (one per slot)
+        int32_t cur[WD_SLOTS], end[WD_SLOTS], nxt[WD_SLOTS];
+#pragma unroll
+        for (int u = 0; u < WD_SLOTS; ++u) {
+            const int32_t k = u * 32 + lane;
+            cur[u] = k < nr ? stage[k] : 0;
+            end[u] = k < nr ? stage[WD_MAXR + k] : 0;
+            // partner at the cursor (INT32_MAX once the range is used up)
+            nxt[u] = (k < nr && cur[u] < end[u]) ? __ldg(&idxTs[cur[u]]) : INT32_MAX;
+        }
         __syncwarp();
 
-        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
-        int64_t out_pos = 0;
+        // fill: survivors collect in the ring and leave it in chunks that end
+        // on 128-byte boundaries of I (the first chunk is shorter)
+        int64_t wpos = FILL ? ioff[q] - ioff[item_lo] : 0;  // next output position
+        int32_t rhead = 0, rcount = 0;
+        int32_t need = FILL ? 32 - (int32_t)((reinterpret_cast<uintptr_t>(I + wpos) >> 2) & 31) : 32;
         int32_t my_count = 0;
-        for (int32_t t0 = it.jlo & ~31; t0 < it.jhi; t0 += WD_TILE) {
-            const int32_t t1 = min(t0 + WD_TILE, it.jhi);  // partners j in [max(t0, jlo), t1)
+        for (int32_t t0 = it.jlo & ~31; t0 < it.jhi; t0 += TILE) {
+            const int32_t t1 = min(t0 + TILE, it.jhi);  // partners j in [max(t0, jlo), t1)
             const int32_t jfirst = max(t0, it.jlo);
             const int32_t span = t1 - t0;
             // 1. clear (only the words this tile uses)
@@ -663,17 +682,40 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 *reinterpret_cast<uint4*>(ctr + w) = make_uint4(0, 0, 0, 0);
             __syncwarp();
             // 2. non-hub wedges
-            unsigned active = __ballot_sync(0xffffffffu, my_next < t1);
-            while (active) {
+            unsigned act[WD_SLOTS];
+#pragma unroll
+            for (int u = 0; u < WD_SLOTS; ++u) act[u] = __ballot_sync(0xffffffffu, nxt[u] < t1);
+            auto any_active = [&]() {
+                unsigned x = 0;
+#pragma unroll
+                for (int u = 0; u < WD_SLOTS; ++u) x |= act[u];
+                return x != 0;
+            };
+            while (any_active()) {
                 int32_t kk[WD_GROUP], vv[WD_GROUP];
-                unsigned a = active;
+                unsigned aa[WD_SLOTS];
+#pragma unroll
+                for (int u = 0; u < WD_SLOTS; ++u) aa[u] = act[u];
 #pragma unroll
                 for (int g = 0; g < WD_GROUP; ++g) {
-                    const int32_t k = a ? __ffs(a) - 1 : -1;
-                    a &= a - 1u;
+                    int32_t k = -1;
+#pragma unroll
+                    for (int u = 0; u < WD_SLOTS; ++u) {
+                        if (k < 0 && aa[u]) {
+                            k = 32 * u + __ffs(aa[u]) - 1;
+                            aa[u] &= aa[u] - 1u;
+                        }
+                    }
                     kk[g] = k;
-                    const int32_t c = __shfl_sync(0xffffffffu, my_cur, k & 31);
-                    const int32_t e = __shfl_sync(0xffffffffu, my_end, k & 31);
+                    int32_t cs = cur[0], es = end[0];
+#pragma unroll
+                    for (int u = 1; u < WD_SLOTS; ++u)
+                        if ((k >> 5) == u) {
+                            cs = cur[u];
+                            es = end[u];
+                        }
+                    const int32_t c = __shfl_sync(0xffffffffu, cs, k & 31);
+                    const int32_t e = __shfl_sync(0xffffffffu, es, k & 31);
                     const int32_t p = c + lane;
                     vv[g] = (k >= 0 && p < e) ? __ldg(&idxTs[p]) : INT32_MAX;
                 }
@@ -688,76 +730,106 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     }
                     const int n = __popc(__ballot_sync(0xffffffffu, valid));
                     // the first entry not taken is the range's next partner
-                    const int32_t nxt = __shfl_sync(0xffffffffu, vv[g], n & 31);
-                    if (lane == k) {
-                        my_cur += n;
-                        if (n < 32) my_next = nxt;
+                    const int32_t nx = __shfl_sync(0xffffffffu, vv[g], n & 31);
+                    const int uk = k >> 5;
+#pragma unroll
+                    for (int u = 0; u < WD_SLOTS; ++u) {
+                        if (u != uk) continue;
+                        if (lane == (k & 31)) {
+                            cur[u] += n;
+                            if (n < 32) nxt[u] = nx;
+                        }
+                        if (n < 32) act[u] &= ~(1u << (k & 31));
                     }
-                    if (n < 32) active &= ~(1u << k);
                 }
             }
             __syncwarp();
-            // 3. extraction
-            if (!FILL) {
-                for (int32_t g = 0; g < span; g += 128 * WD_CBLK) {
-                    uint4 hv[WD_CBLK];
-                    uint32_t cw[WD_CBLK];
+            // 3. extraction: four consecutive partners per lane
+            for (int32_t g = 0; g < span; g += 128 * WD_CBLK) {
+                uint4 hv[WD_CBLK];
+                uint32_t cw[WD_CBLK];
 #pragma unroll
-                    for (int b = 0; b < WD_CBLK; ++b) {
-                        const int32_t ci = g + b * 128 + 4 * lane;
-                        if (ci < span) {
-                            hv[b] = __ldg(reinterpret_cast<const uint4*>(hubmask + t0 + ci));
-                            cw[b] = ctr[ci >> 2];
-                        } else {
-                            hv[b] = make_uint4(0, 0, 0, 0);
-                            cw[b] = 0;
-                        }
-                    }
-#pragma unroll
-                    for (int b = 0; b < WD_CBLK; ++b) {
-                        const int32_t ci = g + b * 128 + 4 * lane;
-                        const uint32_t p4 = (uint32_t)__popc(hmi & hv[b].x) |
-                                            ((uint32_t)__popc(hmi & hv[b].y) << 8) |
-                                            ((uint32_t)__popc(hmi & hv[b].z) << 16) |
-                                            ((uint32_t)__popc(hmi & hv[b].w) << 24);
-                        uint32_t f4 = (p4 + cw[b] + bias4) & 0x80808080u;
-                        const int32_t j0 = t0 + ci;
-                        if (j0 < jfirst || j0 + 4 > t1) {  // partial block at a tile edge
-#pragma unroll
-                            for (int r = 0; r < 4; ++r)
-                                if (j0 + r < jfirst || j0 + r >= t1) f4 &= ~(0x80u << (8 * r));
-                        }
-                        my_count += __popc(f4);
+                for (int b = 0; b < WD_CBLK; ++b) {
+                    const int32_t ci = g + b * 128 + 4 * lane;
+                    if (ci < span) {
+                        hv[b] = __ldg(reinterpret_cast<const uint4*>(hubmask + t0 + ci));
+                        cw[b] = ctr[ci >> 2];
+                    } else {
+                        hv[b] = make_uint4(0, 0, 0, 0);
+                        cw[b] = 0;
                     }
                 }
-            } else {
-                for (int32_t g = 0; g < span; g += 32 * WD_FBLK) {
-                    uint32_t hm[WD_FBLK], cb[WD_FBLK];
 #pragma unroll
-                    for (int b = 0; b < WD_FBLK; ++b) {
-                        const int32_t ci = g + b * 32 + lane;
-                        hm[b] = ci < span ? __ldg(&hubmask[t0 + ci]) : 0u;
-                        cb[b] = ci < span ? ctr8[ci] : 0u;
+                for (int b = 0; b < WD_CBLK; ++b) {
+                    const int32_t ci = g + b * 128 + 4 * lane;
+                    const uint32_t p4 = (uint32_t)__popc(hmi & hv[b].x) |
+                                        ((uint32_t)__popc(hmi & hv[b].y) << 8) |
+                                        ((uint32_t)__popc(hmi & hv[b].z) << 16) |
+                                        ((uint32_t)__popc(hmi & hv[b].w) << 24);
+                    const uint32_t c4 = p4 + cw[b];  // four overlaps, one per byte
+                    uint32_t f4 = (c4 + bias4) & 0x80808080u;
+                    const int32_t j0 = t0 + ci;
+                    if (j0 < jfirst || j0 + 4 > t1) {  // partial block at a tile edge
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            if (j0 + r < jfirst || j0 + r >= t1) f4 &= ~(0x80u << (8 * r));
                     }
+                    if (!FILL) {
+                        my_count += __popc(f4);
+                        continue;
+                    }
+                    const int32_t mine = __popc(f4);
+                    int32_t inc = mine;
 #pragma unroll
-                    for (int b = 0; b < WD_FBLK; ++b) {
-                        const int32_t ci = g + b * 32 + lane;
-                        const int32_t j = t0 + ci;
-                        const int32_t c = __popc(hmi & hm[b]) + (int32_t)cb[b];
-                        const bool f = j >= jfirst && j < t1 && c >= s;
-                        const unsigned bal = __ballot_sync(0xffffffffu, f);
-                        if (f) {
-                            const int64_t p2 = obase + out_pos + __popc(bal & lt);
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (lane >= d) inc += y;
+                    }
+                    const int32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+                    if (tot == 0) continue;
+                    int32_t slot = rhead + rcount + inc - mine;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if ((f4 >> (8 * r + 7)) & 1u) {
+                            ring[slot & (WD_RING - 1)] =
+                                make_int2(j0 + r, (int32_t)((c4 >> (8 * r)) & 0xffu));
+                            ++slot;
+                        }
+                    }
+                    rcount += tot;
+                    __syncwarp();
+                    while (rcount >= need) {
+                        if (lane < need) {
+                            const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
+                            const int64_t p2 = wpos + lane;
                             if (p2 < limit) {
                                 I[p2] = i;
-                                J[p2] = j;
-                                O[p2] = c;
+                                J[p2] = e.x;
+                                O[p2] = e.y;
                             } else {
                                 atomicOr(err, ERR_BOUNDS);
                             }
                         }
-                        out_pos += __popc(bal);
+                        rhead = (rhead + need) & (WD_RING - 1);
+                        rcount -= need;
+                        wpos += need;
+                        need = 32;
                     }
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+        }
+        if (FILL && rcount > 0) {  // the slice's last, partial chunk
+            if (lane < rcount) {
+                const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
+                const int64_t p2 = wpos + lane;
+                if (p2 < limit) {
+                    I[p2] = i;
+                    J[p2] = e.x;
+                    O[p2] = e.y;
+                } else {
+                    atomicOr(err, ERR_BOUNDS);
                 }
             }
             __syncwarp();
@@ -814,7 +886,7 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 
 struct Occupancy {
     int sms = 0;
-    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, wdense_ctas = 0;
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, wdense_ctas = 0, wdense_fill_ctas = 0;
 };
 
 Occupancy& occupancy() {
@@ -834,11 +906,15 @@ Occupancy& occupancy() {
                                           (int)WD_SMEM));
         SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<true>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)WD_SMEM));
+                                          (int)WD_SMEM_FILL));
         int a = 0, b = 0, c = 0, d = 0;
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_wdense_items<true>,
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_wdense_items<false>,
                                                                    WD_WARPS * 32, WD_SMEM));
         o.wdense_ctas = o.sms * (d > 0 ? d : 1);
+        int d2 = 0;
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d2, k_wdense_items<true>,
+                                                                   WD_WARPS * 32, WD_SMEM_FILL));
+        o.wdense_fill_ctas = o.sms * (d2 > 0 ? d2 : 1);
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
                                                                    WARP_CTA_WARPS * 32, 0));
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_block_items<true>,
@@ -896,7 +972,8 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
     if (p.mode_count[MODE_WDENSE]) {
         ran[MODE_WDENSE] = true;
         tick(MODE_WDENSE, 0);
-        k_wdense_items<FILL><<<oc.wdense_ctas, WD_WARPS * 32, WD_SMEM, st>>>(
+        k_wdense_items<FILL><<<FILL ? oc.wdense_fill_ctas : oc.wdense_ctas, WD_WARPS * 32,
+                               FILL ? WD_SMEM_FILL : WD_SMEM, st>>>(
             p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi, g.off,
             g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O,
             queue + MODE_WDENSE, limit, err);
