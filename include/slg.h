@@ -190,6 +190,42 @@ slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms8, int64_t* la
  */
 slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out16);
 
+/*
+ * slg_batch_load -- many hypergraphs, each with its own s, as one handle.
+ *
+ * Rows are the independent units of Algorithm 2's parallel loop (Section
+ * III-C), and hyperedges of different members share no vertex, so the s-line
+ * graph of the members' disjoint union is the union of their s-line graphs,
+ * each member with its own threshold. The union is assembled on the device
+ * from the members' already-built incidence and dual; one plan, one counting
+ * pass and one fill per window then serve all members.
+ *
+ *   gs     : k loaded member graphs (they stay owned by the caller and must
+ *            outlive the call; the batch copies what it needs).
+ *   s      : k thresholds (host), each >= 1.
+ *   stream : cudaStream_t (as void*) for the batch's device work.
+ *   out    : receives the batch handle (release with slg_free).
+ *
+ * On a batch handle every call that takes s must be given s = 0 ("each
+ * member's own s"); any other value is SLG_EINVAL. Rows are numbered member by
+ * member (member b's rows start at row_base[b], see slg_batch_info), so the
+ * batch's canonical list is the members' lists one after another; inside it
+ * I and J hold member-local hyperedge ids, and digests hash member-local ids,
+ * so a member's slice is identical to what its own handle produces.
+ * Errors: SLG_EINVAL (k < 1, NULL member, s < 1, more than 2^31 rows,
+ * vertices or incidences in total), SLG_ENOMEM, SLG_ECUDA.
+ */
+slg_status slg_batch_load(slg_graph* const* gs, const int32_t* s, int32_t k, void* stream,
+                          slg_graph** out);
+
+/* Members of a batch: *k and row_base[0..k] (host), member b owning rows
+ * row_base[b] .. row_base[b+1]-1 of the batch. SLG_EINVAL if not a batch. */
+slg_status slg_batch_info(const slg_graph* b, int32_t* k, int32_t* row_base);
+
+/* pair_base[0..k] (host): member b's pairs occupy positions pair_base[b] ..
+ * pair_base[b+1]-1 of the batch's list. Runs the counting pass if needed. */
+slg_status slg_batch_pair_offsets(slg_graph* b, int64_t* pair_base);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t slg_kernel_launches(void);
 

@@ -21,7 +21,8 @@ __all__ = [
     "SlgError", "Graph", "slg_load", "slg_free", "slg_count", "slg_bound", "slg_build",
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
-    "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "library_path",
+    "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
+    "slg_batch_info", "slg_batch_pair_offsets", "library_path",
     "lib",
 ]
 
@@ -72,6 +73,9 @@ _SIGS = {
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
     "slg_kernel_launches": (_i64, []),
     "slg_scan_counts_noalloc": (_i32, [_vp, _vp, _i64, _vp]),
+    "slg_batch_load": (_i32, [ctypes.POINTER(_vp), _i32p, _i32, _vp, ctypes.POINTER(_vp)]),
+    "slg_batch_info": (_i32, [_vp, _i32p, _i32p]),
+    "slg_batch_pair_offsets": (_i32, [_vp, _i64p]),
 }
 
 
@@ -286,6 +290,36 @@ def slg_mode_stats(g: Graph, s: int):
 
 def slg_kernel_launches() -> int:
     return int(lib().slg_kernel_launches())
+
+
+def slg_batch_load(graphs, s_list, stream=None) -> Graph:
+    """One handle over many graphs, each with its own s (pass s=0 to its calls)."""
+    k = len(graphs)
+    arr = (_vp * k)(*[g.handle for g in graphs])
+    s_arr = np.ascontiguousarray(s_list, dtype=np.int32)
+    h = _vp()
+    _check(lib().slg_batch_load(arr, s_arr.ctypes.data_as(_i32p), k, _stream_handle(stream),
+                                ctypes.byref(h)))
+    mm, nn, nz = _i32(), _i32(), _i64()
+    _check(lib().slg_graph_info(h, ctypes.byref(mm), ctypes.byref(nn), ctypes.byref(nz)))
+    return Graph(h.value, mm.value, nn.value, nz.value)
+
+
+def slg_batch_info(g: Graph) -> np.ndarray:
+    """row_base[0..k] of a batch."""
+    k = _i32()
+    _check(lib().slg_batch_info(g.handle, ctypes.byref(k), None))
+    rb = np.zeros(k.value + 1, np.int32)
+    _check(lib().slg_batch_info(g.handle, ctypes.byref(k), rb.ctypes.data_as(_i32p)))
+    return rb
+
+
+def slg_batch_pair_offsets(g: Graph) -> np.ndarray:
+    """pair_base[0..k] of a batch."""
+    k = len(slg_batch_info(g)) - 1
+    out = np.zeros(k + 1, np.int64)
+    _check(lib().slg_batch_pair_offsets(g.handle, out.ctypes.data_as(_i64p)))
+    return out
 
 
 def slg_scan_counts_noalloc(counts, offsets, stream=None):

@@ -4,6 +4,7 @@
 // of transpose.cu, plan.cu, count_fill.cu and scan.cu. There is no CPU path.
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <vector>
 
@@ -110,6 +111,7 @@ struct slg_graph {
     slg::Timer timer;
     slg::ModeTimer mtimer;
     float ms[5] = {0, 0, 0, 0, 0};
+    std::vector<int32_t> batch_row_base;  // members' first rows (k+1) when this is a batch
 };
 
 using slg::Error;
@@ -143,13 +145,23 @@ void free_graph_dev(slg::GraphDev& g, cudaStream_t st) {
     slg::dfree(g.tpos, st);
     slg::dfree(g.hubidx, st);
     slg::dfree(g.hubmask, st);
+    slg::dfree(g.srow, st);
+    slg::dfree(g.rbase, st);
 }
 
 // Count pass for s (cached per handle): plan, count, offsets.
+void check_s(const slg_graph* h, int32_t s) {
+    if (h->g.srow) {
+        if (s != 0) throw Error{SLG_EINVAL, "a batch uses each graph's own s: pass s = 0"};
+    } else if (s < 1) {
+        throw Error{SLG_EINVAL, "s must be >= 1"};
+    }
+}
+
 void ensure_counted(slg_graph* h, int32_t s) {
-    if (s < 1) throw Error{SLG_EINVAL, "s must be >= 1"};
+    check_s(h, s);
     slg::Plan& p = h->plan;
-    if (p.s == s && p.counted) return;
+    if (p.built && p.s == s && p.counted) return;
     h->timer.mark(0, h->st);
     slg::plan_build(h->g, s, h->bp, p, h->st);
     h->timer.mark(1, h->st);
@@ -334,10 +346,11 @@ slg_status slg_count(slg_graph* h, int32_t s, int64_t* pairs, int64_t* wedges) {
 
 slg_status slg_bound(slg_graph* h, int32_t s, int64_t* pairs_ub) {
     if (!h || !pairs_ub) return fail(SLG_EINVAL, "NULL argument");
-    if (s < 1) return fail(SLG_EINVAL, "s must be >= 1");
     API_BEGIN
-    if (h->plan.s != s) slg::plan_build(h->g, s, h->bp, h->plan, h->st);
-    *pairs_ub = h->plan.wedges / s;
+    check_s(h, s);
+    if (!h->plan.built || h->plan.s != s) slg::plan_build(h->g, s, h->bp, h->plan, h->st);
+    // every s-incident pair accounts for at least s wedges (at least 1 in a batch)
+    *pairs_ub = h->plan.wedges / (s > 0 ? s : 1);
     API_END
 }
 
@@ -525,4 +538,114 @@ slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_ite
     API_END
 }
 
+slg_status slg_batch_load(slg_graph* const* gs, const int32_t* s, int32_t k, void* stream,
+                          slg_graph** out) {
+    if (!out) return fail(SLG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (k < 1 || !gs || !s) return fail(SLG_EINVAL, "need k >= 1 graphs and their s");
+    int64_t M = 0, N = 0, NNZ = 0;
+    int32_t min_size = INT32_MAX, max_size = 0;
+    std::vector<slg::BatchPart> parts((size_t)k);
+    for (int32_t b = 0; b < k; ++b) {
+        const slg_graph* m = gs[b];
+        if (!m) return fail(SLG_EINVAL, "NULL member graph");
+        if (m->g.srow) return fail(SLG_EINVAL, "a batch cannot contain a batch");
+        if (s[b] < 1) return fail(SLG_EINVAL, "every member's s must be >= 1");
+        slg::BatchPart& P = parts[(size_t)b];
+        P.off = m->g.off;
+        P.idx = m->g.idx;
+        P.size = m->g.size;
+        P.rowid = m->g.rowid;
+        P.offT = m->g.offT;
+        P.idxT = m->g.idxT;
+        P.tpos = m->g.tpos;
+        P.m = m->g.m;
+        P.n = m->g.n;
+        P.nnz = m->g.nnz;
+        P.row_base = (int32_t)M;
+        P.vert_base = (int32_t)N;
+        P.nnz_base = NNZ;
+        P.s = s[b];
+        M += m->g.m;
+        N += m->g.n;
+        NNZ += m->g.nnz;
+        if (M >= INT32_MAX || N >= INT32_MAX || NNZ >= INT32_MAX)
+            return fail(SLG_EINVAL, "the batch exceeds 2^31 rows, vertices or incidences");
+        if (m->g.min_size > 0) min_size = std::min(min_size, m->g.min_size);
+        max_size = std::max(max_size, m->g.max_size);
+    }
+    slg_graph* h = new slg_graph();
+    h->st = (cudaStream_t)stream;
+    try {
+        SLG_CUDA_TRY(cudaGetDevice(&h->device));
+        slg::GraphDev& g = h->g;
+        g.m = (int32_t)M;
+        g.n = (int32_t)N;
+        g.nnz = NNZ;
+        g.min_size = min_size == INT32_MAX ? 0 : min_size;
+        g.max_size = max_size;
+        g.off = slg::dalloc<int32_t>((size_t)M + 1, h->st);
+        g.idx = slg::dalloc<int32_t>((size_t)NNZ + 4, h->st);
+        g.size = slg::dalloc<int32_t>((size_t)M, h->st);
+        g.rowid = slg::dalloc<int32_t>((size_t)NNZ + 4, h->st);
+        g.offT = slg::dalloc<int32_t>((size_t)N + 1, h->st);
+        g.idxT = slg::dalloc<int32_t>((size_t)NNZ + 4, h->st);
+        g.tpos = slg::dalloc<int32_t>((size_t)NNZ + 4, h->st);
+        g.srow = slg::dalloc<int32_t>((size_t)M, h->st);
+        g.rbase = slg::dalloc<int32_t>((size_t)M, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(g.idxT + NNZ, 0, sizeof(int32_t) * 4, h->st));
+        slg::BatchPart* parts_dev = slg::dalloc<slg::BatchPart>((size_t)k, h->st);
+        SLG_CUDA_TRY(cudaMemcpyAsync(parts_dev, parts.data(), sizeof(slg::BatchPart) * k,
+                                     cudaMemcpyHostToDevice, h->st));
+        slg::launch_concat(parts_dev, k, (int32_t)M, (int32_t)N, NNZ, g, h->st);
+        g.hubidx = slg::dalloc<int32_t>((size_t)N + 1, h->st);
+        g.hubmask = slg::dalloc<uint32_t>((size_t)M + 64, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(g.hubmask, 0, sizeof(uint32_t) * ((size_t)M + 64), h->st));
+        g.nhubs = slg::build_hubs(g.off, g.idx, g.offT, g.m, g.n, g.hubidx, g.hubmask, h->st);
+        SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+        slg::dfree(parts_dev, h->st);
+        h->batch_row_base.resize((size_t)k + 1);
+        for (int32_t b = 0; b < k; ++b) h->batch_row_base[(size_t)b] = parts[(size_t)b].row_base;
+        h->batch_row_base[(size_t)k] = (int32_t)M;
+        h->timer.init();
+        slg::mtimer_init(h->mtimer);
+    } catch (const Error& e) {
+        free_graph_dev(h->g, h->st);
+        cudaStreamSynchronize(h->st);
+        delete h;
+        return fail(e.code, e.msg);
+    }
+    *out = h;
+    slg::g_last_error.clear();
+    return SLG_OK;
+}
+
+slg_status slg_batch_info(const slg_graph* h, int32_t* k, int32_t* row_base) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (h->batch_row_base.empty()) return fail(SLG_EINVAL, "not a batch");
+    const int32_t kk = (int32_t)h->batch_row_base.size() - 1;
+    if (k) *k = kk;
+    if (row_base) memcpy(row_base, h->batch_row_base.data(), sizeof(int32_t) * ((size_t)kk + 1));
+    return SLG_OK;
+}
+
+slg_status slg_batch_pair_offsets(slg_graph* h, int64_t* pair_base) {
+    if (!h || !pair_base) return fail(SLG_EINVAL, "NULL argument");
+    if (h->batch_row_base.empty()) return fail(SLG_EINVAL, "not a batch");
+    API_BEGIN
+    ensure_counted(h, 0);
+    const int32_t k = (int32_t)h->batch_row_base.size() - 1;
+    int32_t* rb = slg::dalloc<int32_t>((size_t)k + 1, h->st);
+    int64_t* po = slg::dalloc<int64_t>((size_t)k + 1, h->st);
+    SLG_CUDA_TRY(cudaMemcpyAsync(rb, h->batch_row_base.data(), sizeof(int32_t) * ((size_t)k + 1),
+                                 cudaMemcpyHostToDevice, h->st));
+    slg::launch_gather_offsets(h->plan.rowoff, rb, k, po, h->st);
+    copy_out(pair_base, po, sizeof(int64_t) * ((size_t)k + 1), h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    slg::dfree(rb, h->st);
+    slg::dfree(po, h->st);
+    API_END
+}
+
 }  // extern "C"
+

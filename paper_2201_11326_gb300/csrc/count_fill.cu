@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(WARP_CTA_WARPS * 32)
 k_warp_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
              const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
              const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
-             const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
+             const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
              int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
              int32_t* __restrict__ J, int32_t* __restrict__ O, int64_t limit,
              int32_t* __restrict__ err) {
@@ -145,6 +145,8 @@ k_warp_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t q = list[pos];
         const Item it = items[q];
         const int32_t i = it.row;
+        const int32_t s = rs.s_of(i);
+        const int32_t ib = rs.base_of(i);
         const int32_t e1 = off[i + 1];
         for (int32_t eb = off[i]; eb < e1; eb += 32) {
             const int32_t e = eb + lane;
@@ -203,8 +205,8 @@ k_warp_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 int32_t r = 0;
                 for (int32_t u = 0; u < count; ++u) r += (sj[w][u] < jj) ? 1 : 0;
                 if (obase + r < limit) {
-                    I[obase + r] = i;
-                    J[obase + r] = jj;
+                    I[obase + r] = i - ib;
+                    J[obase + r] = jj - ib;
                     O[obase + r] = so[w][t];
                 } else {
                     atomicOr(err, ERR_BOUNDS);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS)
 k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
               const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
-              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, int32_t s,
+              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
               int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
               int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
               int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
@@ -255,6 +257,8 @@ k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t q = list[pos];
         const Item it = items[q];
         const int32_t i = it.row;
+        const int32_t s = rs.s_of(i);
+        const int32_t ib = rs.base_of(i);
         const int32_t e0 = off[i], e1 = off[i + 1];
         const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
         int64_t out_pos = 0;  // same value in every thread
@@ -373,8 +377,8 @@ k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     const unsigned long long v = tab[t];
                     const int64_t p2 = obase + out_pos + t;
                     if (p2 < limit) {
-                        I[p2] = i;
-                        J[p2] = (int32_t)(v >> 32);
+                        I[p2] = i - ib;
+                        J[p2] = (int32_t)(v >> 32) - ib;
                         O[p2] = (int32_t)(v & 0xffffffffu);
                     } else {
                         atomicOr(err, ERR_BOUNDS);
@@ -425,7 +429,7 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
               const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
               const int32_t* __restrict__ hubidx, const uint32_t* __restrict__ hubmask,
               const int32_t* __restrict__ wbeg, const int32_t* __restrict__ wend,
-              const int32_t* __restrict__ idxTs, int32_t s, int32_t* __restrict__ icnt,
+              const int32_t* __restrict__ idxTs, RowS rs, int32_t* __restrict__ icnt,
               const int64_t* __restrict__ ioff, int32_t* __restrict__ I, int32_t* __restrict__ J,
               int32_t* __restrict__ O, int32_t* __restrict__ queue, int64_t limit,
               int32_t* __restrict__ err) {
@@ -452,6 +456,8 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t q = list[pos];
         const Item it = items[q];
         const int32_t i = it.row;
+        const int32_t s = rs.s_of(i);
+        const int32_t ib = rs.base_of(i);
         const uint32_t hmi = hubmask[i];
         const int32_t e0 = off[i];
         const int32_t ne = off[i + 1] - e0;
@@ -536,8 +542,8 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         const int32_t ci = seg0 + r * 32 + lane;
                         const int64_t p2 = base + __popc(bal & lt);
                         if (p2 < limit) {
-                            I[p2] = i;
-                            J[p2] = t0 + ci;
+                            I[p2] = i - ib;
+                            J[p2] = t0 + ci - ib;
                             O[p2] = dense_count(hmi, hubmask, ctr, t0, ci);
                         } else {
                             atomicOr(err, ERR_BOUNDS);
@@ -598,7 +604,7 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
                const int32_t* __restrict__ hubidx, const uint32_t* __restrict__ hubmask,
                const int32_t* __restrict__ wbeg, const int32_t* __restrict__ wend,
-               const int32_t* __restrict__ idxTs, int32_t s, int32_t* __restrict__ icnt,
+               const int32_t* __restrict__ idxTs, RowS rs, int32_t* __restrict__ icnt,
                const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
                int32_t* __restrict__ J, int32_t* __restrict__ O, int32_t* __restrict__ queue,
                int64_t limit, int32_t* __restrict__ err) {
@@ -611,8 +617,6 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     int2* ring = reinterpret_cast<int2*>(stage + WD_STAGE_WORDS);  // fill only
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
-    // byte-wise threshold: x >= s  <=>  bit 7 of x + (128 - s), for x < 128
-    const uint32_t bias4 = 0x01010101u * (uint32_t)(128 - min(s, 128));
 
     for (;;) {
         int32_t pos = 0;
@@ -622,6 +626,9 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t q = list[pos];
         const Item it = items[q];
         const int32_t i = it.row;
+        const int32_t ib = rs.base_of(i);
+        // byte-wise threshold: x >= s  <=>  bit 7 of x + (128 - s), for x < 128
+        const uint32_t bias4 = 0x01010101u * (uint32_t)(128 - min(rs.s_of(i), 128));
         const uint32_t hmi = hubmask[i];
         const int32_t e0 = off[i];
         const int32_t ne = off[i + 1] - e0;
@@ -803,8 +810,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                             const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
                             const int64_t p2 = wpos + lane;
                             if (p2 < limit) {
-                                I[p2] = i;
-                                J[p2] = e.x;
+                                I[p2] = i - ib;
+                                J[p2] = e.x - ib;
                                 O[p2] = e.y;
                             } else {
                                 atomicOr(err, ERR_BOUNDS);
@@ -825,8 +832,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
                 const int64_t p2 = wpos + lane;
                 if (p2 < limit) {
-                    I[p2] = i;
-                    J[p2] = e.x;
+                    I[p2] = i - ib;
+                    J[p2] = e.x - ib;
                     O[p2] = e.y;
                 } else {
                     atomicOr(err, ERR_BOUNDS);
@@ -844,9 +851,14 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 
 // =============================================================== digest
 
+// Digest of a window: the pair at window position p belongs to the row whose
+// output range holds base + p. For a single graph that row is I[p]; in a
+// batch I holds graph-local ids, so the row is found by binary search over the
+// window's row offsets, and the hash uses the local ids (so that each graph's
+// digests equal those of the graph computed alone).
 __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restrict__ J,
                          const int32_t* __restrict__ O, int64_t P, int64_t base,
-                         const int64_t* __restrict__ rowoff, int32_t r0, int32_t r1,
+                         const int64_t* __restrict__ rowoff, int32_t r0, int32_t r1, RowS rs,
                          unsigned long long* __restrict__ total,
                          unsigned long long* __restrict__ rows, int32_t* __restrict__ err) {
     const int lane = threadIdx.x & 31;
@@ -855,28 +867,42 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < P; b += stride) {
         const int64_t p = b + threadIdx.x;
         bool ok = p < P;
-        int32_t i = -1;
+        int32_t g = -1;  // global row
         unsigned long long h = 0;
         if (ok) {
-            i = I[p];
-            if (i < r0 || i >= r1) {
+            const int32_t li = I[p];
+            if (rs.rbase) {
+                int32_t a = r0, z = r1 - 1;  // last row with rowoff[row] <= base + p
+                while (a < z) {
+                    const int32_t mid = (a + z + 1) >> 1;
+                    if (rowoff[mid] <= base + p)
+                        a = mid;
+                    else
+                        z = mid - 1;
+                }
+                g = a;
+                if (li != g - rs.rbase[g]) g = -2;
+            } else {
+                g = li;
+            }
+            if (g < r0 || g >= r1) {
                 atomicOr(err, ERR_DIGEST);
                 ok = false;
-                i = -1;
+                g = -1;
             } else {
-                h = pair_digest(i, base + p - rowoff[i], J[p], O[p]);
+                h = pair_digest(li, base + p - rowoff[g], J[p], O[p]);
                 acc += h;
             }
         }
         if (rows) {
-            const unsigned peers = __match_any_sync(0xffffffffu, i);
+            const unsigned peers = __match_any_sync(0xffffffffu, g);
             unsigned long long sum = 0;
             // sum of h over the peers, by shuffling each peer's value to the leader
             for (unsigned m2 = peers; m2; m2 &= m2 - 1) {
                 const int src = __ffs(m2) - 1;
                 sum += __shfl_sync(peers, h, src);
             }
-            if (ok && lane == __ffs(peers) - 1) atomicAdd(&rows[i - r0], sum);
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&rows[g - r0], sum);
         }
     }
 #pragma unroll
@@ -946,7 +972,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_WARP, 0);
         k_warp_items<FILL><<<oc.warp_ctas, WARP_CTA_WARPS * 32, 0, st>>>(
             p.items, p.mode_list[MODE_WARP], p.mode_rank[MODE_WARP], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, limit, err);
+            p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_WARP, 1);
     }
@@ -955,7 +981,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_BLOCK, 0);
         k_block_items<FILL><<<oc.block_ctas, BLOCK_THREADS, 0, st>>>(
             p.items, p.mode_list[MODE_BLOCK], p.mode_rank[MODE_BLOCK], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O, queue + MODE_BLOCK, limit, err);
+            p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O, queue + MODE_BLOCK, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_BLOCK, 1);
     }
@@ -964,7 +990,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_DENSE, 0);
         k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
             p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O,
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O,
             queue + MODE_DENSE, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_DENSE, 1);
@@ -975,7 +1001,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         k_wdense_items<FILL><<<FILL ? oc.wdense_fill_ctas : oc.wdense_ctas, WD_WARPS * 32,
                                FILL ? WD_SMEM_FILL : WD_SMEM, st>>>(
             p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.s, icnt, p.ioff, I, J, O,
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O,
             queue + MODE_WDENSE, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_WDENSE, 1);
@@ -1040,8 +1066,8 @@ void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const 
     int64_t blocks = (P + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     SLG_CUDA_TRY(cudaStreamSynchronize(st));
-    k_digest<<<(int)blocks, 256, 0, st>>>(I, J, O, P, base, p.rowoff, r0, r1, total_dev, rows_dev,
-                                          sc + NMODES);
+    k_digest<<<(int)blocks, 256, 0, st>>>(I, J, O, P, base, p.rowoff, r0, r1, p.rs, total_dev,
+                                          rows_dev, sc + NMODES);
     SLG_LAUNCH_CHECK();
     check_scratch(sc, st, "digest");
 }

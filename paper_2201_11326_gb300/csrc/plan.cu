@@ -27,10 +27,13 @@ int grid_for(int64_t work, int threads) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < (n);       \
          k += (int64_t)gridDim.x * blockDim.x)
 
-// keep[k] = |e_{idxT[k]}| >= s, for every position k of H^T
+// keep[k] = |e_j| >= s_j for j = idxT[k], for every position k of H^T
 __global__ void k_keep_flags(const int32_t* __restrict__ idxT, const int32_t* __restrict__ size,
-                             int64_t nnz, int32_t s, int32_t* __restrict__ keep) {
-    GRID_STRIDE(k, nnz) keep[k] = size[idxT[k]] >= s ? 1 : 0;
+                             int64_t nnz, RowS rs, int32_t* __restrict__ keep) {
+    GRID_STRIDE(k, nnz) {
+        const int32_t j = idxT[k];
+        keep[k] = size[j] >= rs.s_of(j) ? 1 : 0;
+    }
 }
 
 // pruned transpose: idxTs[ks[k]] = idxT[k] for kept k (ks = exclusive scan of keep)
@@ -46,12 +49,12 @@ __global__ void k_compact(const int32_t* __restrict__ idxT, const int32_t* __res
 __global__ void k_wedge_ranges(const int32_t* __restrict__ idx, const int32_t* __restrict__ rowid,
                                const int32_t* __restrict__ size, const int32_t* __restrict__ tpos,
                                const int32_t* __restrict__ offT, const int32_t* __restrict__ ks,
-                               int64_t nnz, int32_t s, int32_t* __restrict__ wbeg,
+                               int64_t nnz, RowS rs, int32_t* __restrict__ wbeg,
                                int32_t* __restrict__ wend) {
     GRID_STRIDE(e, nnz) {
         const int32_t i = rowid[e];
         int32_t b = 0, t = 0;
-        if (size[i] >= s) {
+        if (size[i] >= rs.s_of(i)) {
             const int32_t v = idx[e];
             const int32_t p = tpos[e];
             b = (ks ? ks[p] : p) + 1;
@@ -274,6 +277,7 @@ void Plan::release(cudaStream_t st) {
     dfree(ioff, st);
     dfree(rowoff, st);
     s = 0;
+    built = false;
     nitems = 0;
     counted = false;
     pairs = wedges = 0;
@@ -282,12 +286,14 @@ void Plan::release(cudaStream_t st) {
 void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st) {
     p.release(st);
     p.s = s;
+    p.rs = RowS{g.srow, g.rbase, s};
+    p.built = true;
     const int64_t nnz = g.nnz;
     const int32_t m = g.m;
     const int T = 256;
 
     // pruned transpose
-    if (s <= g.min_size) {
+    if (!g.srow && s <= g.min_size) {
         p.idxTs = g.idxT;
         p.idxTs_owned = false;
         p.ks = nullptr;
@@ -295,7 +301,7 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
         int32_t* keep = dalloc<int32_t>(nnz, st);
         p.ks = dalloc<int32_t>(nnz + 1, st);
         if (nnz) {
-            k_keep_flags<<<grid_for(nnz, T), T, 0, st>>>(g.idxT, g.size, nnz, s, keep);
+            k_keep_flags<<<grid_for(nnz, T), T, 0, st>>>(g.idxT, g.size, nnz, p.rs, keep);
             SLG_LAUNCH_CHECK();
         }
         scan_i32_to_i32(keep, p.ks, nnz, st);
@@ -314,7 +320,7 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.wend = dalloc<int32_t>(nnz, st);
     if (nnz) {
         k_wedge_ranges<<<grid_for(nnz, T), T, 0, st>>>(g.idx, g.rowid, g.size, g.tpos, g.offT, p.ks,
-                                                       nnz, s, p.wbeg, p.wend);
+                                                       nnz, p.rs, p.wbeg, p.wend);
         SLG_LAUNCH_CHECK();
     }
     // per-row work

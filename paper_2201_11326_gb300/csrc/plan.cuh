@@ -18,15 +18,43 @@ struct GraphDev {
     int32_t* offT = nullptr;   // [n+1] H^T offsets
     int32_t* idxT = nullptr;   // [nnz] adj(v) ascending
     int32_t* tpos = nullptr;   // [nnz] position of incidence e inside H^T
+    int32_t* srow = nullptr;   // [m] per-row s of a batch (null for a single graph)
+    int32_t* rbase = nullptr;  // [m] first row of the row's graph in a batch
     int32_t nhubs = 0;
     int32_t* hubidx = nullptr;     // [n]  hub number of vertex v, -1 if none
     uint32_t* hubmask = nullptr;   // [m]  bit b set when hub b is in e_i
 };
 
+// Device descriptor of one member of a batch.
+struct BatchPart {
+    const int32_t* off;
+    const int32_t* idx;
+    const int32_t* size;
+    const int32_t* rowid;
+    const int32_t* offT;
+    const int32_t* idxT;
+    const int32_t* tpos;
+    int32_t m, n;
+    int64_t nnz;
+    int32_t row_base, vert_base;
+    int64_t nnz_base;
+    int32_t s;
+};
+
+// Writes the disjoint union of the members into `out` (arrays preallocated:
+// off[M+1], idx/rowid/idxT/tpos[NNZ], size/srow/rbase[M], offT[N+1]).
+void launch_concat(const BatchPart* parts_dev, int32_t k, int32_t M, int32_t N, int64_t NNZ,
+                   const GraphDev& out, cudaStream_t st);
+// out[b] = rowoff[row_base[b]] for b = 0..k
+void launch_gather_offsets(const int64_t* rowoff, const int32_t* row_base_dev, int32_t k,
+                           int64_t* out_dev, cudaStream_t st);
+
 // Everything derived for one s. Items and offsets are valid once built;
 // icnt/ioff/rowoff once `counted`.
 struct Plan {
-    int32_t s = 0;
+    int32_t s = 0;              // 0 for a batch (per-row s)
+    bool built = false;
+    RowS rs{};                  // thresholds and id bases used by the kernels
     int32_t* ks = nullptr;      // [nnz+1] kept-prefix over H^T positions (null when nothing is pruned)
     int32_t* idxTs = nullptr;   // pruned H^T (aliases idxT when nothing is pruned)
     bool idxTs_owned = false;

@@ -70,6 +70,18 @@ struct Item {
     int32_t mode;
 };
 
+// Threshold and output-id base of a row. A single graph has one s for all
+// rows and its ids start at 0; a batch (disjoint union of graphs, each with
+// its own s) has per-row values, and ids are written relative to the first
+// row of the row's own graph.
+struct RowS {
+    const int32_t* srow;   // per-row s, or null: every row uses s
+    const int32_t* rbase;  // first row of the row's graph, or null: 0
+    int32_t s;
+    __device__ __forceinline__ int32_t s_of(int32_t i) const { return srow ? srow[i] : s; }
+    __device__ __forceinline__ int32_t base_of(int32_t i) const { return rbase ? rbase[i] : 0; }
+};
+
 // Per-handler kernel timing (CUDA events on the graph's stream), for the
 // counting pass [0] and the fill pass [1].
 struct ModeTimer {

@@ -1,0 +1,92 @@
+"""Full-size parity on the medium workload, in the benchmark's launch configuration.
+
+The medium hypergraph (m = 1,000,000) is built through windows of at most 2^31
+pairs into reused device buffers, exactly as bench.py times it. Its s-line
+graphs hold up to 4.8e11 pairs, so the comparison with the oracle is per row:
+for 1,000 seeded random rows and the 100 rows with the most wedges, the
+library's per-row pair count and per-row digest (a position-sensitive hash of
+the row's list) must equal the oracle's. Globally, the row counts must add up
+to |L_s| and, at s = 1, the overlaps of all pairs must add up to
+sum_v C(deg v, 2), the closed form of the wedge count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2201_11326_gb300 as slg
+
+pytestmark = pytest.mark.gpu
+
+WINDOW = 1 << 31
+
+
+@pytest.fixture(scope="module")
+def medium():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    slg.build.build()
+    h = synth.cached("medium_m1000000_seed0", lambda: synth.medium(seed=0, m=1_000_000))
+    return torch, h
+
+
+def row_wedges(h, s):
+    """W_{s,i} from vertex degrees restricted to E_s (no overlaps involved)."""
+    m = h.m
+    sizes = np.diff(h.off).astype(np.int64)
+    row = np.repeat(np.arange(m, dtype=np.int64), sizes)
+    keep = sizes[row] >= s
+    v, r = h.idx[keep].astype(np.int64), row[keep]
+    order = np.lexsort((r, v))
+    vs, rs = v[order], r[order]
+    ends = np.searchsorted(vs, vs, side="right")
+    later = ends - 1 - np.arange(vs.size)  # entries after this one in adj_s(v)
+    w = np.zeros(m, np.int64)
+    np.add.at(w, rs, later)
+    return w
+
+
+@pytest.mark.parametrize("s", [1, 4, 8])
+def test_medium_full_size_sampled_rows(medium, s):
+    torch, h = medium
+    dev = torch.device("cuda")
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        pairs, wedges = slg.slg_count(g, s)
+        rowoff = slg.slg_row_offsets(g, s)
+        counts = np.diff(rowoff)
+        assert int(counts.sum()) == pairs
+        I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        digests = torch.zeros(h.m, dtype=torch.int64, device=dev)
+        osum = 0
+        splits = slg.slg_plan_windows(g, s, WINDOW)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            P, _ = slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW,
+                                        row_digests=digests[int(r0):int(r1)])
+            assert P == rowoff[r1] - rowoff[r0]
+            if s == 1:
+                osum += int(O[:P].sum(dtype=torch.int64).item())
+        dig = digests.cpu().numpy().view(np.uint64)
+    finally:
+        g.free()
+
+    # rows to check: 1000 seeded random rows + the 100 rows with the most wedges
+    rng = np.random.default_rng([7, s])
+    sample = rng.choice(h.m, size=1000, replace=False)
+    w = row_wedges(h, s)
+    heavy = np.argsort(-w, kind="stable")[:100]
+    rows = np.unique(np.concatenate([sample, heavy])).astype(np.int32)
+    ocount, odig, osum_rows = oracle.rows(h.off, h.idx, rows, [s])
+    assert np.array_equal(counts[rows], ocount[:, 0])
+    assert np.array_equal(dig[rows], odig[:, 0])
+    assert np.array_equal(osum_rows[:, 0], w[rows])  # oracle overlap sums = wedge counts
+
+    deg_s = np.bincount(h.idx[np.repeat(np.diff(h.off) >= s, np.diff(h.off))],
+                        minlength=h.n).astype(np.int64)
+    assert wedges == int((deg_s * (deg_s - 1) // 2).sum())
+    if s == 1:
+        # every wedge is one unit of some pair's overlap
+        assert osum == wedges

@@ -256,3 +256,54 @@ def test_repeated_calls_are_identical():
     b = slg.slg_build(g, 2)
     assert_same(a, b, "rebuild")
     g.free()
+
+
+# ------------------------------------------------------------------ batches
+
+
+def _batch_members():
+    hs = [synth.tiny(seed=3), synth.medium(seed=12, m=3000), synth.striped_hub(5, 9000, 700, 50),
+          synth.uniform_random(9, 200, 150, 0, 12)]
+    for b in range(12):
+        g, s = synth.batch_member(b)
+        if g.m <= 6000:
+            hs.append(g)
+    rng = np.random.default_rng(5)
+    s_list = [int(x) for x in rng.integers(1, 5, size=len(hs))]
+    return hs, s_list
+
+
+@pytest.mark.parametrize("mode", ["default", "block_only", "dense_only", "dense_cta_only"])
+def test_batch_members_equal_their_own_lists(mode):
+    hs, s_list = _batch_members()
+    gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    b = slg.slg_batch_load(gs, s_list)
+    try:
+        slg.slg_set_bins(b, *FORCED[mode])
+        rb = slg.slg_batch_info(b)
+        assert rb.tolist() == np.concatenate([[0], np.cumsum([h.m for h in hs])]).tolist()
+        pairs, wedges = slg.slg_count(b, 0)
+        pb = slg.slg_batch_pair_offsets(b)
+        I, J, O = slg.slg_build(b, 0)
+        assert pb[-1] == pairs == I.size
+        tot_w = 0
+        for k, (h, s) in enumerate(zip(hs, s_list)):
+            want = oracle.slg(h.off, h.idx, s)
+            sl = slice(int(pb[k]), int(pb[k + 1]))
+            assert_same((I[sl], J[sl], O[sl]), want, f"member {k} s={s}")
+            tot_w += slg.slg_count(gs[k], s)[1]
+        assert wedges == tot_w
+        # digests of the batch equal the members' own
+        rd = np.zeros(b.m, np.uint64)
+        cap = max(int(pb[-1]), 1)
+        Iw, Jw, Ow = (np.zeros(cap, np.int32) for _ in range(3))
+        slg.slg_build_window(b, 0, 0, b.m, Iw, Jw, Ow, cap, row_digests=rd)
+        for k, h in enumerate(hs):
+            _, dig, _ = oracle.rows(h.off, h.idx, None, [s_list[k]])
+            assert np.array_equal(rd[rb[k]:rb[k + 1]], dig[:, 0]), k
+        with pytest.raises(slg.SlgError):
+            slg.slg_count(b, 2)
+    finally:
+        b.free()
+        for g in gs:
+            g.free()
