@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--window", type=int, default=1 << 31, help="pairs per output window")
+    ap.add_argument("--workload", choices=["medium", "batch", "serve"], default="medium")
+    ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
     return ap.parse_args()
 
 
@@ -411,10 +413,107 @@ def bench_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ batched form
+
+BATCH_WORKLOAD = ("batched: {k} hypergraphs, m log-uniform in [100, 100000], n = m/2, sizes "
+                  "log-normal(1.8,1.0) clipped [2,5000], Zipf(1.7) popularity, each with s "
+                  "uniform in {{1,2,3,4}}")
+
+
+def bench_batch(args):
+    """One batch handle (disjoint union, per-graph s) against sequential calls.
+
+    Both arms start from the same graphs already loaded on the device (inputs
+    resident). Batched step: slg_batch_load + one counting pass + the fill of
+    every window of the concatenated list. Sequential step: for each graph its
+    own counting pass and window fills.
+    """
+    import torch
+    import paper_2201_11326_gb300 as slg
+    dev = torch.cuda.current_device()
+    k = args.graphs
+    t0 = time.perf_counter()
+    members = [synth.batch_member(b) for b in range(k)]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(dev)
+    graphs = [slg.slg_load(h.off, h.idx, h.m, h.n, stream=stream) for h, _ in members]
+    s_list = [s for _, s in members]
+    I = torch.empty(args.window, dtype=torch.int32, device=dev)
+    J = torch.empty_like(I)
+    O = torch.empty_like(I)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def batched():
+        b = slg.slg_batch_load(graphs, s_list, stream=stream)
+        pairs, wedges = slg.slg_count(b, 0)
+        for r0, r1 in zip(*(lambda sp: (sp[:-1], sp[1:]))(slg.slg_plan_windows(b, 0, args.window))):
+            slg.slg_build_window(b, 0, int(r0), int(r1), I, J, O, args.window)
+        b.free()
+        return pairs, wedges
+
+    def sequential():
+        P = W = 0
+        for g, s in zip(graphs, s_list):
+            pairs, wedges = slg.slg_count(g, s)
+            P += pairs
+            W += wedges
+            sp = slg.slg_plan_windows(g, s, args.window)
+            for r0, r1 in zip(sp[:-1], sp[1:]):
+                slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, args.window)
+        return P, W
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            flush.fill_(0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            l0 = slg.slg_kernel_launches()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+        return out, e0.elapsed_time(e1), slg.slg_kernel_launches() - l0
+
+    res = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        for _ in range(args.warmup):
+            timed(fn)
+        times, launches = [], 0
+        for _ in range(args.steps):
+            (P, W), ms, nl = timed(fn)
+            times.append(ms)
+            launches = nl
+        ms = statistics.mean(times)
+        res[name] = {"wedges_per_s": W / (ms / 1e3), "s_edges_per_s": P / (ms / 1e3),
+                     "ms_per_step": round(ms, 1), "gpu_launches": int(launches),
+                     "pairs": P, "wedges": W}
+    for g in graphs:
+        g.free()
+    out = {
+        "metric": "batched s-line wedges/s (per-graph s, one batch handle)",
+        "value": res["batched"]["wedges_per_s"], "unit": "wedges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(k=k), "graphs": k,
+                   "rows": int(sum(h.m for h, _ in members)),
+                   "nnz": int(sum(h.nnz for h, _ in members)), "window_pairs": args.window,
+                   "generation_s": round(gen_s, 1)},
+        "batched": res["batched"], "sequential": res["sequential"],
+        "speedup_vs_sequential": res["batched"]["wedges_per_s"] / res["sequential"]["wedges_per_s"],
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batch":
+        bench_batch(args)
+    elif args.workload == "serve":
+        bench_serve(args)
     else:
         bench_ours(args)
 

@@ -559,6 +559,8 @@ slg_status slg_batch_load(slg_graph* const* gs, const int32_t* s, int32_t k, voi
         P.offT = m->g.offT;
         P.idxT = m->g.idxT;
         P.tpos = m->g.tpos;
+        P.hubidx = m->g.hubidx;
+        P.hubmask = m->g.hubmask;
         P.m = m->g.m;
         P.n = m->g.n;
         P.nnz = m->g.nnz;
@@ -594,14 +596,14 @@ slg_status slg_batch_load(slg_graph* const* gs, const int32_t* s, int32_t k, voi
         g.srow = slg::dalloc<int32_t>((size_t)M, h->st);
         g.rbase = slg::dalloc<int32_t>((size_t)M, h->st);
         SLG_CUDA_TRY(cudaMemsetAsync(g.idxT + NNZ, 0, sizeof(int32_t) * 4, h->st));
+        g.hubidx = slg::dalloc<int32_t>((size_t)N + 1, h->st);
+        g.hubmask = slg::dalloc<uint32_t>((size_t)M + 64, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(g.hubmask, 0, sizeof(uint32_t) * ((size_t)M + 64), h->st));
         slg::BatchPart* parts_dev = slg::dalloc<slg::BatchPart>((size_t)k, h->st);
         SLG_CUDA_TRY(cudaMemcpyAsync(parts_dev, parts.data(), sizeof(slg::BatchPart) * k,
                                      cudaMemcpyHostToDevice, h->st));
         slg::launch_concat(parts_dev, k, (int32_t)M, (int32_t)N, NNZ, g, h->st);
-        g.hubidx = slg::dalloc<int32_t>((size_t)N + 1, h->st);
-        g.hubmask = slg::dalloc<uint32_t>((size_t)M + 64, h->st);
-        SLG_CUDA_TRY(cudaMemsetAsync(g.hubmask, 0, sizeof(uint32_t) * ((size_t)M + 64), h->st));
-        g.nhubs = slg::build_hubs(g.off, g.idx, g.offT, g.m, g.n, g.hubidx, g.hubmask, h->st);
+        g.nhubs = slg::MAX_HUBS;  // per member
         SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
         slg::dfree(parts_dev, h->st);
         h->batch_row_base.resize((size_t)k + 1);

@@ -5,8 +5,10 @@
 // of the union is the union of the members' s-line graphs, each member keeping
 // its own threshold. The union is assembled on the device from the members'
 // CSR and transposes (already built when they were loaded): row, vertex and
-// incidence ids are shifted by per-member bases. One plan, one counting pass,
-// one scan and one fill per window then serve every member at once.
+// incidence ids are shifted by per-member bases. Hub numbers stay per member:
+// rows of different members never pair, so every member keeps its own (up to
+// 32) hubs and masks. One plan, one counting pass, one scan and one fill per
+// window then serve every member at once.
 #include "plan.cuh"
 
 namespace slg {
@@ -23,6 +25,7 @@ __global__ void k_concat(const BatchPart* __restrict__ parts, int32_t M, int32_t
         out.size[r] = P.size[i];
         out.srow[r] = P.s;
         out.rbase[r] = P.row_base;
+        out.hubmask[r] = P.hubmask[i];
     }
     for (int64_t e = t0; e < P.nnz; e += stride) {
         const int64_t x = P.nnz_base + e;
@@ -31,8 +34,10 @@ __global__ void k_concat(const BatchPart* __restrict__ parts, int32_t M, int32_t
         out.idxT[x] = P.row_base + P.idxT[e];
         out.tpos[x] = (int32_t)(P.nnz_base + P.tpos[e]);
     }
-    for (int64_t v = t0; v < P.n; v += stride)
+    for (int64_t v = t0; v < P.n; v += stride) {
         out.offT[P.vert_base + v] = (int32_t)(P.nnz_base + P.offT[v]);
+        out.hubidx[P.vert_base + v] = P.hubidx[v];
+    }
     if (blockIdx.y == k - 1 && t0 == 0) {
         out.off[M] = (int32_t)NNZ;
         out.offT[N] = (int32_t)NNZ;

@@ -34,6 +34,8 @@ struct BatchPart {
     const int32_t* offT;
     const int32_t* idxT;
     const int32_t* tpos;
+    const int32_t* hubidx;
+    const uint32_t* hubmask;
     int32_t m, n;
     int64_t nnz;
     int32_t row_base, vert_base;
@@ -42,7 +44,8 @@ struct BatchPart {
 };
 
 // Writes the disjoint union of the members into `out` (arrays preallocated:
-// off[M+1], idx/rowid/idxT/tpos[NNZ], size/srow/rbase[M], offT[N+1]).
+// off[M+1], idx/rowid/idxT/tpos[NNZ], size/srow/rbase/hubmask[M], offT[N+1],
+// hubidx[N]).
 void launch_concat(const BatchPart* parts_dev, int32_t k, int32_t M, int32_t N, int64_t NNZ,
                    const GraphDev& out, cudaStream_t st);
 // out[b] = rowoff[row_base[b]] for b = 0..k

@@ -22,14 +22,21 @@ Recipe (every draw comes from numpy's PCG64 via ``default_rng``):
   permutation / target degrees from ``default_rng([*seed, 1])`` and the
   members of row chunk c (rows ``[c*2**18, (c+1)*2**18)``) from
   ``default_rng([*seed, 2, c])``, so a chunk can be drawn without the others.
+* the batched, served and large workloads draw members with the same rule in
+  C (``fastgen.c``: alias-method draws, rejection of repeats, threaded over
+  rows, row r on the SplitMix64 stream keyed by the seed and r); their sizes
+  and popularity still come from the numpy streams above.
 
 A hyperedge size is clamped to n so that every row can be filled.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import os
+import subprocess
 import tempfile
+import threading
 from typing import Sequence
 
 import numpy as np
@@ -159,8 +166,56 @@ def members(seed: Sequence[int], sizes: np.ndarray, weights: np.ndarray) -> np.n
     return np.concatenate(parts) if parts else np.zeros(0, np.int64)
 
 
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_FG_SRC = os.path.join(_HERE, "fastgen.c")
+_FG_LIB = os.path.join(_HERE, "_build", "libfastgen.so")
+_fg_lock = threading.Lock()
+_fg = None
+
+
+def build_fastgen(force: bool = False) -> str:
+    """Compile the C member draw (plain gcc -O2)."""
+    os.makedirs(os.path.dirname(_FG_LIB), exist_ok=True)
+    if force or not os.path.exists(_FG_LIB) or (
+            os.path.getmtime(_FG_LIB) < os.path.getmtime(_FG_SRC)):
+        tmp = _FG_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o",
+                               tmp, _FG_SRC, "-lm"])
+        os.replace(tmp, _FG_LIB)
+    return _FG_LIB
+
+
+def _fastgen():
+    global _fg
+    with _fg_lock:
+        if _fg is None:
+            lib = ctypes.CDLL(build_fastgen())
+            lib.fastgen_members.restype = ctypes.c_int
+            lib.fastgen_members.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_int]
+            _fg = lib
+    return _fg
+
+
+def members_fast(seed: Sequence[int], sizes: np.ndarray, weights: np.ndarray):
+    """Same rule as ``members``, drawn in C; returns (off int64 [m+1], idx int32)."""
+    sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    off = np.zeros(sizes.size + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    idx = np.empty(max(int(off[-1]), 1), np.int32)
+    key = int(np.random.SeedSequence([*seed, 3]).generate_state(1, dtype=np.uint64)[0])
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 4
+    rc = _fastgen().fastgen_members(sizes.size, sizes.ctypes.data, off.ctypes.data,
+                                    w.ctypes.data, w.size, key, idx.ctypes.data, threads)
+    if rc != 0:
+        raise MemoryError("fastgen_members failed")
+    return off, idx[:int(off[-1])]
+
+
 def build(seed: Sequence[int], m: int, n: int, size_kind: str, size_args: tuple,
-          pop_kind: str, pop_args: tuple, name: str = "") -> Hypergraph:
+          pop_kind: str, pop_args: tuple, name: str = "", fast: bool = False) -> Hypergraph:
     seed = tuple(int(x) for x in seed)
     rs = np.random.default_rng([*seed, 0])
     if size_kind == "zipf":
@@ -177,9 +232,12 @@ def build(seed: Sequence[int], m: int, n: int, size_kind: str, size_args: tuple,
         w = popularity_chung_lu(rp, n, *pop_args)
     else:
         raise ValueError(pop_kind)
-    idx = members(seed, sizes, w)
-    off = np.zeros(m + 1, np.int64)
-    np.cumsum(sizes, out=off[1:])
+    if fast:
+        off, idx = members_fast(seed, sizes, w)
+    else:
+        idx = members(seed, sizes, w)
+        off = np.zeros(m + 1, np.int64)
+        np.cumsum(sizes, out=off[1:])
     if off[-1] >= 2**31:
         raise ValueError("nnz does not fit int32 offsets")
     return Hypergraph(off.astype(np.int32), idx.astype(np.int32), int(n), name)
@@ -209,7 +267,7 @@ def large(seed: int = 0, m: int = 20_000_000, n: int | None = None) -> Hypergrap
     Chung-Lu popularity with vertex degree Zipf(1.8) capped at 100,000."""
     n = m // 2 if n is None else n
     return build((seed,), m, n, "lognormal", (2.0, 1.1, 2, 20000), "chung_lu",
-                 (1.8, 100_000), f"large_m{m}")
+                 (1.8, 100_000), f"large_m{m}", fast=True)
 
 
 def batch_member(b: int, base_seed: int = 0) -> tuple[Hypergraph, int]:
@@ -222,7 +280,7 @@ def batch_member(b: int, base_seed: int = 0) -> tuple[Hypergraph, int]:
     m = int(np.rint(np.exp(rng.uniform(np.log(100), np.log(100_000)))))
     s = int(rng.integers(1, 5))
     g = build((base_seed, b), m, max(m // 2, 1), "lognormal", (1.8, 1.0, 2, 5000), "zipf",
-              (1.7,), f"batch{b}_m{m}")
+              (1.7,), f"batch{b}_m{m}", fast=True)
     return g, s
 
 
@@ -235,7 +293,7 @@ def served_member(g: int, base_seed: int = 0) -> Hypergraph:
         rng = np.random.default_rng([base_seed, 1000 + g, 9])
         m = int(np.rint(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
     return build((base_seed, 1000 + g), m, m // 2, "lognormal", (1.8, 1.0, 2, 5000), "zipf",
-                 (1.7,), f"served{g}_m{m}")
+                 (1.7,), f"served{g}_m{m}", fast=True)
 
 
 def uniform_random(seed: int, m: int, n: int, lo: int, hi: int) -> Hypergraph:

@@ -49,3 +49,18 @@ def test_save_load_roundtrip(tmp_path):
     synth.save(h, p)
     g = synth.load(p)
     assert np.array_equal(h.off, g.off) and np.array_equal(h.idx, g.idx) and g.n == h.n
+
+
+def test_fast_member_draw():
+    # the C draw follows the same rule: valid rows of the requested sizes,
+    # deterministic per seed, Zipf(1.7) hubs in most rows
+    a = synth.build((4,), 20000, 10000, "lognormal", (1.8, 1.0, 2, 5000), "zipf", (1.7,),
+                    fast=True)
+    b = synth.build((4,), 20000, 10000, "lognormal", (1.8, 1.0, 2, 5000), "zipf", (1.7,),
+                    fast=True)
+    assert np.array_equal(a.idx, b.idx) and oracle.validate(a.off, a.idx, a.n)
+    ref = synth.build((4,), 20000, 10000, "lognormal", (1.8, 1.0, 2, 5000), "zipf", (1.7,))
+    assert np.array_equal(a.sizes(), ref.sizes())  # same size stream
+    da, dr = np.bincount(a.idx, minlength=a.n), np.bincount(ref.idx, minlength=ref.n)
+    assert abs(int(da.max()) - int(dr.max())) < 0.02 * a.m
+    assert set(np.argsort(-da)[:3].tolist()) == set(np.argsort(-dr)[:3].tolist())
