@@ -506,6 +506,83 @@ def bench_batch(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------- served form
+
+SERVE_WORKLOAD = ("served: 64 resident hypergraphs (8 with m=1,000,000, 56 with m log-uniform "
+                  "in [1e3,1e5]; n = m/2; medium recipe), queries (uniform graph, s uniform in "
+                  "1..16), Poisson arrivals")
+
+
+def bench_serve(args):
+    """Latency and throughput of the query server against one query at a time.
+
+    For each arrival rate the same seeded query stream is played against a
+    server with 8 workers (queries overlap on the device, admission by
+    predicted kept-result memory) and against the same runtime with one worker
+    (a one-query-at-a-time loop). Latency is submit -> result ready.
+    """
+    import torch
+    import paper_2201_11326_gb300 as slg
+    dev = torch.cuda.current_device()
+    t0 = time.perf_counter()
+    hs = [synth.served_member(g) for g in range(64)]
+    gen_s = time.perf_counter() - t0
+    gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    torch.cuda.synchronize()
+    rates = [100, 300, 1000, 3000, 10000]
+    nq = args.graphs if args.graphs != 4096 else 128
+    rng = np.random.default_rng([1, 2])
+    streams = {}
+    for r in rates:
+        gap = rng.exponential(1.0 / r, size=nq)
+        streams[r] = (np.cumsum(gap) - gap[0], rng.integers(0, 64, size=nq),
+                      rng.integers(1, 17, size=nq))
+
+    def play(srv, ids, r):
+        arr, gsel, ssel = streams[r]
+        slg.slg_serve_stats(srv, reset=True)
+        tickets = []
+        start = time.perf_counter()
+        for a, g, s in zip(arr, gsel, ssel):
+            delay = start + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(slg.slg_serve_submit(srv, ids[int(g)], int(s)))
+        for t in tickets:
+            slg.slg_serve_poll(srv, t, 600000)
+            slg.slg_serve_release(srv, t)
+        st = slg.slg_serve_stats(srv)
+        return {"rate": r, "p50_ms": round(st["p50_us"] / 1e3, 2),
+                "p99_ms": round(st["p99_us"] / 1e3, 2), "mean_ms": round(st["mean_us"] / 1e3, 2),
+                "queries_per_s": round(st["queries_per_s"], 2), "wedges_per_s": st["wedges_per_s"],
+                "s_edges_per_s": st["pairs_per_s"], "span_s": round(st["span_s"], 2)}
+
+    res = {}
+    for name, workers in (("served", 8), ("one_at_a_time", 1)):
+        srv = slg.Server(memory_budget=64 << 30, window_pairs=1 << 28,
+                         max_result_pairs=1 << 26, workers=workers, max_s=16, digest=False)
+        ids = [slg.slg_serve_register(srv, g) for g in gs]
+        # warm-up: a few queries
+        for g in (0, 9, 20):
+            slg.slg_serve_poll(srv, slg.slg_serve_submit(srv, ids[g], 4), 600000)
+        res[name] = [play(srv, ids, r) for r in rates]
+        srv.close()
+    for g in gs:
+        g.free()
+    served, loop = res["served"], res["one_at_a_time"]
+    out = {
+        "metric": "served p50/p99 query latency (s-line graphs of resident hypergraphs)",
+        "value": served[0]["p99_ms"], "unit": "ms (p99 at 100 queries/s)", "n_gpus": 1,
+        "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "queries_per_rate": nq, "rates": rates,
+                   "workers": 8, "memory_budget_GiB": 64, "window_pairs": 1 << 28,
+                   "max_result_pairs": 1 << 26, "generation_s": round(gen_s, 1),
+                   "rows": int(sum(h.m for h in hs)), "nnz": int(sum(h.nnz for h in hs))},
+        "served": served, "one_at_a_time": loop,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":

@@ -226,6 +226,75 @@ slg_status slg_batch_info(const slg_graph* b, int32_t* k, int32_t* row_base);
  * pair_base[b+1]-1 of the batch's list. Runs the counting pass if needed. */
 slg_status slg_batch_pair_offsets(slg_graph* b, int64_t* pair_base);
 
+/*
+ * Serving: s-line queries (graph, s) over resident hypergraphs.
+ *
+ * The paper's ensembles compute many s-line graphs of one hypergraph
+ * (Algorithm 3, Section III-D; Section V). A server keeps registered graphs on
+ * the device and runs queries on `workers` threads, each with its own CUDA
+ * stream and streaming window, so queries overlap on the device (a query uses
+ * a private plan over the shared graph arrays). A query whose predicted result
+ * 12 * floor(W_s / s) bytes (every s-incident pair accounts for at least s
+ * wedges, Section III-E) is at most max_result_pairs pairs is kept on the
+ * device until released, and is admitted only when its prediction fits in
+ * memory_budget minus the results already held; larger results are streamed
+ * through the worker's window (window_pairs pairs, allocated at creation,
+ * outside the budget) and return counts and digest only. Pending queries are
+ * taken in submission order, skipping one that does not fit yet.
+ */
+typedef struct slg_server slg_server;
+
+typedef struct {
+    int64_t memory_budget;    /* bytes for kept results */
+    int64_t window_pairs;     /* pairs per streaming window, one window per worker */
+    int64_t max_result_pairs; /* larger results are streamed, not kept */
+    int32_t workers;          /* concurrent queries (host threads, CUDA streams) */
+    int32_t max_s;            /* W_s is precomputed for s = 1..max_s at registration */
+    int32_t digest;           /* nonzero: compute each result's digest (slg_build_window) */
+    int32_t reserved0;
+} slg_serve_cfg;
+
+typedef struct {
+    slg_status status;
+    int32_t materialized; /* 1: the list is kept (slg_serve_fetch); 0: streamed */
+    int64_t pairs;        /* |L_s| */
+    int64_t wedges;       /* W_s */
+    uint64_t digest;      /* digest of the whole list (if cfg.digest) */
+    double latency_us;    /* submit -> done */
+    double queue_us;      /* submit -> start */
+} slg_serve_result;
+
+typedef struct {
+    int64_t completed;
+    double p50_us, p99_us, mean_us, max_us; /* latency, submit -> done */
+    double span_s;                          /* first submit -> last completion */
+    double queries_per_s, pairs_per_s, wedges_per_s;
+    int64_t peak_memory;                    /* bytes of kept results, at most */
+    int64_t pending;
+    int64_t running;
+} slg_serve_stats_t;
+
+/* Create a server on the current device (starts the worker threads). */
+slg_status slg_serve_create(const slg_serve_cfg* cfg, slg_server** out);
+/* Stop the workers (queries still pending are dropped) and free everything. */
+void slg_serve_destroy(slg_server* srv);
+/* Register a loaded graph (not a batch); it must outlive the server. Computes
+ * W_s for s = 1..max_s. */
+slg_status slg_serve_register(slg_server* srv, slg_graph* g, int32_t* graph_id);
+/* Queue a query; SLG_ECAPACITY if its kept result could never fit the budget. */
+slg_status slg_serve_submit(slg_server* srv, int32_t graph_id, int32_t s, uint64_t* ticket);
+/* Wait up to timeout_ms for a query; SLG_ETIMEOUT if it has not finished. */
+slg_status slg_serve_poll(slg_server* srv, uint64_t ticket, int32_t timeout_ms,
+                          slg_serve_result* out);
+/* Copy a kept result (canonical list) into I/J/O (host or device, cap pairs). */
+slg_status slg_serve_fetch(slg_server* srv, uint64_t ticket, int32_t* I, int32_t* J, int32_t* O,
+                           int64_t cap);
+/* Forget a finished query and free its kept result. */
+slg_status slg_serve_release(slg_server* srv, uint64_t ticket);
+/* Latency percentiles and throughput of the queries finished since the last
+ * reset (reset != 0 starts a new period). */
+slg_status slg_serve_stats(slg_server* srv, int32_t reset, slg_serve_stats_t* out);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t slg_kernel_launches(void);
 

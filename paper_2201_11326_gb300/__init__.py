@@ -22,7 +22,9 @@ __all__ = [
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
-    "slg_batch_info", "slg_batch_pair_offsets", "library_path",
+    "slg_batch_info", "slg_batch_pair_offsets", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
+    "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
 ]
 
@@ -53,6 +55,29 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("window_pairs", ctypes.c_int64),
+                ("max_result_pairs", ctypes.c_int64), ("workers", ctypes.c_int32),
+                ("max_s", ctypes.c_int32), ("digest", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("materialized", ctypes.c_int32),
+                ("pairs", ctypes.c_int64), ("wedges", ctypes.c_int64),
+                ("digest", ctypes.c_uint64), ("latency_us", ctypes.c_double),
+                ("queue_us", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("queries_per_s", ctypes.c_double), ("pairs_per_s", ctypes.c_double),
+                ("wedges_per_s", ctypes.c_double), ("peak_memory", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("running", ctypes.c_int64)]
+
+
 _SIGS = {
     "slg_last_error": (ctypes.c_char_p, []),
     "slg_version": (_i32, []),
@@ -76,6 +101,14 @@ _SIGS = {
     "slg_batch_load": (_i32, [ctypes.POINTER(_vp), _i32p, _i32, _vp, ctypes.POINTER(_vp)]),
     "slg_batch_info": (_i32, [_vp, _i32p, _i32p]),
     "slg_batch_pair_offsets": (_i32, [_vp, _i64p]),
+    "slg_serve_create": (_i32, [ctypes.POINTER(ServeCfg), ctypes.POINTER(_vp)]),
+    "slg_serve_destroy": (None, [_vp]),
+    "slg_serve_register": (_i32, [_vp, _vp, _i32p]),
+    "slg_serve_submit": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_uint64)]),
+    "slg_serve_poll": (_i32, [_vp, ctypes.c_uint64, _i32, ctypes.POINTER(ServeResult)]),
+    "slg_serve_fetch": (_i32, [_vp, ctypes.c_uint64, _vp, _vp, _vp, _i64]),
+    "slg_serve_release": (_i32, [_vp, ctypes.c_uint64]),
+    "slg_serve_stats": (_i32, [_vp, _i32, ctypes.POINTER(ServeStats)]),
 }
 
 
@@ -320,6 +353,76 @@ def slg_batch_pair_offsets(g: Graph) -> np.ndarray:
     out = np.zeros(k + 1, np.int64)
     _check(lib().slg_batch_pair_offsets(g.handle, out.ctypes.data_as(_i64p)))
     return out
+
+
+class Server:
+    """A query server (handle of libslg's slg_server)."""
+
+    def __init__(self, memory_budget: int, window_pairs: int, max_result_pairs: int,
+                 workers: int = 4, max_s: int = 16, digest: bool = True):
+        cfg = ServeCfg(memory_budget, window_pairs, max_result_pairs, workers, max_s,
+                       1 if digest else 0, 0)
+        h = _vp()
+        _check(lib().slg_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h.value
+        self._graphs = []
+
+    def close(self):
+        if self._h:
+            lib().slg_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def slg_serve_create(memory_budget: int, window_pairs: int, max_result_pairs: int,
+                     workers: int = 4, max_s: int = 16, digest: bool = True) -> Server:
+    return Server(memory_budget, window_pairs, max_result_pairs, workers, max_s, digest)
+
+
+def slg_serve_destroy(srv: Server):
+    srv.close()
+
+
+def slg_serve_register(srv: Server, g: Graph) -> int:
+    gid = _i32()
+    _check(lib().slg_serve_register(srv._h, g.handle, ctypes.byref(gid)))
+    srv._graphs.append(g)
+    return gid.value
+
+
+def slg_serve_submit(srv: Server, graph_id: int, s: int) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().slg_serve_submit(srv._h, graph_id, s, ctypes.byref(t)))
+    return t.value
+
+
+def slg_serve_poll(srv: Server, ticket: int, timeout_ms: int = 60000) -> dict:
+    r = ServeResult()
+    _check(lib().slg_serve_poll(srv._h, ticket, timeout_ms, ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in ServeResult._fields_}
+
+
+def slg_serve_fetch(srv: Server, ticket: int, pairs: int):
+    I = np.zeros(max(pairs, 1), np.int32)
+    J = np.zeros(max(pairs, 1), np.int32)
+    O = np.zeros(max(pairs, 1), np.int32)
+    _check(lib().slg_serve_fetch(srv._h, ticket, _ptr(I), _ptr(J), _ptr(O), pairs))
+    return I[:pairs], J[:pairs], O[:pairs]
+
+
+def slg_serve_release(srv: Server, ticket: int):
+    _check(lib().slg_serve_release(srv._h, ticket))
+
+
+def slg_serve_stats(srv: Server, reset: bool = False) -> dict:
+    st = ServeStats()
+    _check(lib().slg_serve_stats(srv._h, 1 if reset else 0, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in ServeStats._fields_}
 
 
 def slg_scan_counts_noalloc(counts, offsets, stream=None):

@@ -8,7 +8,7 @@
 #include <atomic>
 #include <vector>
 
-#include "plan.cuh"
+#include "handle.cuh"
 
 namespace slg {
 
@@ -68,6 +68,8 @@ void dfree(T*& p, cudaStream_t st) {
     p = nullptr;
 }
 
+}  // namespace
+
 BinParams default_bins() {
     BinParams b;
     b.warp_max_wedges = 128;
@@ -78,41 +80,41 @@ BinParams default_bins() {
     return b;
 }
 
-struct Timer {
-    bool on = false;
-    cudaEvent_t ev[6] = {};
-    void init() {
-        for (auto& e : ev)
-            if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
-    }
-    void mark(int k, cudaStream_t st) {
-        if (on) SLG_CUDA_TRY(cudaEventRecord(ev[k], st));
-    }
-    void destroy() {
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
-    }
-};
+void Timer::init() {
+    for (auto& e : ev)
+        if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
+}
+void Timer::mark(int k, cudaStream_t st) {
+    if (on) SLG_CUDA_TRY(cudaEventRecord(ev[k], st));
+}
+void Timer::destroy() {
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+}
 
 void mtimer_init(ModeTimer& t) {
     for (auto& e : t.ev)
         if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
 }
 
-}  // namespace
-}  // namespace slg
+slg_graph* make_view(const slg_graph* base, cudaStream_t st) {
+    slg_graph* h = new slg_graph();
+    h->g = base->g;
+    h->owns_data = false;
+    h->st = st;
+    h->device = base->device;
+    h->bp = base->bp;
+    try {
+        h->timer.init();
+        mtimer_init(h->mtimer);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    return h;
+}
 
-struct slg_graph {
-    slg::GraphDev g;
-    slg::Plan plan;
-    cudaStream_t st = nullptr;
-    int device = 0;
-    slg::BinParams bp = slg::default_bins();
-    slg::Timer timer;
-    slg::ModeTimer mtimer;
-    float ms[5] = {0, 0, 0, 0, 0};
-    std::vector<int32_t> batch_row_base;  // members' first rows (k+1) when this is a batch
-};
+}  // namespace slg
 
 using slg::Error;
 
@@ -310,7 +312,7 @@ void slg_free(slg_graph* h) {
         h->plan.release(h->st);
     } catch (...) {
     }
-    free_graph_dev(h->g, h->st);
+    if (h->owns_data) free_graph_dev(h->g, h->st);
     cudaStreamSynchronize(h->st);
     h->timer.destroy();
     for (auto& e : h->mtimer.ev)

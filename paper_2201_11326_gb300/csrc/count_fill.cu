@@ -23,6 +23,7 @@
 // pass writes (i, j, overlap) in ascending j with warp-ballot compaction (the
 // per-thread output lists of Algorithm 2 are not needed).
 #include <cstdio>
+#include <mutex>
 
 #include "plan.cuh"
 
@@ -915,9 +916,12 @@ struct Occupancy {
     int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, wdense_ctas = 0, wdense_fill_ctas = 0;
 };
 
-Occupancy& occupancy() {
-    static Occupancy o;
-    if (o.sms == 0) {
+Occupancy g_occ;
+std::once_flag g_occ_once;
+
+void occupancy_init() {
+    Occupancy& o = g_occ;
+    {
         int dev = 0;
         SLG_CUDA_TRY(cudaGetDevice(&dev));
         SLG_CUDA_TRY(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev));
@@ -951,7 +955,11 @@ Occupancy& occupancy() {
         o.block_ctas = o.sms * (b > 0 ? b : 1);
         o.dense_ctas = o.sms * (c > 0 ? c : 1);
     }
-    return o;
+}
+
+Occupancy& occupancy() {
+    std::call_once(g_occ_once, occupancy_init);
+    return g_occ;
 }
 
 template <bool FILL>

@@ -1,0 +1,44 @@
+// The graph handle behind the C ABI's opaque slg_graph (internal).
+#pragma once
+
+#include <vector>
+
+#include "plan.cuh"
+
+namespace slg {
+
+BinParams default_bins();
+
+// CUDA events around the phases of the last counting pass / fill.
+struct Timer {
+    bool on = false;
+    cudaEvent_t ev[6] = {};
+    void init();
+    void mark(int k, cudaStream_t st);
+    void destroy();
+};
+
+void mtimer_init(ModeTimer& t);
+
+}  // namespace slg
+
+struct slg_graph {
+    slg::GraphDev g;
+    bool owns_data = true;  // false for a view sharing another handle's arrays
+    slg::Plan plan;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    slg::BinParams bp = slg::default_bins();
+    slg::Timer timer;
+    slg::ModeTimer mtimer;
+    float ms[5] = {0, 0, 0, 0, 0};
+    std::vector<int32_t> batch_row_base;  // members' first rows (k+1) when this is a batch
+};
+
+namespace slg {
+
+// A handle that shares base's device arrays (which must outlive it) with its
+// own plan and stream, so that several s of one graph can run concurrently.
+slg_graph* make_view(const slg_graph* base, cudaStream_t st);
+
+}  // namespace slg
