@@ -548,9 +548,26 @@ def bench_serve(args):
             if delay > 0:
                 time.sleep(delay)
             tickets.append(slg.slg_serve_submit(srv, ids[int(g)], int(s)))
-        for t in tickets:
-            slg.slg_serve_poll(srv, t, 600000)
-            slg.slg_serve_release(srv, t)
+        # collect in completion order, releasing each kept result at once (a
+        # result held by the client counts against the server's memory budget)
+        outstanding = list(tickets)
+        deadline = time.perf_counter() + 1800
+        while outstanding and time.perf_counter() < deadline:
+            still = []
+            for t in outstanding:
+                try:
+                    slg.slg_serve_poll(srv, t, 0)
+                except slg.SlgError as e:
+                    if e.code != slg.SLG_ETIMEOUT:
+                        raise
+                    still.append(t)
+                    continue
+                slg.slg_serve_release(srv, t)
+            outstanding = still
+            if outstanding:
+                time.sleep(0.002)
+        if outstanding:
+            raise RuntimeError(f"{len(outstanding)} queries did not finish")
         st = slg.slg_serve_stats(srv)
         return {"rate": r, "p50_ms": round(st["p50_us"] / 1e3, 2),
                 "p99_ms": round(st["p99_us"] / 1e3, 2), "mean_ms": round(st["mean_us"] / 1e3, 2),
@@ -558,13 +575,18 @@ def bench_serve(args):
                 "s_edges_per_s": st["pairs_per_s"], "span_s": round(st["span_s"], 2)}
 
     res = {}
-    for name, workers in (("served", 8), ("one_at_a_time", 1)):
+    arms = (("served", dict(workers=8, policy=1, small_workers=2, small_wedges=2_000_000_000)),
+            ("served_fifo", dict(workers=8, policy=0)),
+            ("one_at_a_time", dict(workers=1, policy=0)))
+    for name, kw in arms:
         srv = slg.Server(memory_budget=64 << 30, window_pairs=1 << 28,
-                         max_result_pairs=1 << 26, workers=workers, max_s=16, digest=False)
+                         max_result_pairs=1 << 26, max_s=16, digest=False, **kw)
         ids = [slg.slg_serve_register(srv, g) for g in gs]
         # warm-up: a few queries
         for g in (0, 9, 20):
-            slg.slg_serve_poll(srv, slg.slg_serve_submit(srv, ids[g], 4), 600000)
+            t = slg.slg_serve_submit(srv, ids[g], 4)
+            slg.slg_serve_poll(srv, t, 600000)
+            slg.slg_serve_release(srv, t)
         res[name] = [play(srv, ids, r) for r in rates]
         srv.close()
     for g in gs:
@@ -575,10 +597,11 @@ def bench_serve(args):
         "value": served[0]["p99_ms"], "unit": "ms (p99 at 100 queries/s)", "n_gpus": 1,
         "higher_is_better": False, "dtype": "int32", "data": "synthetic",
         "config": {"workload": SERVE_WORKLOAD, "queries_per_rate": nq, "rates": rates,
-                   "workers": 8, "memory_budget_GiB": 64, "window_pairs": 1 << 28,
+                   "workers": 8, "policy": "least predicted W_s first, 2 of 8 workers for "
+                   "queries with W_s <= 2e9", "memory_budget_GiB": 64, "window_pairs": 1 << 28,
                    "max_result_pairs": 1 << 26, "generation_s": round(gen_s, 1),
                    "rows": int(sum(h.m for h in hs)), "nnz": int(sum(h.nnz for h in hs))},
-        "served": served, "one_at_a_time": loop,
+        "served": served, "served_fifo": res["served_fifo"], "one_at_a_time": loop,
     }
     print(json.dumps(out), flush=True)
 

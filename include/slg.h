@@ -98,6 +98,17 @@ slg_status slg_graph_info(const slg_graph* g, int32_t* m, int32_t* n, int64_t* n
 slg_status slg_transpose_copy(slg_graph* g, int32_t* offT, int32_t* idxT);
 
 /*
+ * slg_dual -- the dual hypergraph H* (Section II-A: vertices and hyperedges
+ * swap roles, incidence H^T) as a new handle. Its s-line graphs are the
+ * s-clique graphs of H (Section III-H: vertices u, v joined when they share at
+ * least s hyperedges, i.e. the off-diagonal of W = H H^T - D_V thresholded at
+ * s), with vertex ids as row ids. Built from the device-resident transpose
+ * (no host copy); release with slg_free. Errors as slg_load; SLG_EINVAL for a
+ * batch.
+ */
+slg_status slg_dual(slg_graph* g, void* stream, slg_graph** out);
+
+/*
  * slg_count -- exact size of L_s(H) and the algorithmic work, without
  * writing the list (the counting half of Algorithm 2, Section III-C).
  *
@@ -240,7 +251,10 @@ slg_status slg_batch_pair_offsets(slg_graph* b, int64_t* pair_base);
  * memory_budget minus the results already held; larger results are streamed
  * through the worker's window (window_pairs pairs, allocated at creation,
  * outside the budget) and return counts and digest only. Pending queries are
- * taken in submission order, skipping one that does not fit yet.
+ * taken in submission order (policy 0) or smallest predicted W_s first
+ * (policy 1), skipping one that does not fit yet; small_workers of the workers
+ * take only queries predicted at most small_wedges wedges, so that short
+ * queries are not queued behind long ones.
  */
 typedef struct slg_server slg_server;
 
@@ -251,7 +265,10 @@ typedef struct {
     int32_t workers;          /* concurrent queries (host threads, CUDA streams) */
     int32_t max_s;            /* W_s is precomputed for s = 1..max_s at registration */
     int32_t digest;           /* nonzero: compute each result's digest (slg_build_window) */
+    int32_t policy;           /* 0: submission order; 1: smallest predicted W_s first */
+    int32_t small_workers;    /* workers that only take queries with W_s <= small_wedges */
     int32_t reserved0;
+    int64_t small_wedges;     /* threshold for the small-query workers */
 } slg_serve_cfg;
 
 typedef struct {

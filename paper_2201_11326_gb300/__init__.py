@@ -22,7 +22,7 @@ __all__ = [
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
-    "slg_batch_info", "slg_batch_pair_offsets", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -59,7 +59,8 @@ class ServeCfg(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_int64), ("window_pairs", ctypes.c_int64),
                 ("max_result_pairs", ctypes.c_int64), ("workers", ctypes.c_int32),
                 ("max_s", ctypes.c_int32), ("digest", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("policy", ctypes.c_int32), ("small_workers", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("small_wedges", ctypes.c_int64)]
 
 
 class ServeResult(ctypes.Structure):
@@ -99,6 +100,7 @@ _SIGS = {
     "slg_kernel_launches": (_i64, []),
     "slg_scan_counts_noalloc": (_i32, [_vp, _vp, _i64, _vp]),
     "slg_batch_load": (_i32, [ctypes.POINTER(_vp), _i32p, _i32, _vp, ctypes.POINTER(_vp)]),
+    "slg_dual": (_i32, [_vp, _vp, ctypes.POINTER(_vp)]),
     "slg_batch_info": (_i32, [_vp, _i32p, _i32p]),
     "slg_batch_pair_offsets": (_i32, [_vp, _i64p]),
     "slg_serve_create": (_i32, [ctypes.POINTER(ServeCfg), ctypes.POINTER(_vp)]),
@@ -325,6 +327,15 @@ def slg_kernel_launches() -> int:
     return int(lib().slg_kernel_launches())
 
 
+def slg_dual(g: Graph, stream=None) -> Graph:
+    """The dual H*; its s-line graphs are the s-clique graphs of H."""
+    h = _vp()
+    _check(lib().slg_dual(g.handle, _stream_handle(stream), ctypes.byref(h)))
+    mm, nn, nz = _i32(), _i32(), _i64()
+    _check(lib().slg_graph_info(h, ctypes.byref(mm), ctypes.byref(nn), ctypes.byref(nz)))
+    return Graph(h.value, mm.value, nn.value, nz.value)
+
+
 def slg_batch_load(graphs, s_list, stream=None) -> Graph:
     """One handle over many graphs, each with its own s (pass s=0 to its calls)."""
     k = len(graphs)
@@ -359,9 +370,10 @@ class Server:
     """A query server (handle of libslg's slg_server)."""
 
     def __init__(self, memory_budget: int, window_pairs: int, max_result_pairs: int,
-                 workers: int = 4, max_s: int = 16, digest: bool = True):
+                 workers: int = 4, max_s: int = 16, digest: bool = True, policy: int = 0,
+                 small_workers: int = 0, small_wedges: int = 0):
         cfg = ServeCfg(memory_budget, window_pairs, max_result_pairs, workers, max_s,
-                       1 if digest else 0, 0)
+                       1 if digest else 0, policy, small_workers, 0, small_wedges)
         h = _vp()
         _check(lib().slg_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h.value
@@ -380,8 +392,10 @@ class Server:
 
 
 def slg_serve_create(memory_budget: int, window_pairs: int, max_result_pairs: int,
-                     workers: int = 4, max_s: int = 16, digest: bool = True) -> Server:
-    return Server(memory_budget, window_pairs, max_result_pairs, workers, max_s, digest)
+                     workers: int = 4, max_s: int = 16, digest: bool = True, policy: int = 0,
+                     small_workers: int = 0, small_wedges: int = 0) -> Server:
+    return Server(memory_budget, window_pairs, max_result_pairs, workers, max_s, digest, policy,
+                  small_workers, small_wedges)
 
 
 def slg_serve_destroy(srv: Server):

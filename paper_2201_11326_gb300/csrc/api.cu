@@ -651,5 +651,14 @@ slg_status slg_batch_pair_offsets(slg_graph* h, int64_t* pair_base) {
     API_END
 }
 
+slg_status slg_dual(slg_graph* h, void* stream, slg_graph** out) {
+    if (!out) return fail(SLG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (h->g.srow) return fail(SLG_EINVAL, "the dual of a batch is not defined");
+    // the dual's incidence is this graph's transpose, already on the device
+    return slg_load(h->g.offT, h->g.idxT, h->g.n, h->g.m, stream, out);
+}
+
 }  // extern "C"
 

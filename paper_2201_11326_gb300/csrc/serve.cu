@@ -31,6 +31,7 @@ using Clock = std::chrono::steady_clock;
 struct ServeQuery {
     int32_t graph = 0, s = 0;
     int64_t reserved = 0;  // bytes held against the budget
+    int64_t work = 0;      // predicted W_s
     Clock::time_point t_submit, t_start, t_done;
     slg_status status = SLG_OK;
     bool started = false, done = false, materialized = false;
@@ -75,10 +76,14 @@ struct slg_server {
 
 namespace {
 
-int64_t predicted_pairs(const slg_server* S, int32_t graph, int32_t s) {
+int64_t predicted_wedges(const slg_server* S, int32_t graph, int32_t s) {
     const std::vector<int64_t>& w = S->wedges[(size_t)graph];
     const int32_t k = std::min<int32_t>(s, (int32_t)w.size());
-    return w[(size_t)k - 1] / s;
+    return w[(size_t)k - 1];  // W_s is non-increasing in s
+}
+
+int64_t predicted_pairs(const slg_server* S, int32_t graph, int32_t s) {
+    return predicted_wedges(S, graph, s) / s;
 }
 
 // The reservation a query needs: its kept result, or nothing when it streams.
@@ -145,15 +150,21 @@ void worker_loop(slg_server* S, size_t wi) {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop) return;
-                // first pending query whose reservation fits
-                auto it = S->pending.begin();
-                for (; it != S->pending.end(); ++it) {
+                // a pending query whose reservation fits: the first one, or the
+                // one with the least predicted work; small-query workers skip
+                // the large ones
+                const bool small_only = (int32_t)wi < S->cfg.small_workers;
+                auto pick = S->pending.end();
+                for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
                     const ServeQuery& Q = S->q[*it];
-                    if (S->mem_in_use + Q.reserved <= S->cfg.memory_budget) break;
+                    if (S->mem_in_use + Q.reserved > S->cfg.memory_budget) continue;
+                    if (small_only && Q.work > S->cfg.small_wedges) continue;
+                    if (pick == S->pending.end() || S->q[*pick].work > Q.work) pick = it;
+                    if (S->cfg.policy == 0) break;
                 }
-                if (it != S->pending.end()) {
-                    ticket = *it;
-                    S->pending.erase(it);
+                if (pick != S->pending.end()) {
+                    ticket = *pick;
+                    S->pending.erase(pick);
                     break;
                 }
                 S->cv_work.wait(lk);
@@ -231,7 +242,8 @@ slg_status slg_serve_create(const slg_serve_cfg* cfg, slg_server** out) {
     if (!out || !cfg) return sfail(SLG_EINVAL, "NULL argument");
     *out = nullptr;
     if (cfg->workers < 1 || cfg->window_pairs < 1 || cfg->max_s < 1 || cfg->memory_budget < 0 ||
-        cfg->max_result_pairs < 0)
+        cfg->max_result_pairs < 0 || cfg->policy < 0 || cfg->policy > 1 ||
+        cfg->small_workers < 0 || cfg->small_workers >= cfg->workers)
         return sfail(SLG_EINVAL, "bad server configuration");
     slg_server* S = new slg_server();
     S->cfg = *cfg;
@@ -323,6 +335,7 @@ slg_status slg_serve_submit(slg_server* S, int32_t graph_id, int32_t s, uint64_t
     Q.graph = graph_id;
     Q.s = s;
     Q.reserved = need;
+    Q.work = predicted_wedges(S, graph_id, s);
     Q.t_submit = Clock::now();
     if (!S->any_submit) {
         S->first_submit = Q.t_submit;

@@ -178,6 +178,20 @@ def test_hub_masks_many_hubs():
             assert_same(gpu_list(h, s, FORCED[mode]), want, f"{mode} s={s}")
 
 
+def test_s_clique_graphs_through_the_dual():
+    for h in (synth.tiny(), synth.medium(seed=15, m=3000)):
+        g = slg.slg_load(h.off, h.idx, h.m, h.n)
+        d = slg.slg_dual(g)
+        try:
+            assert (d.m, d.n, d.nnz) == (h.n, h.m, h.nnz)
+            offT, idxT = oracle.transpose(h.off, h.idx, h.n)
+            for s in (1, 2, 4):
+                assert_same(slg.slg_build(d, s), oracle.slg_par(offT, idxT, s), f"dual s={s}")
+        finally:
+            d.free()
+            g.free()
+
+
 def test_invalid_input_rejected():
     bad = {
         "unsorted": (np.array([0, 2], np.int32), np.array([3, 1], np.int32), 1, 4),

@@ -35,7 +35,7 @@ def oracle_digest(h, s):
 def test_mixed_queries_match_oracle(graphs):
     hs, gs = graphs
     srv = slg.Server(memory_budget=8 << 30, window_pairs=1 << 22, max_result_pairs=1 << 22,
-                     workers=4, max_s=8)
+                     workers=4, max_s=8, policy=1, small_workers=1, small_wedges=10_000_000)
     try:
         ids = [slg.slg_serve_register(srv, g) for g in gs]
         rng = np.random.default_rng(3)

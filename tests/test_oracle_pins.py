@@ -208,6 +208,19 @@ def test_transpose_vs_scipy():
     assert np.array_equal(idxT, H.indices.astype(np.int32))
 
 
+def test_s_clique_is_line_graph_of_dual():
+    # Section III-H: W = H H^T - D_V; the s-clique graph joins u, v with
+    # W[u, v] >= s, and equals the s-line graph of the dual H*
+    h = synth.medium(seed=14, m=1500)
+    H = sp.csr_matrix((np.ones(h.nnz, np.int64), h.idx, h.off), shape=(h.m, h.n))
+    Wm = (H.T @ H).tocoo()  # n x n: W[u,v] = hyperedges holding both u and v (+ D_V)
+    offT, idxT = oracle.transpose(h.off, h.idx, h.n)
+    for s in (1, 2, 5):
+        keep = (Wm.row < Wm.col) & (Wm.data >= s)
+        want = sorted(zip(Wm.row[keep].tolist(), Wm.col[keep].tolist(), Wm.data[keep].tolist()))
+        assert as_triples(*oracle.slg(offT, idxT, s)) == want
+
+
 # ------------------------------------------------------------ closed forms
 
 
