@@ -344,7 +344,9 @@ slg_status slg_serve_submit(slg_server* S, int32_t graph_id, int32_t s, uint64_t
     S->pending.push_back(t);
     *ticket = t;
     lk.unlock();
-    S->cv_work.notify_one();
+    // every worker re-examines the queue: a worker restricted to small
+    // queries may not take this one, so waking a single waiter could stall it
+    S->cv_work.notify_all();
     return SLG_OK;
 }
 

@@ -109,6 +109,21 @@ def test_streamed_results_and_admission(graphs):
         srv.close()
 
 
+def test_large_query_reaches_a_general_worker(graphs):
+    # with workers restricted to small queries, a large query must still run
+    hs, gs = graphs
+    srv = slg.Server(1 << 30, 1 << 20, 1 << 24, workers=3, max_s=4, policy=1, small_workers=2,
+                     small_wedges=1)
+    try:
+        gid = slg.slg_serve_register(srv, gs[1])
+        for _ in range(3):
+            t = slg.slg_serve_submit(srv, gid, 2)
+            assert slg.slg_serve_poll(srv, t, 60000)["status"] == 0
+            slg.slg_serve_release(srv, t)
+    finally:
+        srv.close()
+
+
 def test_poll_timeout(graphs):
     hs, gs = graphs
     srv = slg.Server(1 << 30, 1 << 20, 1 << 24, workers=1, max_s=4)
