@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--window", type=int, default=1 << 31, help="pairs per output window")
-    ap.add_argument("--workload", choices=["medium", "batch", "serve"], default="medium")
+    ap.add_argument("--workload", choices=["medium", "batch", "serve", "ensemble"],
+                    default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
     return ap.parse_args()
 
@@ -506,6 +507,116 @@ def bench_batch(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- ensemble
+
+def run_ensemble(slg, g, s_list, bufs):
+    """Algorithm 3 on a loaded graph: one plan for min(s_list), every list counted,
+    then every window of all lists (the lists of a window back to back)."""
+    I, J, O = bufs
+    cap = I.numel()
+    pairs, _ = slg.slg_ensemble_count(g, s_list)
+    splits = slg.slg_ensemble_plan_windows(g, s_list, cap)
+    for r0, r1 in zip(splits[:-1], splits[1:]):
+        slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap)
+    return pairs
+
+
+def bench_ensemble(args):
+    """The s sweep of the medium workload as one ensemble against one s at a time.
+
+    Both arms start from the CSR resident in HBM and run slg_load inside the
+    step. Ensemble step: one plan for the smallest s, the counting pass for
+    every s, then the fill of every window of all lists. Per-s step: the
+    default benchmark's step. Same metric (sum over s of W_s per second).
+    """
+    import torch
+    import paper_2201_11326_gb300 as slg
+    dev = torch.cuda.current_device()
+    s_list = s_values(args.s)
+    h = workload(args.m)
+    off_d = torch.from_numpy(h.off).to(dev)
+    idx_d = torch.from_numpy(h.idx).to(dev)
+    stream = torch.cuda.Stream(dev)
+    I = torch.empty(args.window, dtype=torch.int32, device=dev)
+    J = torch.empty_like(I)
+    O = torch.empty_like(I)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+    counts = {s: slg.slg_count(g, s) for s in s_list}
+    g.free()
+    W = sum(w for _, w in counts.values())
+    P = sum(p for p, _ in counts.values())
+
+    def ens():
+        g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+        slg.slg_set_timing(g, True)
+        pairs = run_ensemble(slg, g, s_list, (I, J, O))
+        ks = slg.slg_kernel_stats(g)
+        g.free()
+        assert pairs == [counts[s][0] for s in s_list]
+        return ks
+
+    def sweep():
+        g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+        slg.slg_set_timing(g, True)
+        run_sweep(slg, g, s_list, (I, J, O), stream, {})
+        ks = slg.slg_kernel_stats(g)
+        g.free()
+        return ks
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            flush.fill_(0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            l0 = slg.slg_kernel_launches()
+            e0.record(stream)
+            ks = fn()
+            e1.record(stream)
+            e1.synchronize()
+        return e0.elapsed_time(e1), slg.slg_kernel_launches() - l0, ks
+
+    names = list(slg.MODE_NAMES)
+    res = {}
+    clocks = None
+    for name, fn in (("ensemble", ens), ("per_s", sweep)):
+        for _ in range(args.warmup):
+            timed(fn)
+        if name == "ensemble":
+            clocks = Clocks(dev)
+        times, launches, kms = [], 0, {}
+        for _ in range(args.steps):
+            ms, nl, (kt, _) = timed(fn)
+            times.append(ms)
+            launches = nl
+            for pi, ps in enumerate(("count", "fill")):
+                for k in range(slg.NMODES):
+                    key = f"{ps}_{names[k]}"
+                    kms[key] = kms.get(key, 0.0) + kt[pi][k] / args.steps
+        if name == "ensemble":
+            clk = clocks.stop()
+        ms = statistics.mean(times)
+        res[name] = {"wedges_per_s": W / (ms / 1e3), "s_edges_per_s": P / (ms / 1e3),
+                     "ms_per_step": round(ms, 1), "gpu_launches": int(launches),
+                     "kernel_ms_per_step": {k: round(v, 1) for k, v in kms.items()}}
+    out = {
+        "metric": "s-line wedges/s of an ensemble (medium hypergraph, s=1..8 as one ensemble, "
+                  "bit-exact)",
+        "value": res["ensemble"]["wedges_per_s"], "unit": "wedges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["ensemble"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list,
+                   "window_pairs": args.window, "wedges": W, "pairs": P,
+                   "l2": "flushed before each step (512 MiB device write); inputs resident"},
+        "ensemble": res["ensemble"], "per_s": res["per_s"],
+        "speedup_vs_per_s": res["ensemble"]["wedges_per_s"] / res["per_s"]["wedges_per_s"],
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------- served form
 
 SERVE_WORKLOAD = ("served: 64 resident hypergraphs (8 with m=1,000,000, 56 with m log-uniform "
@@ -614,6 +725,8 @@ def main():
         bench_batch(args)
     elif args.workload == "serve":
         bench_serve(args)
+    elif args.workload == "ensemble":
+        bench_ensemble(args)
     else:
         bench_ours(args)
 

@@ -178,6 +178,60 @@ slg_status slg_plan_windows(slg_graph* g, int32_t s, int64_t cap, int32_t* row_s
                             int32_t max_windows, int32_t* nwindows);
 
 /*
+ * Ensembles (Algorithm 3, Section III-D): the s-line graphs of one hypergraph
+ * for several thresholds s_list[0] < s_list[1] < ... < s_list[k-1]. Algorithm
+ * 3 counts the overlaps once (pruned by the smallest s) and then filters the
+ * counted pairs once per threshold. Here one plan, pruned by s_list[0], serves
+ * every list: the counting pass runs over it once per threshold, and the fill
+ * writes every list of a row window from it.
+ *
+ * Every ensemble call takes the same (s_list, k), with 1 <= k <=
+ * SLG_ENSEMBLE_MAX and s_list strictly ascending, s_list[0] >= 1. The counts
+ * are cached per handle until another s or list is used. Errors: SLG_EINVAL for
+ * a bad list or a batch handle.
+ *
+ * slg_ensemble_count -- pairs[t] = |L_{s_list[t]}(H)| (k entries, may be
+ * NULL); wedges = W_{s_list[0]} (may be NULL).
+ */
+#define SLG_ENSEMBLE_MAX 16
+slg_status slg_ensemble_count(slg_graph* g, const int32_t* s_list, int32_t k, int64_t* pairs,
+                              int64_t* wedges);
+
+/*
+ * slg_ensemble_row_offsets -- rowoff[t*(m+1) + i] is row i's first position in
+ * the canonical list of L_{s_list[t]}(H) (k*(m+1) int64 entries, host or
+ * device).
+ */
+slg_status slg_ensemble_row_offsets(slg_graph* g, const int32_t* s_list, int32_t k,
+                                    int64_t* rowoff);
+
+/*
+ * slg_ensemble_plan_windows -- as slg_plan_windows, with a window's size being
+ * the sum of its pairs over the k lists.
+ */
+slg_status slg_ensemble_plan_windows(slg_graph* g, const int32_t* s_list, int32_t k, int64_t cap,
+                                     int32_t* row_splits, int32_t max_windows,
+                                     int32_t* nwindows);
+
+/*
+ * slg_ensemble_build_window -- the pairs of rows [row_begin, row_end) of every
+ * list. I, J, O (cap entries each, host or device, all of one kind) receive
+ * the lists back to back: list t occupies positions seg_t .. seg_t + pairs[t]
+ * - 1, seg_t = pairs[0] + ... + pairs[t-1]. Each list is the contiguous slice
+ * of its canonical list (sorted by (i, j)).
+ *
+ *   pairs       : k entries, receives each list's pair count for the window.
+ *   digests     : NULL or k entries, each list's digest as in slg_build_window.
+ *   row_digests : NULL or k*(row_end - row_begin) entries, list-major.
+ * Errors: SLG_ECAPACITY when the k lists together exceed cap (pairs is set,
+ * nothing is written); SLG_EINVAL as above or for a bad range.
+ */
+slg_status slg_ensemble_build_window(slg_graph* g, const int32_t* s_list, int32_t k,
+                                     int32_t row_begin, int32_t row_end, int32_t* I, int32_t* J,
+                                     int32_t* O, int64_t cap, int64_t* pairs, uint64_t* digests,
+                                     uint64_t* row_digests);
+
+/*
  * Phase timing. When enabled, the library records CUDA events on the graph's
  * stream around each phase; slg_last_timing then returns, for the last
  * counting pass and the last fill, ms[0..4] = planning (pruning, per-row

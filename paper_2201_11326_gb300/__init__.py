@@ -22,7 +22,9 @@ __all__ = [
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
-    "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "slg_ensemble_count",
+    "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -92,6 +94,11 @@ _SIGS = {
     "slg_build": (_i32, [_vp, _i32, _vp, _vp, _vp, _i64, _i64p]),
     "slg_build_window": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _i64, _i64p, _u64p, _vp]),
     "slg_plan_windows": (_i32, [_vp, _i32, _i64, _i32p, _i32, _i32p]),
+    "slg_ensemble_count": (_i32, [_vp, _i32p, _i32, _i64p, _i64p]),
+    "slg_ensemble_row_offsets": (_i32, [_vp, _i32p, _i32, _vp]),
+    "slg_ensemble_plan_windows": (_i32, [_vp, _i32p, _i32, _i64, _i32p, _i32, _i32p]),
+    "slg_ensemble_build_window": (_i32, [_vp, _i32p, _i32, _i32, _i32, _vp, _vp, _vp, _i64,
+                                         _i64p, _u64p, _vp]),
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
@@ -292,6 +299,76 @@ def slg_plan_windows(g: Graph, s: int, cap: int, max_windows: int = 1 << 20) -> 
     _check(lib().slg_plan_windows(g.handle, s, cap, splits.ctypes.data_as(_i32p), max_windows,
                                   ctypes.byref(nw)))
     return splits[:nw.value + 1].copy()
+
+
+ENSEMBLE_MAX = 16
+
+
+def _s_list(s_list):
+    a = np.ascontiguousarray(np.asarray(s_list, dtype=np.int32).reshape(-1))
+    return a, a.ctypes.data_as(_i32p), int(a.size)
+
+
+def slg_ensemble_count(g: Graph, s_list):
+    """([|L_s| for s in s_list], W_{s_list[0]}); s_list strictly ascending."""
+    a, ap, k = _s_list(s_list)
+    pairs = np.zeros(max(k, 1), np.int64)
+    w = _i64()
+    _check(lib().slg_ensemble_count(g.handle, ap, k, pairs.ctypes.data_as(_i64p),
+                                    ctypes.byref(w)))
+    return [int(x) for x in pairs[:k]], w.value
+
+
+def slg_ensemble_row_offsets(g: Graph, s_list, out=None):
+    """[k, m+1] row offsets, one row per list."""
+    a, ap, k = _s_list(s_list)
+    if out is None:
+        out = np.zeros((k, g.m + 1), np.int64)
+    _check(lib().slg_ensemble_row_offsets(g.handle, ap, k, _ptr(out)))
+    return out
+
+
+def slg_ensemble_plan_windows(g: Graph, s_list, cap: int,
+                              max_windows: int = 1 << 20) -> np.ndarray:
+    a, ap, k = _s_list(s_list)
+    splits = np.zeros(max_windows + 1, np.int32)
+    nw = _i32()
+    _check(lib().slg_ensemble_plan_windows(g.handle, ap, k, cap, splits.ctypes.data_as(_i32p),
+                                           max_windows, ctypes.byref(nw)))
+    return splits[:nw.value + 1].copy()
+
+
+def slg_ensemble_build_window(g: Graph, s_list, row_begin: int, row_end: int, I, J, O,
+                              cap: int | None = None, digest: bool = False, row_digests=None):
+    """Rows [row_begin, row_end) of every list, back to back in I/J/O.
+
+    Returns (pairs per list, digests per list or None).
+    """
+    a, ap, k = _s_list(s_list)
+    if cap is None:
+        cap = len(I)
+    pairs = np.zeros(max(k, 1), np.int64)
+    dig = np.zeros(max(k, 1), np.uint64)
+    _check(lib().slg_ensemble_build_window(
+        g.handle, ap, k, row_begin, row_end, _ptr(I), _ptr(J), _ptr(O), cap,
+        pairs.ctypes.data_as(_i64p), dig.ctypes.data_as(_u64p) if digest else None,
+        _ptr(row_digests)))
+    return [int(x) for x in pairs[:k]], ([int(x) for x in dig[:k]] if digest else None)
+
+
+def slg_ensemble_build(g: Graph, s_list):
+    """Every list of the ensemble as host arrays: [(I, J, O) per s]."""
+    pairs, _ = slg_ensemble_count(g, s_list)
+    tot = sum(pairs)
+    I = np.zeros(max(tot, 1), np.int32)
+    J = np.zeros(max(tot, 1), np.int32)
+    O = np.zeros(max(tot, 1), np.int32)
+    got, _ = slg_ensemble_build_window(g, s_list, 0, g.m, I, J, O, cap=tot)
+    out, b = [], 0
+    for p in got:
+        out.append((I[b:b + p], J[b:b + p], O[b:b + p]))
+        b += p
+    return out
 
 
 def slg_set_timing(g: Graph, enable: bool = True):

@@ -165,9 +165,9 @@ void ensure_counted(slg_graph* h, int32_t s) {
     slg::Plan& p = h->plan;
     if (p.built && p.s == s && p.counted) return;
     h->timer.mark(0, h->st);
-    slg::plan_build(h->g, s, h->bp, p, h->st);
+    if (!(p.built && p.s == s)) slg::plan_build(h->g, s, h->bp, p, h->st);
     h->timer.mark(1, h->st);
-    slg::run_count(h->g, p, &h->mtimer, h->st);
+    slg::run_count(h->g, p, p.rs, p.icnt, &h->mtimer, h->st);
     h->timer.mark(2, h->st);
     slg::plan_offsets(h->g, p, h->st);  // synchronises
     h->timer.mark(3, h->st);
@@ -177,6 +177,35 @@ void ensure_counted(slg_graph* h, int32_t s) {
         SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[1], h->timer.ev[1], h->timer.ev[2]));
         SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[2], h->timer.ev[2], h->timer.ev[3]));
         h->ms[3] = h->ms[4] = 0;
+    }
+}
+
+// Ensemble for s_list (Algorithm 3): the plan built for s_list[0], every
+// list counted (cached per handle, like ensure_counted).
+void ensure_ensemble(slg_graph* h, const int32_t* s_list, int32_t k) {
+    if (h->g.srow) throw Error{SLG_EINVAL, "an ensemble takes one graph, not a batch"};
+    if (!s_list || k < 1 || k > slg::ENS_MAX)
+        throw Error{SLG_EINVAL, "an ensemble takes 1 to 16 thresholds"};
+    for (int32_t t = 0; t < k; ++t) {
+        if (s_list[t] < 1) throw Error{SLG_EINVAL, "s must be >= 1"};
+        if (t > 0 && s_list[t] <= s_list[t - 1])
+            throw Error{SLG_EINVAL, "ensemble thresholds must be strictly ascending"};
+    }
+    slg::Plan& p = h->plan;
+    if (p.built && p.s == s_list[0] && p.ens.counted && p.ens.k == k &&
+        std::equal(s_list, s_list + k, p.ens.s))
+        return;
+    h->timer.mark(0, h->st);
+    if (!(p.built && p.s == s_list[0])) slg::plan_build(h->g, s_list[0], h->bp, p, h->st);
+    h->timer.mark(1, h->st);
+    slg::ensemble_count(h->g, p, s_list, k, &h->mtimer, h->st);  // synchronises
+    h->timer.mark(2, h->st);
+    h->timer.mark(3, h->st);
+    if (h->timer.on) {
+        SLG_CUDA_TRY(cudaEventSynchronize(h->timer.ev[3]));
+        SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[0], h->timer.ev[0], h->timer.ev[1]));
+        SLG_CUDA_TRY(cudaEventElapsedTime(&h->ms[1], h->timer.ev[1], h->timer.ev[2]));
+        h->ms[2] = h->ms[3] = h->ms[4] = 0;
     }
 }
 
@@ -207,9 +236,11 @@ int64_t fill_window_dev(slg_graph* h, int32_t r0, int32_t r1, int32_t* I, int32_
                         const WindowInfo& w) {
     const int64_t P = w.end - w.base;
     h->timer.mark(3, h->st);
-    slg::run_fill(h->g, h->plan, w.q0, w.q1, I, J, O, P, &h->mtimer, h->st);
+    slg::run_fill(h->g, h->plan, h->plan.rs, h->plan.ioff, w.q0, w.q1, I, J, O, P, &h->mtimer,
+                  h->st);
     h->timer.mark(4, h->st);
-    if (dtot || drows) slg::run_digest(h->g, h->plan, r0, r1, I, J, O, P, dtot, drows, h->st);
+    if (dtot || drows)
+        slg::run_digest(h->plan.rs, h->plan.rowoff, r0, r1, I, J, O, P, dtot, drows, h->st);
     h->timer.mark(5, h->st);
     return P;
 }
@@ -431,11 +462,11 @@ slg_status slg_build(slg_graph* h, int32_t s, int32_t* I, int32_t* J, int32_t* O
     } else {
         // host destination: produce bounded windows through a device staging buffer
         const int64_t stage = (int64_t)1 << 27;  // pairs per window (1.5 GiB staging)
-        const int64_t maxrow = slg::plan_max_row(h->g, h->plan, h->st);
+        const int64_t maxrow = slg::plan_max_row(h->g, h->plan.rowoff, h->st);
         const int64_t cap_w = stage > maxrow ? stage : maxrow;
         const int64_t C = cap_w - maxrow > 0 ? cap_w - maxrow : 1;
         int32_t* splits_d = slg::dalloc<int32_t>((size_t)h->g.m + 1, h->st);
-        const int32_t nw = slg::plan_windows(h->g, h->plan, C, splits_d, h->st);
+        const int32_t nw = slg::plan_windows(h->g, h->plan.rowoff, C, splits_d, h->st);
         std::vector<int32_t> splits((size_t)nw + 1);
         copy_out(splits.data(), splits_d, sizeof(int32_t) * nw, h->st);
         SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
@@ -467,18 +498,143 @@ slg_status slg_plan_windows(slg_graph* h, int32_t s, int64_t cap, int32_t* row_s
     API_BEGIN
     *nwindows = 0;
     ensure_counted(h, s);
-    const int64_t maxrow = slg::plan_max_row(h->g, h->plan, h->st);
+    const int64_t maxrow = slg::plan_max_row(h->g, h->plan.rowoff, h->st);
     if (maxrow > cap) throw Error{SLG_ECAPACITY, "a single row has more pairs than cap"};
     const int64_t C = cap - maxrow > 0 ? cap - maxrow : 1;
-    const int32_t nw = slg::plan_windows(h->g, h->plan, C, nullptr, h->st);
+    const int32_t nw = slg::plan_windows(h->g, h->plan.rowoff, C, nullptr, h->st);
     *nwindows = nw;
     if (nw > max_windows) throw Error{SLG_ECAPACITY, "more windows needed than max_windows"};
     int32_t* splits_d = slg::dalloc<int32_t>((size_t)nw + 1, h->st);
-    slg::plan_windows(h->g, h->plan, C, splits_d, h->st);
+    slg::plan_windows(h->g, h->plan.rowoff, C, splits_d, h->st);
     copy_out(row_splits, splits_d, sizeof(int32_t) * nw, h->st);
     SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
     slg::dfree(splits_d, h->st);
     row_splits[nw] = h->g.m;
+    API_END
+}
+
+slg_status slg_ensemble_count(slg_graph* h, const int32_t* s_list, int32_t k, int64_t* pairs,
+                              int64_t* wedges) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    API_BEGIN
+    ensure_ensemble(h, s_list, k);
+    if (pairs)
+        for (int32_t t = 0; t < k; ++t) pairs[t] = h->plan.ens.pairs[t];
+    if (wedges) *wedges = h->plan.wedges;
+    API_END
+}
+
+slg_status slg_ensemble_row_offsets(slg_graph* h, const int32_t* s_list, int32_t k,
+                                    int64_t* rowoff) {
+    if (!h || !rowoff) return fail(SLG_EINVAL, "NULL argument");
+    API_BEGIN
+    ensure_ensemble(h, s_list, k);
+    copy_out(rowoff, h->plan.ens.rowoff, sizeof(int64_t) * (size_t)k * ((size_t)h->g.m + 1),
+             h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    API_END
+}
+
+slg_status slg_ensemble_plan_windows(slg_graph* h, const int32_t* s_list, int32_t k, int64_t cap,
+                                     int32_t* row_splits, int32_t max_windows,
+                                     int32_t* nwindows) {
+    if (!h || !row_splits || !nwindows) return fail(SLG_EINVAL, "NULL argument");
+    if (cap < 1) return fail(SLG_EINVAL, "cap must be >= 1");
+    API_BEGIN
+    *nwindows = 0;
+    ensure_ensemble(h, s_list, k);
+    const int64_t* tot = h->plan.ens.rowtot;
+    const int64_t maxrow = slg::plan_max_row(h->g, tot, h->st);
+    if (maxrow > cap) throw Error{SLG_ECAPACITY, "a single row has more pairs than cap"};
+    const int64_t C = cap - maxrow > 0 ? cap - maxrow : 1;
+    const int32_t nw = slg::plan_windows(h->g, tot, C, nullptr, h->st);
+    *nwindows = nw;
+    if (nw > max_windows) throw Error{SLG_ECAPACITY, "more windows needed than max_windows"};
+    int32_t* splits_d = slg::dalloc<int32_t>((size_t)nw + 1, h->st);
+    slg::plan_windows(h->g, tot, C, splits_d, h->st);
+    copy_out(row_splits, splits_d, sizeof(int32_t) * nw, h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    slg::dfree(splits_d, h->st);
+    row_splits[nw] = h->g.m;
+    API_END
+}
+
+slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_t k, int32_t r0,
+                                     int32_t r1, int32_t* I, int32_t* J, int32_t* O, int64_t cap,
+                                     int64_t* pairs, uint64_t* digests, uint64_t* row_digests) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (r0 < 0 || r1 < r0 || r1 > h->g.m) return fail(SLG_EINVAL, "bad row range");
+    API_BEGIN
+    ensure_ensemble(h, s_list, k);
+    slg::Plan& p = h->plan;
+    const int64_t m1 = (int64_t)h->g.m + 1, ni = p.nitems;
+    // slice of each list: rowoff_t[r0] .. rowoff_t[r1]; items row_item[r0] .. row_item[r1]
+    int64_t base[slg::ENS_MAX], end[slg::ENS_MAX], seg[slg::ENS_MAX + 1];
+    int32_t q0 = 0, q1 = 0;
+    for (int32_t t = 0; t < k; ++t) {
+        copy_out(&base[t], p.ens.rowoff + t * m1 + r0, sizeof(int64_t), h->st);
+        copy_out(&end[t], p.ens.rowoff + t * m1 + r1, sizeof(int64_t), h->st);
+    }
+    copy_out(&q0, p.row_item + r0, sizeof(int32_t), h->st);
+    copy_out(&q1, p.row_item + r1, sizeof(int32_t), h->st);
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    seg[0] = 0;
+    for (int32_t t = 0; t < k; ++t) {
+        seg[t + 1] = seg[t] + (end[t] - base[t]);
+        if (pairs) pairs[t] = end[t] - base[t];
+    }
+    const int64_t P = seg[k];
+    if (P > cap) throw Error{SLG_ECAPACITY, "output buffer too small for the window"};
+    if (P > 0 && (!I || !J || !O)) throw Error{SLG_EINVAL, "NULL output array"};
+    const bool dev = P == 0 || (slg::is_device_ptr(I) && slg::is_device_ptr(J) &&
+                                slg::is_device_ptr(O));
+    int32_t *dI = I, *dJ = J, *dO = O;
+    if (!dev) {
+        dI = slg::dalloc<int32_t>(P, h->st);
+        dJ = slg::dalloc<int32_t>(P, h->st);
+        dO = slg::dalloc<int32_t>(P, h->st);
+    }
+    const int32_t nr = r1 - r0;
+    unsigned long long* dd = nullptr;  // per list: total, then one entry per row
+    if (digests || row_digests) {
+        const size_t nd = (size_t)k * ((size_t)nr + 1);
+        dd = slg::dalloc<unsigned long long>(nd, h->st);
+        SLG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(unsigned long long) * nd, h->st));
+    }
+    h->timer.mark(3, h->st);
+    for (int32_t t = 0; t < k; ++t) {
+        const int64_t Pt = seg[t + 1] - seg[t];
+        slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
+                      dI + seg[t], dJ + seg[t], dO + seg[t], Pt, &h->mtimer, h->st);
+    }
+    h->timer.mark(4, h->st);
+    if (dd) {
+        for (int32_t t = 0; t < k; ++t) {
+            unsigned long long* dt = dd + (size_t)t * ((size_t)nr + 1);
+            slg::run_digest(p.rs_for(p.ens.s[t]), p.ens.rowoff + t * m1, r0, r1, dI + seg[t],
+                            dJ + seg[t], dO + seg[t], seg[t + 1] - seg[t], dt,
+                            row_digests ? dt + 1 : nullptr, h->st);
+        }
+    }
+    h->timer.mark(5, h->st);
+    if (!dev) {
+        copy_out(I, dI, sizeof(int32_t) * P, h->st);
+        copy_out(J, dJ, sizeof(int32_t) * P, h->st);
+        copy_out(O, dO, sizeof(int32_t) * P, h->st);
+    }
+    for (int32_t t = 0; dd && t < k; ++t) {
+        const unsigned long long* dt = dd + (size_t)t * ((size_t)nr + 1);
+        if (digests) copy_out(digests + t, dt, sizeof(uint64_t), h->st);
+        if (row_digests) copy_out(row_digests + (size_t)t * nr, dt + 1, sizeof(uint64_t) * nr, h->st);
+    }
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
+    finish_timing(h, P);
+    if (!dev) {
+        slg::dfree(dI, h->st);
+        slg::dfree(dJ, h->st);
+        slg::dfree(dO, h->st);
+    }
+    slg::dfree(dd, h->st);
     API_END
 }
 

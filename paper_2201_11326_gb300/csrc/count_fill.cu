@@ -144,6 +144,7 @@ k_warp_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     const int64_t nw = (int64_t)gridDim.x * WARP_CTA_WARPS;
     for (int64_t pos = lo + (int64_t)blockIdx.x * WARP_CTA_WARPS + w; pos < hi; pos += nw) {
         const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) continue;  // nothing to write
         const Item it = items[q];
         const int32_t i = it.row;
         const int32_t s = rs.s_of(i);
@@ -256,6 +257,10 @@ k_block_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t pos = sh_pos;
         if (pos >= hi) break;
         const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) {  // nothing to write (same in every thread)
+            __syncthreads();  // everyone has read sh_pos before thread 0 rewrites it
+            continue;
+        }
         const Item it = items[q];
         const int32_t i = it.row;
         const int32_t s = rs.s_of(i);
@@ -455,6 +460,10 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int32_t pos = sh_pos;
         if (pos >= hi) break;
         const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) {  // nothing to write (same in every thread)
+            __syncthreads();  // everyone has read sh_pos before thread 0 rewrites it
+            continue;
+        }
         const Item it = items[q];
         const int32_t i = it.row;
         const int32_t s = rs.s_of(i);
@@ -625,6 +634,7 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         pos = __shfl_sync(0xffffffffu, pos, 0);
         if (pos >= hi) break;
         const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) continue;  // nothing to write
         const Item it = items[q];
         const int32_t i = it.row;
         const int32_t ib = rs.base_of(i);
@@ -963,9 +973,9 @@ Occupancy& occupancy() {
 }
 
 template <bool FILL>
-void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
-                  int32_t* icnt, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
-                  int32_t* scratch, ModeTimer* mt, cudaStream_t st) {
+void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
+                  int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
+                  int64_t limit, int32_t* scratch, ModeTimer* mt, cudaStream_t st) {
     // scratch: NMODES queue heads, then the error flag
     Occupancy& oc = occupancy();
     int32_t* queue = scratch;
@@ -980,7 +990,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_WARP, 0);
         k_warp_items<FILL><<<oc.warp_ctas, WARP_CTA_WARPS * 32, 0, st>>>(
             p.items, p.mode_list[MODE_WARP], p.mode_rank[MODE_WARP], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O, limit, err);
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_WARP, 1);
     }
@@ -989,7 +999,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_BLOCK, 0);
         k_block_items<FILL><<<oc.block_ctas, BLOCK_THREADS, 0, st>>>(
             p.items, p.mode_list[MODE_BLOCK], p.mode_rank[MODE_BLOCK], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O, queue + MODE_BLOCK, limit, err);
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue + MODE_BLOCK, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_BLOCK, 1);
     }
@@ -998,7 +1008,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         tick(MODE_DENSE, 0);
         k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
             p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O,
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O,
             queue + MODE_DENSE, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_DENSE, 1);
@@ -1009,7 +1019,7 @@ void launch_items(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t ite
         k_wdense_items<FILL><<<FILL ? oc.wdense_fill_ctas : oc.wdense_ctas, WD_WARPS * 32,
                                FILL ? WD_SMEM_FILL : WD_SMEM, st>>>(
             p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, p.rs, icnt, p.ioff, I, J, O,
+            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O,
             queue + MODE_WDENSE, limit, err);
         SLG_LAUNCH_CHECK();
         tick(MODE_WDENSE, 1);
@@ -1048,33 +1058,34 @@ void check_scratch(int32_t* s, cudaStream_t st, const char* what) {
 
 }  // namespace
 
-void run_count(const GraphDev& g, Plan& p, ModeTimer* mt, cudaStream_t st) {
+void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
+               cudaStream_t st) {
     int32_t* sc = new_scratch(st);
-    launch_items<false>(g, p, 0, (int32_t)p.nitems, p.icnt, nullptr, nullptr, nullptr, 0, sc, mt,
-                        st);
+    launch_items<false>(g, p, rs, 0, (int32_t)p.nitems, icnt, nullptr, nullptr, nullptr, nullptr,
+                        0, sc, mt, st);
     check_scratch(sc, st, "counting pass");
 }
 
-void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
-              int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt, cudaStream_t st) {
+void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
+              int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
+              cudaStream_t st) {
     if (item_hi <= item_lo) return;
     int32_t* sc = new_scratch(st);
-    launch_items<true>(g, p, item_lo, item_hi, nullptr, I, J, O, limit, sc, mt, st);
+    launch_items<true>(g, p, rs, item_lo, item_hi, nullptr, ioff, I, J, O, limit, sc, mt, st);
     check_scratch(sc, st, "fill pass");
 }
 
-void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const int32_t* I,
+void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,
                 unsigned long long* rows_dev, cudaStream_t st) {
-    (void)g;
     if (P <= 0) return;
     int64_t base = 0;
-    SLG_CUDA_TRY(cudaMemcpyAsync(&base, p.rowoff + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&base, rowoff + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     int32_t* sc = new_scratch(st);
     int64_t blocks = (P + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     SLG_CUDA_TRY(cudaStreamSynchronize(st));
-    k_digest<<<(int)blocks, 256, 0, st>>>(I, J, O, P, base, p.rowoff, r0, r1, p.rs, total_dev,
+    k_digest<<<(int)blocks, 256, 0, st>>>(I, J, O, P, base, rowoff, r0, r1, rs, total_dev,
                                           rows_dev, sc + NMODES);
     SLG_LAUNCH_CHECK();
     check_scratch(sc, st, "digest");

@@ -241,6 +241,17 @@ __global__ void k_mode_stats(const int32_t* __restrict__ row_item, const Item* _
     }
 }
 
+// rowtot[r] = sum over the k lists of rowoff[t][r] (cumulative, so the sum of
+// the lists' row counts before row r)
+__global__ void k_sum_rows(const int64_t* __restrict__ rowoff, int32_t k, int32_t m,
+                           int64_t* __restrict__ rowtot) {
+    GRID_STRIDE(r, (int64_t)m + 1) {
+        int64_t acc = 0;
+        for (int32_t t = 0; t < k; ++t) acc += rowoff[(int64_t)t * ((int64_t)m + 1) + r];
+        rowtot[r] = acc;
+    }
+}
+
 template <typename T>
 T* dalloc(size_t count, cudaStream_t st) {
     T* p = nullptr;
@@ -256,7 +267,17 @@ void dfree(T*& p, cudaStream_t st) {
 
 }  // namespace
 
+void Plan::release_ensemble(cudaStream_t st) {
+    dfree(ens.icnt, st);
+    dfree(ens.ioff, st);
+    dfree(ens.rowoff, st);
+    dfree(ens.rowtot, st);
+    ens.k = 0;
+    ens.counted = false;
+}
+
 void Plan::release(cudaStream_t st) {
+    release_ensemble(st);
     if (idxTs_owned) dfree(idxTs, st);
     idxTs = nullptr;
     dfree(ks, st);
@@ -402,6 +423,35 @@ void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st) {
     p.counted = true;
 }
 
+void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, ModeTimer* mt,
+                    cudaStream_t st) {
+    p.release_ensemble(st);
+    Plan::Ensemble& e = p.ens;
+    e.k = k;
+    for (int32_t t = 0; t < k; ++t) e.s[t] = s[t];
+    const int64_t ni = p.nitems, m1 = (int64_t)g.m + 1;
+    e.icnt = dalloc<int32_t>((size_t)(k * ni), st);
+    e.ioff = dalloc<int64_t>((size_t)(k * (ni + 1)), st);
+    e.rowoff = dalloc<int64_t>((size_t)(k * m1), st);
+    e.rowtot = dalloc<int64_t>((size_t)m1, st);
+    const int T = 256;
+    for (int32_t t = 0; t < k; ++t) {
+        // the plan's work (pruned at s[0] <= s[t]) with threshold s[t]: a pair
+        // with overlap >= s[t] has both sizes >= s[t] >= s[0], so it is there
+        run_count(g, p, p.rs_for(s[t]), e.icnt + t * ni, mt, st);
+        scan_i32_to_i64(e.icnt + t * ni, e.ioff + t * (ni + 1), ni, st);
+        k_rowoff<<<grid_for(m1, T), T, 0, st>>>(p.row_item, e.ioff + t * (ni + 1), g.m,
+                                                e.rowoff + t * m1);
+        SLG_LAUNCH_CHECK();
+        SLG_CUDA_TRY(cudaMemcpyAsync(&e.pairs[t], e.ioff + t * (ni + 1) + ni, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    k_sum_rows<<<grid_for(m1, T), T, 0, st>>>(e.rowoff, k, g.m, e.rowtot);
+    SLG_LAUNCH_CHECK();
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    e.counted = true;
+}
+
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st) {
     unsigned long long* d = dalloc<unsigned long long>(NMODES * 4, st);
     SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NMODES * 4, st));
@@ -418,11 +468,11 @@ void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], c
         for (int c = 0; c < 4; ++c) out[k][c] = (int64_t)h[k * 4 + c];
 }
 
-int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st) {
+int64_t plan_max_row(const GraphDev& g, const int64_t* rowoff, cudaStream_t st) {
     unsigned long long* d = dalloc<unsigned long long>(1, st);
     SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
     if (g.m) {
-        k_max_row<<<grid_for(g.m, 256), 256, 0, st>>>(p.rowoff, g.m, d);
+        k_max_row<<<grid_for(g.m, 256), 256, 0, st>>>(rowoff, g.m, d);
         SLG_LAUNCH_CHECK();
     }
     unsigned long long h = 0;
@@ -432,14 +482,14 @@ int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st) {
     return (int64_t)h;
 }
 
-int32_t plan_windows(const GraphDev& g, const Plan& p, int64_t C, int32_t* splits_dev,
+int32_t plan_windows(const GraphDev& g, const int64_t* rowoff, int64_t C, int32_t* splits_dev,
                      cudaStream_t st) {
     const int T = 256;
     const int32_t m = g.m;
     int32_t* flags = dalloc<int32_t>(m, st);
     int32_t* rank = dalloc<int32_t>((size_t)m + 1, st);
     if (m) {
-        k_window_flags<<<grid_for(m, T), T, 0, st>>>(p.rowoff, m, C, flags);
+        k_window_flags<<<grid_for(m, T), T, 0, st>>>(rowoff, m, C, flags);
         SLG_LAUNCH_CHECK();
     }
     scan_i32_to_i32(flags, rank, m, st);

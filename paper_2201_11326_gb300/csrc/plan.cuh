@@ -80,24 +80,49 @@ struct Plan {
     int64_t pairs = 0;
     int64_t wedges = 0;
 
+    // Ensemble (Algorithm 3, Section III-D): thresholds s[0] < ... < s[k-1]
+    // counted over this plan, which is built for s[0]. List t of a row holds
+    // its partners with overlap >= s[t]; per list, counts and offsets as above.
+    struct Ensemble {
+        int32_t k = 0;
+        int32_t s[ENS_MAX] = {};
+        int32_t* icnt = nullptr;    // [k][nitems]
+        int64_t* ioff = nullptr;    // [k][nitems+1]
+        int64_t* rowoff = nullptr;  // [k][m+1]
+        int64_t* rowtot = nullptr;  // [m+1] sum of the k row offsets (window planning)
+        int64_t pairs[ENS_MAX] = {};
+        bool counted = false;
+    } ens;
+
+    RowS rs_for(int32_t s_t) const { return RowS{rs.srow, rs.rbase, s_t}; }
+    void release_ensemble(cudaStream_t st);
     void release(cudaStream_t st);
 };
 
 void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st);
 void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st);
-int64_t plan_max_row(const GraphDev& g, const Plan& p, cudaStream_t st);
-int32_t plan_windows(const GraphDev& g, const Plan& p, int64_t C, int32_t* splits_dev,
+// Largest row total and window splits over cumulative row offsets rowoff[m+1]
+// (a single list's or the ensemble's sum).
+int64_t plan_max_row(const GraphDev& g, const int64_t* rowoff, cudaStream_t st);
+int32_t plan_windows(const GraphDev& g, const int64_t* rowoff, int64_t C, int32_t* splits_dev,
                      cudaStream_t st);
+// Counts and offsets of every list of an ensemble (the plan is built for s[0]).
+void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, ModeTimer* mt,
+                    cudaStream_t st);
 
 // Counting and filling (count_fill.cu). Items [item_lo, item_hi) are filled
 // into I/J/O at position ioff[q] - ioff[item_lo].
-void run_count(const GraphDev& g, Plan& p, ModeTimer* mt, cudaStream_t st);
-void run_fill(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi, int32_t* I,
-              int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt, cudaStream_t st);
+// `rs` carries the threshold (the plan's own, or one of an ensemble's), icnt
+// and ioff the matching per-item counts and offsets.
+void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
+               cudaStream_t st);
+void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
+              int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
+              cudaStream_t st);
 // Per-handler totals over rows: rows, wedges, incidences, pairs (needs counts).
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
-void run_digest(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, const int32_t* I,
+void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,
                 unsigned long long* rows_dev, cudaStream_t st);
 

@@ -117,6 +117,7 @@ constexpr int WD_TILE = 4096;             // j per warp tile (8-bit counters, 4 
 constexpr int WD_ITEM = 8192;             // j per MODE_WDENSE item = WD_ITEM * dense_item_tiles
 constexpr int WD_MAXR = 32;               // non-hub wedge ranges a MODE_WDENSE row may have
 constexpr int DENSE_MAX_SIZE = 65535;     // |e_i| bound for 16-bit counters
+constexpr int ENS_MAX = 16;               // thresholds in one ensemble (Algorithm 3)
 
 // --------------------------------------------------------- device helpers
 
