@@ -8,7 +8,7 @@ Zipf(1.7) vertex popularity, seed 0) with the sweep s = 1..8.
 One step = the whole hot path on that input, resident in HBM:
   slg_load from device memory (validate, transpose), then for every s:
   counting pass (prune, per-row work, binning, count, scan), window plan and
-  the fill of every window of at most 2^31 pairs into a reused device window.
+  the fill of every window of at most 2^33 pairs into a reused device window.
 Metric: wedges per second, W = sum_s W_s with W_s = sum_v C(d_s(v), 2);
 s-edges per second (sum_s |L_s| / time) is reported beside it.
 
@@ -38,7 +38,7 @@ import synth  # noqa: E402
 WORKLOAD = ("medium: m=1,000,000 hyperedges, n=500,000 vertices, sizes log-normal(1.8,1.0) "
             "clipped [2,5000], vertex popularity Zipf(1.7), seed 0; s=1..8 sweep")
 METRIC = "s-line wedges/s (medium hypergraph, s=1..8, bit-exact)"
-WINDOW = 1 << 31          # default pairs per output window (24 GiB of I/J/O)
+WINDOW = 1 << 33          # default pairs per output window (96 GiB of I/J/O)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--cpu-rows", type=int, default=600, help="rows in the CPU-oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--window", type=int, default=1 << 31, help="pairs per output window")
+    ap.add_argument("--window", type=int, default=WINDOW, help="pairs per output window")
     ap.add_argument("--workload", choices=["medium", "batch", "serve", "ensemble"],
                     default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
@@ -266,7 +266,10 @@ def bench_ours(args):
         cands.append(("fill", k, cb + 12 * pairs_mode[k], ms_tot[1][k] / args.steps,
                       ln_tot[1][k] / args.steps))
     dom = max(cands, key=lambda c: c[3])
-    kname = f"k_{names[dom[1]]}_items<{'true' if dom[0] == 'fill' else 'false'}>"
+    # the kernel as ncu names it (dense handlers carry a second, ensemble flag)
+    fill_flag = "1" if dom[0] == "fill" else "0"
+    kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>" if names[dom[1]] in ("dense", "wdense")
+             else f"k_{names[dom[1]]}_items<{fill_flag}>")
     achieved = dom[2] / (dom[3] / 1e3) / 1e9 if dom[3] > 0 else 0.0
     traffic = profiled_traffic(kname, dom[2] / max(dom[4], 1))
     # the output writes alone: 12 B per pair of the dominant kernel's handler
@@ -509,16 +512,28 @@ def bench_batch(args):
 
 # ---------------------------------------------------------------- ensemble
 
-def run_ensemble(slg, g, s_list, bufs):
-    """Algorithm 3 on a loaded graph: one plan for min(s_list), every list counted,
-    then every window of all lists (the lists of a window back to back)."""
+def run_ensemble(slg, g, s_list, bufs, strategy="fused"):
+    """Algorithm 3 on a loaded graph: one plan for min(s_list) and one counting
+    pass for every list, then the fills. "fused": windows hold every list of
+    their rows and the dense handlers write all lists in one pass; "per_list":
+    each list's own windows, filled from the shared plan one list at a time."""
     I, J, O = bufs
     cap = I.numel()
     pairs, _ = slg.slg_ensemble_count(g, s_list)
-    splits = slg.slg_ensemble_plan_windows(g, s_list, cap)
-    for r0, r1 in zip(splits[:-1], splits[1:]):
-        slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap)
+    if strategy == "fused":
+        splits = slg.slg_ensemble_plan_windows(g, s_list, cap)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap)
+    else:
+        for t in range(len(s_list)):
+            splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap, which=t)
     return pairs
+
+
+ENSEMBLE_STRATEGY = "per_list"   # the faster fill strategy on the medium workload
+OTHER_STRATEGY = "fused"
 
 
 def bench_ensemble(args):
@@ -547,14 +562,16 @@ def bench_ensemble(args):
     W = sum(w for _, w in counts.values())
     P = sum(p for p, _ in counts.values())
 
-    def ens():
-        g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
-        slg.slg_set_timing(g, True)
-        pairs = run_ensemble(slg, g, s_list, (I, J, O))
-        ks = slg.slg_kernel_stats(g)
-        g.free()
-        assert pairs == [counts[s][0] for s in s_list]
-        return ks
+    def ens(strategy):
+        def run():
+            g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+            slg.slg_set_timing(g, True)
+            pairs = run_ensemble(slg, g, s_list, (I, J, O), strategy)
+            ks = slg.slg_kernel_stats(g)
+            g.free()
+            assert pairs == [counts[s][0] for s in s_list]
+            return ks
+        return run
 
     def sweep():
         g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
@@ -580,7 +597,9 @@ def bench_ensemble(args):
     names = list(slg.MODE_NAMES)
     res = {}
     clocks = None
-    for name, fn in (("ensemble", ens), ("per_s", sweep)):
+    for name, fn in (("ensemble", ens(ENSEMBLE_STRATEGY)), ("ensemble_" + OTHER_STRATEGY,
+                                                           ens(OTHER_STRATEGY)),
+                     ("per_s", sweep)):
         for _ in range(args.warmup):
             timed(fn)
         if name == "ensemble":
@@ -610,7 +629,8 @@ def bench_ensemble(args):
         "config": {"workload": WORKLOAD, "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list,
                    "window_pairs": args.window, "wedges": W, "pairs": P,
                    "l2": "flushed before each step (512 MiB device write); inputs resident"},
-        "ensemble": res["ensemble"], "per_s": res["per_s"],
+        "strategy": ENSEMBLE_STRATEGY, "ensemble": res["ensemble"],
+        "ensemble_" + OTHER_STRATEGY: res["ensemble_" + OTHER_STRATEGY], "per_s": res["per_s"],
         "speedup_vs_per_s": res["ensemble"]["wedges_per_s"] / res["per_s"]["wedges_per_s"],
         "clocks": clk,
     }

@@ -182,8 +182,8 @@ slg_status slg_plan_windows(slg_graph* g, int32_t s, int64_t cap, int32_t* row_s
  * for several thresholds s_list[0] < s_list[1] < ... < s_list[k-1]. Algorithm
  * 3 counts the overlaps once (pruned by the smallest s) and then filters the
  * counted pairs once per threshold. Here one plan, pruned by s_list[0], serves
- * every list: the counting pass runs over it once per threshold, and the fill
- * writes every list of a row window from it.
+ * every list: one counting pass counts every list, and the fills write either
+ * every list of a row window in one pass or one list at a time.
  *
  * Every ensemble call takes the same (s_list, k), with 1 <= k <=
  * SLG_ENSEMBLE_MAX and s_list strictly ascending, s_list[0] >= 1. The counts
@@ -206,27 +206,35 @@ slg_status slg_ensemble_row_offsets(slg_graph* g, const int32_t* s_list, int32_t
                                     int64_t* rowoff);
 
 /*
- * slg_ensemble_plan_windows -- as slg_plan_windows, with a window's size being
- * the sum of its pairs over the k lists.
+ * slg_ensemble_plan_windows -- as slg_plan_windows for the lists selected by
+ * `which`: SLG_ENSEMBLE_ALL (-1) sizes a window by the sum of its pairs over
+ * the k lists, t in [0, k) by list t alone.
  */
-slg_status slg_ensemble_plan_windows(slg_graph* g, const int32_t* s_list, int32_t k, int64_t cap,
-                                     int32_t* row_splits, int32_t max_windows,
+#define SLG_ENSEMBLE_ALL (-1)
+slg_status slg_ensemble_plan_windows(slg_graph* g, const int32_t* s_list, int32_t k, int32_t which,
+                                     int64_t cap, int32_t* row_splits, int32_t max_windows,
                                      int32_t* nwindows);
 
 /*
- * slg_ensemble_build_window -- the pairs of rows [row_begin, row_end) of every
- * list. I, J, O (cap entries each, host or device, all of one kind) receive
- * the lists back to back: list t occupies positions seg_t .. seg_t + pairs[t]
- * - 1, seg_t = pairs[0] + ... + pairs[t-1]. Each list is the contiguous slice
- * of its canonical list (sorted by (i, j)).
+ * slg_ensemble_build_window -- the pairs of rows [row_begin, row_end).
  *
- *   pairs       : k entries, receives each list's pair count for the window.
- *   digests     : NULL or k entries, each list's digest as in slg_build_window.
- *   row_digests : NULL or k*(row_end - row_begin) entries, list-major.
- * Errors: SLG_ECAPACITY when the k lists together exceed cap (pairs is set,
- * nothing is written); SLG_EINVAL as above or for a bad range.
+ * which = SLG_ENSEMBLE_ALL: every list, back to back in I, J, O (cap entries
+ * each, host or device, all of one kind): list t occupies positions seg_t ..
+ * seg_t + pairs[t] - 1, seg_t = pairs[0] + ... + pairs[t-1]. The dense
+ * handlers write all lists in one pass over the overlaps.
+ * which = t in [0, k): list t alone, at positions 0 .. pairs[0] - 1.
+ * Each list is the contiguous slice of its canonical list (sorted by (i, j)).
+ *
+ *   pairs       : k entries (ALL) or 1 entry (one list): the pair counts.
+ *   digests     : NULL or as many entries as pairs: digests as in
+ *                 slg_build_window.
+ *   row_digests : NULL or (entries of pairs) * (row_end - row_begin) entries,
+ *                 list-major.
+ * Errors: SLG_ECAPACITY when the selected lists together exceed cap (pairs is
+ * set, nothing is written); SLG_EINVAL as above, for a bad range or a bad
+ * `which`.
  */
-slg_status slg_ensemble_build_window(slg_graph* g, const int32_t* s_list, int32_t k,
+slg_status slg_ensemble_build_window(slg_graph* g, const int32_t* s_list, int32_t k, int32_t which,
                                      int32_t row_begin, int32_t row_end, int32_t* I, int32_t* J,
                                      int32_t* O, int64_t cap, int64_t* pairs, uint64_t* digests,
                                      uint64_t* row_digests);

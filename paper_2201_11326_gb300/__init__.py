@@ -24,7 +24,7 @@ __all__ = [
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
-    "slg_ensemble_build", "ENSEMBLE_MAX", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -96,9 +96,9 @@ _SIGS = {
     "slg_plan_windows": (_i32, [_vp, _i32, _i64, _i32p, _i32, _i32p]),
     "slg_ensemble_count": (_i32, [_vp, _i32p, _i32, _i64p, _i64p]),
     "slg_ensemble_row_offsets": (_i32, [_vp, _i32p, _i32, _vp]),
-    "slg_ensemble_plan_windows": (_i32, [_vp, _i32p, _i32, _i64, _i32p, _i32, _i32p]),
-    "slg_ensemble_build_window": (_i32, [_vp, _i32p, _i32, _i32, _i32, _vp, _vp, _vp, _i64,
-                                         _i64p, _u64p, _vp]),
+    "slg_ensemble_plan_windows": (_i32, [_vp, _i32p, _i32, _i32, _i64, _i32p, _i32, _i32p]),
+    "slg_ensemble_build_window": (_i32, [_vp, _i32p, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                         _i64, _i64p, _u64p, _vp]),
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32]),
@@ -328,32 +328,38 @@ def slg_ensemble_row_offsets(g: Graph, s_list, out=None):
     return out
 
 
-def slg_ensemble_plan_windows(g: Graph, s_list, cap: int,
+ENSEMBLE_ALL = -1
+
+
+def slg_ensemble_plan_windows(g: Graph, s_list, cap: int, which: int = ENSEMBLE_ALL,
                               max_windows: int = 1 << 20) -> np.ndarray:
+    """Row splits for windows of at most cap pairs: all lists together (which = -1)
+    or list `which` alone."""
     a, ap, k = _s_list(s_list)
     splits = np.zeros(max_windows + 1, np.int32)
     nw = _i32()
-    _check(lib().slg_ensemble_plan_windows(g.handle, ap, k, cap, splits.ctypes.data_as(_i32p),
-                                           max_windows, ctypes.byref(nw)))
+    _check(lib().slg_ensemble_plan_windows(g.handle, ap, k, which, cap,
+                                           splits.ctypes.data_as(_i32p), max_windows,
+                                           ctypes.byref(nw)))
     return splits[:nw.value + 1].copy()
 
 
 def slg_ensemble_build_window(g: Graph, s_list, row_begin: int, row_end: int, I, J, O,
-                              cap: int | None = None, digest: bool = False, row_digests=None):
-    """Rows [row_begin, row_end) of every list, back to back in I/J/O.
-
-    Returns (pairs per list, digests per list or None).
-    """
+                              cap: int | None = None, digest: bool = False, row_digests=None,
+                              which: int = ENSEMBLE_ALL):
+    """Rows [row_begin, row_end) of every list back to back (which = -1) or of list
+    `which` alone. Returns (pairs per selected list, digests or None)."""
     a, ap, k = _s_list(s_list)
     if cap is None:
         cap = len(I)
-    pairs = np.zeros(max(k, 1), np.int64)
-    dig = np.zeros(max(k, 1), np.uint64)
+    nl = k if which < 0 else 1
+    pairs = np.zeros(max(nl, 1), np.int64)
+    dig = np.zeros(max(nl, 1), np.uint64)
     _check(lib().slg_ensemble_build_window(
-        g.handle, ap, k, row_begin, row_end, _ptr(I), _ptr(J), _ptr(O), cap,
+        g.handle, ap, k, which, row_begin, row_end, _ptr(I), _ptr(J), _ptr(O), cap,
         pairs.ctypes.data_as(_i64p), dig.ctypes.data_as(_u64p) if digest else None,
         _ptr(row_digests)))
-    return [int(x) for x in pairs[:k]], ([int(x) for x in dig[:k]] if digest else None)
+    return [int(x) for x in pairs[:nl]], ([int(x) for x in dig[:nl]] if digest else None)
 
 
 def slg_ensemble_build(g: Graph, s_list):
@@ -529,7 +535,7 @@ def slg_scan_counts_noalloc(counts, offsets, stream=None):
 
 
 def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,
-                 dense_min_density: int = 64, dense_item_tiles: int = 16,
+                 dense_min_density: int = 64, dense_item_tiles: int = 4,
                  wdense_max_ranges: int = 32):
     _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
                               dense_item_tiles, wdense_max_ranges))

@@ -75,7 +75,7 @@ BinParams default_bins() {
     b.warp_max_wedges = 128;
     b.block_item_wedges = 1024;
     b.dense_min_density = 64;  // dense when W_i >= span / 4
-    b.dense_item_tiles = 16;
+    b.dense_item_tiles = 4;
     b.wdense_max_ranges = WD_MAXR;
     return b;
 }
@@ -535,15 +535,17 @@ slg_status slg_ensemble_row_offsets(slg_graph* h, const int32_t* s_list, int32_t
     API_END
 }
 
-slg_status slg_ensemble_plan_windows(slg_graph* h, const int32_t* s_list, int32_t k, int64_t cap,
-                                     int32_t* row_splits, int32_t max_windows,
-                                     int32_t* nwindows) {
+slg_status slg_ensemble_plan_windows(slg_graph* h, const int32_t* s_list, int32_t k,
+                                     int32_t which, int64_t cap, int32_t* row_splits,
+                                     int32_t max_windows, int32_t* nwindows) {
     if (!h || !row_splits || !nwindows) return fail(SLG_EINVAL, "NULL argument");
     if (cap < 1) return fail(SLG_EINVAL, "cap must be >= 1");
+    if (which < -1 || which >= k) return fail(SLG_EINVAL, "bad list selector");
     API_BEGIN
     *nwindows = 0;
     ensure_ensemble(h, s_list, k);
-    const int64_t* tot = h->plan.ens.rowtot;
+    const int64_t* tot = which < 0 ? h->plan.ens.rowtot
+                                   : h->plan.ens.rowoff + (int64_t)which * ((int64_t)h->g.m + 1);
     const int64_t maxrow = slg::plan_max_row(h->g, tot, h->st);
     if (maxrow > cap) throw Error{SLG_ECAPACITY, "a single row has more pairs than cap"};
     const int64_t C = cap - maxrow > 0 ? cap - maxrow : 1;
@@ -559,31 +561,35 @@ slg_status slg_ensemble_plan_windows(slg_graph* h, const int32_t* s_list, int32_
     API_END
 }
 
-slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_t k, int32_t r0,
-                                     int32_t r1, int32_t* I, int32_t* J, int32_t* O, int64_t cap,
-                                     int64_t* pairs, uint64_t* digests, uint64_t* row_digests) {
+slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_t k,
+                                     int32_t which, int32_t r0, int32_t r1, int32_t* I,
+                                     int32_t* J, int32_t* O, int64_t cap, int64_t* pairs,
+                                     uint64_t* digests, uint64_t* row_digests) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     if (r0 < 0 || r1 < r0 || r1 > h->g.m) return fail(SLG_EINVAL, "bad row range");
+    if (which < -1 || which >= k) return fail(SLG_EINVAL, "bad list selector");
     API_BEGIN
     ensure_ensemble(h, s_list, k);
     slg::Plan& p = h->plan;
     const int64_t m1 = (int64_t)h->g.m + 1, ni = p.nitems;
-    // slice of each list: rowoff_t[r0] .. rowoff_t[r1]; items row_item[r0] .. row_item[r1]
+    // selected lists t0 .. t1-1; slice of each: rowoff_t[r0] .. rowoff_t[r1];
+    // items row_item[r0] .. row_item[r1]
+    const int32_t t0 = which < 0 ? 0 : which, t1 = which < 0 ? k : which + 1, nl = t1 - t0;
     int64_t base[slg::ENS_MAX], end[slg::ENS_MAX], seg[slg::ENS_MAX + 1];
     int32_t q0 = 0, q1 = 0;
-    for (int32_t t = 0; t < k; ++t) {
+    for (int32_t t = t0; t < t1; ++t) {
         copy_out(&base[t], p.ens.rowoff + t * m1 + r0, sizeof(int64_t), h->st);
         copy_out(&end[t], p.ens.rowoff + t * m1 + r1, sizeof(int64_t), h->st);
     }
     copy_out(&q0, p.row_item + r0, sizeof(int32_t), h->st);
     copy_out(&q1, p.row_item + r1, sizeof(int32_t), h->st);
     SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
-    seg[0] = 0;
-    for (int32_t t = 0; t < k; ++t) {
-        seg[t + 1] = seg[t] + (end[t] - base[t]);
-        if (pairs) pairs[t] = end[t] - base[t];
+    seg[0] = 0;  // seg is indexed by position among the selected lists
+    for (int32_t t = t0; t < t1; ++t) {
+        seg[t - t0 + 1] = seg[t - t0] + (end[t] - base[t]);
+        if (pairs) pairs[t - t0] = end[t] - base[t];
     }
-    const int64_t P = seg[k];
+    const int64_t P = seg[nl];
     if (P > cap) throw Error{SLG_ECAPACITY, "output buffer too small for the window"};
     if (P > 0 && (!I || !J || !O)) throw Error{SLG_EINVAL, "NULL output array"};
     const bool dev = P == 0 || (slg::is_device_ptr(I) && slg::is_device_ptr(J) &&
@@ -597,22 +603,23 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
     const int32_t nr = r1 - r0;
     unsigned long long* dd = nullptr;  // per list: total, then one entry per row
     if (digests || row_digests) {
-        const size_t nd = (size_t)k * ((size_t)nr + 1);
+        const size_t nd = (size_t)nl * ((size_t)nr + 1);
         dd = slg::dalloc<unsigned long long>(nd, h->st);
         SLG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(unsigned long long) * nd, h->st));
     }
     h->timer.mark(3, h->st);
-    for (int32_t t = 0; t < k; ++t) {
-        const int64_t Pt = seg[t + 1] - seg[t];
-        slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
-                      dI + seg[t], dJ + seg[t], dO + seg[t], Pt, &h->mtimer, h->st);
-    }
+    if (which < 0)
+        slg::run_fill_ensemble(h->g, p, q0, q1, seg, dI, dJ, dO, P, &h->mtimer, h->st);
+    else
+        slg::run_fill(h->g, p, p.rs_for(p.ens.s[which]), p.ens.ioff + which * (ni + 1), q0, q1,
+                      dI, dJ, dO, P, &h->mtimer, h->st);
     h->timer.mark(4, h->st);
     if (dd) {
-        for (int32_t t = 0; t < k; ++t) {
-            unsigned long long* dt = dd + (size_t)t * ((size_t)nr + 1);
-            slg::run_digest(p.rs_for(p.ens.s[t]), p.ens.rowoff + t * m1, r0, r1, dI + seg[t],
-                            dJ + seg[t], dO + seg[t], seg[t + 1] - seg[t], dt,
+        for (int32_t t = t0; t < t1; ++t) {
+            const int32_t u = t - t0;
+            unsigned long long* dt = dd + (size_t)u * ((size_t)nr + 1);
+            slg::run_digest(p.rs_for(p.ens.s[t]), p.ens.rowoff + t * m1, r0, r1, dI + seg[u],
+                            dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], dt,
                             row_digests ? dt + 1 : nullptr, h->st);
         }
     }
@@ -622,10 +629,10 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
         copy_out(J, dJ, sizeof(int32_t) * P, h->st);
         copy_out(O, dO, sizeof(int32_t) * P, h->st);
     }
-    for (int32_t t = 0; dd && t < k; ++t) {
-        const unsigned long long* dt = dd + (size_t)t * ((size_t)nr + 1);
-        if (digests) copy_out(digests + t, dt, sizeof(uint64_t), h->st);
-        if (row_digests) copy_out(row_digests + (size_t)t * nr, dt + 1, sizeof(uint64_t) * nr, h->st);
+    for (int32_t u = 0; dd && u < nl; ++u) {
+        const unsigned long long* dt = dd + (size_t)u * ((size_t)nr + 1);
+        if (digests) copy_out(digests + u, dt, sizeof(uint64_t), h->st);
+        if (row_digests) copy_out(row_digests + (size_t)u * nr, dt + 1, sizeof(uint64_t) * nr, h->st);
     }
     SLG_CUDA_TRY(cudaStreamSynchronize(h->st));
     finish_timing(h, P);

@@ -114,6 +114,18 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t x, int32_t* total, in
     return r;
 }
 
+// Several thresholds in one launch (an ensemble, Algorithm 3): the counting
+// pass counts every list's partners, the fill writes every list.
+struct EnsArgs {
+    int32_t k = 0;                   // number of lists (0: one threshold, from RowS)
+    int32_t s[ENS_MAX] = {};         // thresholds, strictly ascending
+    uint32_t bias[ENS_MAX] = {};     // 0x01010101 * (128 - min(s[t], 128)), see below
+    int64_t seg[ENS_MAX] = {};       // fill: first position of list t in I/J/O
+    const int64_t* ioff = nullptr;   // fill: per-item offsets of list t at [t * stride]
+    int32_t* icnt = nullptr;         // count: per-item counts of list t at [t * stride]
+    int64_t stride = 0;
+};
+
 // ============================================================ MODE_WARP
 
 template <bool FILL>
@@ -428,7 +440,7 @@ __device__ __forceinline__ int32_t dense_count(uint32_t hmi, const uint32_t* __r
            (int32_t)((w >> ((ci >> LOG_HALF) << 4)) & 0xffffu);
 }
 
-template <bool FILL>
+template <bool FILL, bool ENS>
 __global__ void __launch_bounds__(DENSE_THREADS)
 k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
@@ -438,7 +450,7 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
               const int32_t* __restrict__ idxTs, RowS rs, int32_t* __restrict__ icnt,
               const int64_t* __restrict__ ioff, int32_t* __restrict__ I, int32_t* __restrict__ J,
               int32_t* __restrict__ O, int32_t* __restrict__ queue, int64_t limit,
-              int32_t* __restrict__ err) {
+              int32_t* __restrict__ err, const EnsArgs ea) {
     constexpr int NT = DENSE_THREADS;
     constexpr int NW = DENSE_WARPS;
     extern __shared__ __align__(16) uint32_t dyn[];
@@ -446,6 +458,8 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     int32_t* cur = reinterpret_cast<int32_t*>(dyn + HALF);  // non-hub cursors
     int32_t* endp = cur + DENSE_MAXE;
     __shared__ int32_t wtot[NW];
+    // ensemble: survivors of lists 1.. per warp segment of the current tile
+    __shared__ int32_t wtot_e[ENS ? NW : 1][ENS ? ENS_MAX : 1];
     __shared__ int32_t sh_pos, sh_nnh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -487,6 +501,13 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         }
         const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
         int64_t out_pos = 0;
+        // ensemble: lane t (t >= 1) of every warp keeps list t's position
+        // (fill: the item's next output position before this tile; count: the
+        // item's survivors so far)
+        int64_t ens_pos = 0;
+        if (ENS && FILL && lane > 0 && lane < ea.k)
+            ens_pos = ea.seg[lane] + ea.ioff[lane * ea.stride + q] -
+                      ea.ioff[lane * ea.stride + item_lo];
         __syncthreads();
         const int32_t nnh = sh_nnh;
         for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += DENSE_TILE) {
@@ -519,11 +540,12 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             // extraction, pass 1: survivors per 32 partners, in j order per warp segment
             const int32_t seg0 = warp * DENSE_SEG;
             uint32_t bs0 = 0, bs1 = 0;
-            int32_t cnt = 0;
+            int32_t cnt = 0, ecnt = 0;
             for (int32_t r = 0; r < DENSE_SEG / 32; ++r) {
                 const int32_t ci = seg0 + r * 32 + lane;
-                bool f = false;
-                if (ci < span) f = dense_count(hmi, hubmask, ctr, t0, ci) >= s;
+                int32_t o = 0;
+                if (ci < span) o = dense_count(hmi, hubmask, ctr, t0, ci);
+                const bool f = ci < span && o >= s;
                 const unsigned bal = __ballot_sync(0xffffffffu, f);
                 if (FILL && lane == (r & 31)) {
                     if (r < 32)
@@ -532,8 +554,17 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         bs1 = bal;
                 }
                 cnt += __popc(bal);
+                if (ENS && bal) {
+                    // nested lists: the first list with no survivor ends the scan
+                    for (int t = 1; t < ea.k; ++t) {
+                        const unsigned bt = __ballot_sync(0xffffffffu, f && o >= ea.s[t]);
+                        if (bt == 0) break;
+                        if (lane == t) ecnt += __popc(bt);
+                    }
+                }
             }
             if (lane == 0) wtot[warp] = cnt;
+            if (ENS && lane > 0 && lane < ea.k) wtot_e[warp][lane] = ecnt;
             __syncthreads();
             int32_t before = 0, tile_total = 0;
 #pragma unroll
@@ -542,30 +573,68 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 before += (w < warp) ? v : 0;
                 tile_total += v;
             }
+            int32_t ebefore = 0, etotal = 0;  // lane t: list t
+            if (ENS && lane > 0 && lane < ea.k) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int32_t v = wtot_e[w][lane];
+                    ebefore += (w < warp) ? v : 0;
+                    etotal += v;
+                }
+            }
             if (FILL) {
                 // pass 2: write survivors at their ordered positions
                 int64_t base = obase + out_pos + before;
+                int64_t ebase = ens_pos + ebefore;  // lane t: list t
                 for (int32_t r = 0; r < DENSE_SEG / 32; ++r) {
                     const unsigned bal = __shfl_sync(0xffffffffu, r < 32 ? bs0 : bs1, r & 31);
                     if (bal == 0) continue;
-                    if ((bal >> lane) & 1u) {
-                        const int32_t ci = seg0 + r * 32 + lane;
+                    const bool mine = (bal >> lane) & 1u;
+                    const int32_t ci = seg0 + r * 32 + lane;
+                    int32_t o = 0;
+                    if (mine) {
+                        o = dense_count(hmi, hubmask, ctr, t0, ci);
                         const int64_t p2 = base + __popc(bal & lt);
                         if (p2 < limit) {
                             I[p2] = i - ib;
                             J[p2] = t0 + ci - ib;
-                            O[p2] = dense_count(hmi, hubmask, ctr, t0, ci);
+                            O[p2] = o;
                         } else {
                             atomicOr(err, ERR_BOUNDS);
                         }
                     }
                     base += __popc(bal);
+                    if (ENS) {
+                        for (int t = 1; t < ea.k; ++t) {
+                            const bool ft = mine && o >= ea.s[t];
+                            const unsigned bt = __ballot_sync(0xffffffffu, ft);
+                            if (bt == 0) break;
+                            const int64_t bt_base = __shfl_sync(0xffffffffu, ebase, t);
+                            if (ft) {
+                                const int64_t p2 = bt_base + __popc(bt & lt);
+                                if (p2 < limit) {
+                                    I[p2] = i - ib;
+                                    J[p2] = t0 + ci - ib;
+                                    O[p2] = o;
+                                } else {
+                                    atomicOr(err, ERR_BOUNDS);
+                                }
+                            }
+                            if (lane == t) ebase += __popc(bt);
+                        }
+                    }
                 }
             }
             out_pos += tile_total;
+            if (ENS) ens_pos += etotal;
             __syncthreads();
         }
-        if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
+        if (!FILL && ENS) {
+            if (tid == 0) ea.icnt[q] = (int32_t)out_pos;
+            if (warp == 0 && lane > 0 && lane < ea.k) ea.icnt[lane * ea.stride + q] = (int32_t)ens_pos;
+        } else if (!FILL && tid == 0) {
+            icnt[q] = (int32_t)out_pos;
+        }
         __syncthreads();
     }
 }
@@ -607,8 +676,50 @@ static_assert(WD_TILE % (128 * WD_CBLK) == 0 && WD_TILE_FILL % (128 * WD_CBLK) =
 static_assert(MAX_HUBS + WD_MAXR < 128, "byte-wise overlap sums must stay below 128");
 static_assert(WD_MAXR % 32 == 0 && WD_SLOTS >= 1 && WD_SLOTS <= 2, "cursors per lane");
 
-template <bool FILL>
-__global__ void __launch_bounds__(WD_WARPS * 32, FILL ? 2 : 3)
+// Ensemble fill: the entries e (valid in the lanes with `valid`, ascending j
+// across lanes) of list 0 that were just stored also go to every list t >= 1
+// whose threshold they reach. Lane t holds list t's next position. Lists are
+// taken four at a time so that their ballots and broadcasts overlap; the lists
+// are nested (s ascending), so a group whose first list takes nothing ends it.
+constexpr int ENS_GROUP = 4;
+
+__device__ __forceinline__ void ens_append(int2 e, bool valid, int64_t& ens_pos, int32_t li,
+                                           int32_t ib, int lane, unsigned lt, const EnsArgs& ea,
+                                           int32_t* __restrict__ I, int32_t* __restrict__ J,
+                                           int32_t* __restrict__ O, int64_t limit,
+                                           int32_t* __restrict__ err) {
+    for (int t0 = 1; t0 < ea.k; t0 += ENS_GROUP) {
+        unsigned bal[ENS_GROUP];
+#pragma unroll
+        for (int u = 0; u < ENS_GROUP; ++u) {
+            const int t = t0 + u;
+            bal[u] = __ballot_sync(0xffffffffu, valid && t < ea.k && e.y >= ea.s[t & (ENS_MAX - 1)]);
+        }
+        if (bal[0] == 0) break;
+        int64_t base[ENS_GROUP];
+#pragma unroll
+        for (int u = 0; u < ENS_GROUP; ++u) base[u] = __shfl_sync(0xffffffffu, ens_pos, (t0 + u) & 31);
+#pragma unroll
+        for (int u = 0; u < ENS_GROUP; ++u) {
+            if ((bal[u] >> lane) & 1u) {
+                const int64_t p2 = base[u] + __popc(bal[u] & lt);
+                if (p2 < limit) {
+                    I[p2] = li;
+                    J[p2] = e.x - ib;
+                    O[p2] = e.y;
+                } else {
+                    atomicOr(err, ERR_BOUNDS);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ENS_GROUP; ++u)
+            if (lane == t0 + u) ens_pos += __popc(bal[u]);
+    }
+}
+
+template <bool FILL, bool ENS>
+__global__ void __launch_bounds__(WD_WARPS * 32, (FILL || ENS) ? 2 : 3)
 k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
                const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
@@ -617,7 +728,7 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ idxTs, RowS rs, int32_t* __restrict__ icnt,
                const int64_t* __restrict__ ioff, int32_t* __restrict__ I,
                int32_t* __restrict__ J, int32_t* __restrict__ O, int32_t* __restrict__ queue,
-               int64_t limit, int32_t* __restrict__ err) {
+               int64_t limit, int32_t* __restrict__ err, const EnsArgs ea) {
     constexpr int TILE = FILL ? WD_TILE_FILL : WD_TILE;
     constexpr int WORDS = TILE / 4;
     extern __shared__ __align__(16) uint32_t dyn[];
@@ -684,6 +795,13 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         }
         __syncwarp();
 
+        // ensemble: lane t keeps list t's next output position (fill) or
+        // count (counting pass); lists 1.. of a fill take their entries from
+        // list 0's ring as it is flushed
+        int64_t ens_pos = 0;
+        if (ENS && FILL && lane > 0 && lane < ea.k)
+            ens_pos = ea.seg[lane] + ea.ioff[lane * ea.stride + q] -
+                      ea.ioff[lane * ea.stride + item_lo];
         // fill: survivors collect in the ring and leave it in chunks that end
         // on 128-byte boundaries of I (the first chunk is shorter)
         int64_t wpos = FILL ? ioff[q] - ioff[item_lo] : 0;  // next output position
@@ -763,6 +881,11 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             }
             __syncwarp();
             // 3. extraction: four consecutive partners per lane
+            // (ensemble count: at most 128 partners per lane and tile, so a
+            // byte holds each list's count until the tile ends)
+            uint32_t ecnt[ENS ? ENS_MAX / 4 : 1];
+#pragma unroll
+            for (int u = 0; u < (ENS ? ENS_MAX / 4 : 1); ++u) ecnt[u] = 0;
             for (int32_t g = 0; g < span; g += 128 * WD_CBLK) {
                 uint4 hv[WD_CBLK];
                 uint32_t cw[WD_CBLK];
@@ -786,11 +909,24 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                                         ((uint32_t)__popc(hmi & hv[b].w) << 24);
                     const uint32_t c4 = p4 + cw[b];  // four overlaps, one per byte
                     uint32_t f4 = (c4 + bias4) & 0x80808080u;
+                    uint32_t vmask = 0x80808080u;  // ensemble: the partners of this slice
                     const int32_t j0 = t0 + ci;
                     if (j0 < jfirst || j0 + 4 > t1) {  // partial block at a tile edge
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
-                            if (j0 + r < jfirst || j0 + r >= t1) f4 &= ~(0x80u << (8 * r));
+                            if (j0 + r < jfirst || j0 + r >= t1) {
+                                f4 &= ~(0x80u << (8 * r));
+                                vmask &= ~(0x80u << (8 * r));
+                            }
+                    }
+                    if (!FILL && ENS) {
+                        // byte t % 4 of ecnt[t / 4]: list t's survivors of this tile
+#pragma unroll
+                        for (int t = 0; t < ENS_MAX; ++t)
+                            if (t < ea.k)
+                                ecnt[t >> 2] += (uint32_t)__popc((c4 + ea.bias[t]) & vmask)
+                                                << (8 * (t & 3));
+                        continue;
                     }
                     if (!FILL) {
                         my_count += __popc(f4);
@@ -817,8 +953,9 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     rcount += tot;
                     __syncwarp();
                     while (rcount >= need) {
+                        int2 e = make_int2(0, 0);
                         if (lane < need) {
-                            const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
+                            e = ring[(rhead + lane) & (WD_RING - 1)];
                             const int64_t p2 = wpos + lane;
                             if (p2 < limit) {
                                 I[p2] = i - ib;
@@ -828,6 +965,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                                 atomicOr(err, ERR_BOUNDS);
                             }
                         }
+                        if (ENS) ens_append(e, lane < need, ens_pos, i - ib, ib, lane, lt, ea, I, J,
+                                            O, limit, err);
                         rhead = (rhead + need) & (WD_RING - 1);
                         rcount -= need;
                         wpos += need;
@@ -836,11 +975,21 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     __syncwarp();
                 }
             }
+            if (!FILL && ENS) {
+#pragma unroll
+                for (int t = 0; t < ENS_MAX; ++t) {
+                    if (t >= ea.k) break;
+                    const uint32_t tot =
+                        __reduce_add_sync(0xffffffffu, (ecnt[t >> 2] >> (8 * (t & 3))) & 0xffu);
+                    if (lane == t) ens_pos += tot;
+                }
+            }
             __syncwarp();
         }
         if (FILL && rcount > 0) {  // the slice's last, partial chunk
+            int2 e = make_int2(0, 0);
             if (lane < rcount) {
-                const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
+                e = ring[(rhead + lane) & (WD_RING - 1)];
                 const int64_t p2 = wpos + lane;
                 if (p2 < limit) {
                     I[p2] = i - ib;
@@ -850,9 +999,13 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     atomicOr(err, ERR_BOUNDS);
                 }
             }
+            if (ENS) ens_append(e, lane < rcount, ens_pos, i - ib, ib, lane, lt, ea, I, J, O, limit,
+                                err);
             __syncwarp();
         }
-        if (!FILL) {
+        if (!FILL && ENS) {
+            if (lane < ea.k) ea.icnt[lane * ea.stride + q] = (int32_t)ens_pos;
+        } else if (!FILL) {
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) my_count += __shfl_xor_sync(0xffffffffu, my_count, d);
             if (lane == 0) icnt[q] = my_count;
@@ -923,48 +1076,55 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 
 struct Occupancy {
     int sms = 0;
-    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, wdense_ctas = 0, wdense_fill_ctas = 0;
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0;
+    int wdense_ctas[2][2] = {};  // [fill][ensemble]
 };
 
 Occupancy g_occ;
 std::once_flag g_occ_once;
 
+template <bool FILL, bool ENS>
+int wdense_setup(int sms) {
+    const size_t smem = FILL ? WD_SMEM_FILL : WD_SMEM;
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<FILL, ENS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int d = 0;
+    SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_wdense_items<FILL, ENS>,
+                                                               WD_WARPS * 32, smem));
+    return sms * (d > 0 ? d : 1);
+}
+
 void occupancy_init() {
     Occupancy& o = g_occ;
-    {
-        int dev = 0;
-        SLG_CUDA_TRY(cudaGetDevice(&dev));
-        SLG_CUDA_TRY(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev));
-        SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)DENSE_SMEM));
-        SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)DENSE_SMEM));
-        SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)WD_SMEM));
-        SLG_CUDA_TRY(cudaFuncSetAttribute(k_wdense_items<true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)WD_SMEM_FILL));
-        int a = 0, b = 0, c = 0, d = 0;
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_wdense_items<false>,
-                                                                   WD_WARPS * 32, WD_SMEM));
-        o.wdense_ctas = o.sms * (d > 0 ? d : 1);
-        int d2 = 0;
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d2, k_wdense_items<true>,
-                                                                   WD_WARPS * 32, WD_SMEM_FILL));
-        o.wdense_fill_ctas = o.sms * (d2 > 0 ? d2 : 1);
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
-                                                                   WARP_CTA_WARPS * 32, 0));
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_block_items<true>,
-                                                                   BLOCK_THREADS, 0));
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_dense_items<true>,
-                                                                   DENSE_THREADS, DENSE_SMEM));
-        o.warp_ctas = o.sms * (a > 0 ? a : 1);
-        o.block_ctas = o.sms * (b > 0 ? b : 1);
-        o.dense_ctas = o.sms * (c > 0 ? c : 1);
-    }
+    int dev = 0;
+    SLG_CUDA_TRY(cudaGetDevice(&dev));
+    SLG_CUDA_TRY(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev));
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DENSE_SMEM));
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DENSE_SMEM));
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DENSE_SMEM));
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DENSE_SMEM));
+    o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
+    o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
+    o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
+    o.wdense_ctas[1][1] = wdense_setup<true, true>(o.sms);
+    int a = 0, b = 0, c = 0;
+    SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
+                                                               WARP_CTA_WARPS * 32, 0));
+    SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_block_items<true>,
+                                                               BLOCK_THREADS, 0));
+    SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_dense_items<true, false>,
+                                                               DENSE_THREADS, DENSE_SMEM));
+    o.warp_ctas = o.sms * (a > 0 ? a : 1);
+    o.block_ctas = o.sms * (b > 0 ? b : 1);
+    o.dense_ctas = o.sms * (c > 0 ? c : 1);
 }
 
 Occupancy& occupancy() {
@@ -972,20 +1132,27 @@ Occupancy& occupancy() {
     return g_occ;
 }
 
+constexpr unsigned ALL_MODES = (1u << NMODES) - 1u;
+// ensemble launches: handlers with a fused form, and those run once per list
+constexpr unsigned ENS_FUSED = (1u << MODE_DENSE) | (1u << MODE_WDENSE);
+constexpr unsigned ENS_PER_LIST = ALL_MODES & ~ENS_FUSED;
+
+// One launch per handler in `modes` that has items. queue: NMODES work-queue
+// heads (zeroed, used once); err: the shared error flag. With `ea`, the warp
+// dense handler runs its ensemble form (every list in one launch).
 template <bool FILL>
 void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
                   int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
-                  int64_t limit, int32_t* scratch, ModeTimer* mt, cudaStream_t st) {
-    // scratch: NMODES queue heads, then the error flag
+                  int64_t limit, int32_t* queue, int32_t* err, ModeTimer* mt, cudaStream_t st,
+                  unsigned modes = ALL_MODES, const EnsArgs* ea = nullptr) {
     Occupancy& oc = occupancy();
-    int32_t* queue = scratch;
-    int32_t* err = scratch + NMODES;
     const bool timed = mt && mt->on;
     auto tick = [&](int mode, int edge) {
         if (timed) SLG_CUDA_TRY(cudaEventRecord(mt->ev[2 * mode + edge], st));
     };
+    auto want = [&](int mode) { return ((modes >> mode) & 1u) && p.mode_count[mode] > 0; };
     bool ran[NMODES] = {};
-    if (p.mode_count[MODE_WARP]) {
+    if (want(MODE_WARP)) {
         ran[MODE_WARP] = true;
         tick(MODE_WARP, 0);
         k_warp_items<FILL><<<oc.warp_ctas, WARP_CTA_WARPS * 32, 0, st>>>(
@@ -994,7 +1161,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         SLG_LAUNCH_CHECK();
         tick(MODE_WARP, 1);
     }
-    if (p.mode_count[MODE_BLOCK]) {
+    if (want(MODE_BLOCK)) {
         ran[MODE_BLOCK] = true;
         tick(MODE_BLOCK, 0);
         k_block_items<FILL><<<oc.block_ctas, BLOCK_THREADS, 0, st>>>(
@@ -1003,24 +1170,38 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         SLG_LAUNCH_CHECK();
         tick(MODE_BLOCK, 1);
     }
-    if (p.mode_count[MODE_DENSE]) {
+    if (want(MODE_DENSE)) {
         ran[MODE_DENSE] = true;
         tick(MODE_DENSE, 0);
-        k_dense_items<FILL><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
-            p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O,
-            queue + MODE_DENSE, limit, err);
+        if (ea) {
+            k_dense_items<FILL, true><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
+                p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi,
+                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
+                O, queue + MODE_DENSE, limit, err, *ea);
+        } else {
+            k_dense_items<FILL, false><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
+                p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi,
+                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
+                O, queue + MODE_DENSE, limit, err, EnsArgs{});
+        }
         SLG_LAUNCH_CHECK();
         tick(MODE_DENSE, 1);
     }
-    if (p.mode_count[MODE_WDENSE]) {
+    if (want(MODE_WDENSE)) {
         ran[MODE_WDENSE] = true;
         tick(MODE_WDENSE, 0);
-        k_wdense_items<FILL><<<FILL ? oc.wdense_fill_ctas : oc.wdense_ctas, WD_WARPS * 32,
-                               FILL ? WD_SMEM_FILL : WD_SMEM, st>>>(
-            p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi, g.off,
-            g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O,
-            queue + MODE_WDENSE, limit, err);
+        const size_t smem = FILL ? WD_SMEM_FILL : WD_SMEM;
+        if (ea) {
+            k_wdense_items<FILL, true><<<oc.wdense_ctas[FILL][1], WD_WARPS * 32, smem, st>>>(
+                p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi,
+                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
+                O, queue + MODE_WDENSE, limit, err, *ea);
+        } else {
+            k_wdense_items<FILL, false><<<oc.wdense_ctas[FILL][0], WD_WARPS * 32, smem, st>>>(
+                p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi,
+                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
+                O, queue + MODE_WDENSE, limit, err, EnsArgs{});
+        }
         SLG_LAUNCH_CHECK();
         tick(MODE_WDENSE, 1);
     }
@@ -1036,17 +1217,18 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
     }
 }
 
-int32_t* new_scratch(cudaStream_t st) {
+// Device scratch: nq work-queue heads, then the error flag (all zero).
+int32_t* new_scratch(cudaStream_t st, int nq = NMODES) {
     int32_t* s = nullptr;
-    SLG_CUDA_TRY(cudaMallocAsync((void**)&s, sizeof(int32_t) * (NMODES + 1), st));
-    SLG_CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(int32_t) * (NMODES + 1), st));
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&s, sizeof(int32_t) * (nq + 1), st));
+    SLG_CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(int32_t) * (nq + 1), st));
     return s;
 }
 
 // Reads the error flag (synchronises) and frees the scratch.
-void check_scratch(int32_t* s, cudaStream_t st, const char* what) {
+void check_scratch(int32_t* s, cudaStream_t st, const char* what, int nq = NMODES) {
     int32_t e = 0;
-    SLG_CUDA_TRY(cudaMemcpyAsync(&e, s + NMODES, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaMemcpyAsync(&e, s + nq, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SLG_CUDA_TRY(cudaStreamSynchronize(st));
     SLG_CUDA_TRY(cudaFreeAsync(s, st));
     if (e) {
@@ -1056,13 +1238,24 @@ void check_scratch(int32_t* s, cudaStream_t st, const char* what) {
     }
 }
 
+EnsArgs ens_args(const Plan& p) {
+    EnsArgs ea;
+    ea.k = p.ens.k;
+    for (int t = 0; t < ea.k; ++t) {
+        ea.s[t] = p.ens.s[t];
+        // byte-wise threshold: x >= s  <=>  bit 7 of x + (128 - s), for x < 128
+        ea.bias[t] = 0x01010101u * (uint32_t)(128 - (p.ens.s[t] < 128 ? p.ens.s[t] : 128));
+    }
+    return ea;
+}
+
 }  // namespace
 
 void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
                cudaStream_t st) {
     int32_t* sc = new_scratch(st);
     launch_items<false>(g, p, rs, 0, (int32_t)p.nitems, icnt, nullptr, nullptr, nullptr, nullptr,
-                        0, sc, mt, st);
+                        0, sc, sc + NMODES, mt, st);
     check_scratch(sc, st, "counting pass");
 }
 
@@ -1071,8 +1264,49 @@ void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, in
               cudaStream_t st) {
     if (item_hi <= item_lo) return;
     int32_t* sc = new_scratch(st);
-    launch_items<true>(g, p, rs, item_lo, item_hi, nullptr, ioff, I, J, O, limit, sc, mt, st);
+    launch_items<true>(g, p, rs, item_lo, item_hi, nullptr, ioff, I, J, O, limit, sc, sc + NMODES,
+                       mt, st);
     check_scratch(sc, st, "fill pass");
+}
+
+void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st) {
+    const int32_t k = p.ens.k;
+    const int64_t ni = p.nitems;
+    int32_t* sc = new_scratch(st, NMODES * k);
+    int32_t* err = sc + NMODES * k;
+    // warp-table and CTA-table handlers (sparse rows): one launch per threshold
+    for (int32_t t = 0; t < k; ++t)
+        launch_items<false>(g, p, p.rs_for(p.ens.s[t]), 0, (int32_t)ni, p.ens.icnt + t * ni,
+                            nullptr, nullptr, nullptr, nullptr, 0, sc + NMODES * t, err, mt, st,
+                            ENS_PER_LIST);
+    // dense handlers: every threshold in one launch
+    EnsArgs ea = ens_args(p);
+    ea.icnt = p.ens.icnt;
+    ea.stride = ni;
+    launch_items<false>(g, p, p.rs_for(p.ens.s[0]), 0, (int32_t)ni, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, 0, sc, err, mt, st, ENS_FUSED, &ea);
+    check_scratch(sc, st, "ensemble counting pass", NMODES * k);
+}
+
+void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
+                       const int64_t* seg, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
+                       ModeTimer* mt, cudaStream_t st) {
+    if (item_hi <= item_lo) return;
+    const int32_t k = p.ens.k;
+    const int64_t ni = p.nitems;
+    int32_t* sc = new_scratch(st, NMODES * k);
+    int32_t* err = sc + NMODES * k;
+    for (int32_t t = 0; t < k; ++t)
+        launch_items<true>(g, p, p.rs_for(p.ens.s[t]), item_lo, item_hi, nullptr,
+                           p.ens.ioff + t * (ni + 1), I + seg[t], J + seg[t], O + seg[t],
+                           seg[t + 1] - seg[t], sc + NMODES * t, err, mt, st, ENS_PER_LIST);
+    EnsArgs ea = ens_args(p);
+    ea.ioff = p.ens.ioff;
+    ea.stride = ni + 1;
+    for (int32_t t = 0; t < k; ++t) ea.seg[t] = seg[t];
+    launch_items<true>(g, p, p.rs_for(p.ens.s[0]), item_lo, item_hi, nullptr, p.ens.ioff, I, J, O,
+                       limit, sc, err, mt, st, ENS_FUSED, &ea);
+    check_scratch(sc, st, "ensemble fill pass", NMODES * k);
 }
 
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,

@@ -435,10 +435,10 @@ void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, Mod
     e.rowoff = dalloc<int64_t>((size_t)(k * m1), st);
     e.rowtot = dalloc<int64_t>((size_t)m1, st);
     const int T = 256;
+    // the plan's work (pruned at s[0] <= s[t]) with threshold s[t]: a pair
+    // with overlap >= s[t] has both sizes >= s[t] >= s[0], so it is there
+    run_count_ensemble(g, p, mt, st);
     for (int32_t t = 0; t < k; ++t) {
-        // the plan's work (pruned at s[0] <= s[t]) with threshold s[t]: a pair
-        // with overlap >= s[t] has both sizes >= s[t] >= s[0], so it is there
-        run_count(g, p, p.rs_for(s[t]), e.icnt + t * ni, mt, st);
         scan_i32_to_i64(e.icnt + t * ni, e.ioff + t * (ni + 1), ni, st);
         k_rowoff<<<grid_for(m1, T), T, 0, st>>>(p.row_item, e.ioff + t * (ni + 1), g.m,
                                                 e.rowoff + t * m1);

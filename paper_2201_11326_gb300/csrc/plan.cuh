@@ -119,6 +119,13 @@ void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTim
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
               cudaStream_t st);
+// Ensemble passes over the plan's items (p.ens.k lists, thresholds p.ens.s):
+// counts into p.ens.icnt; the fill writes list t of items [item_lo, item_hi)
+// at I/J/O + seg[t] (seg[k] = total).
+void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st);
+void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
+                       const int64_t* seg, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
+                       ModeTimer* mt, cudaStream_t st);
 // Per-handler totals over rows: rows, wedges, incidences, pairs (needs counts).
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).

@@ -140,6 +140,38 @@ def test_ensemble_windows_digests_and_row_offsets():
         g.free()
 
 
+@pytest.mark.parametrize("mode", ["default", "dense_only", "dense_cta_only", "block_only"])
+def test_ensemble_one_list_at_a_time(mode):
+    # which = t: list t alone, in its own windows, from the shared plan
+    h = synth.medium(seed=2, m=6000)
+    s_list = [1, 2, 4, 7]
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        slg.slg_set_bins(g, *FORCED[mode])
+        pairs, _ = slg.slg_ensemble_count(g, s_list)
+        for t, s in enumerate(s_list):
+            cap = max(500, pairs[t] // 5)
+            splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+            I = np.zeros(cap, np.int32)
+            J = np.zeros(cap, np.int32)
+            O = np.zeros(cap, np.int32)
+            parts, tot = [], 0
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                (p,), (d,) = slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O,
+                                                           cap, digest=True, which=t)
+                parts.append((I[:p].copy(), J[:p].copy(), O[:p].copy()))
+                tot = (tot + d) % (1 << 64)
+            want = oracle_list("med6000", h, s)
+            got = tuple(np.concatenate([x[c] for x in parts]) for c in range(3))
+            assert_same(got, want, f"list {t} s={s} {mode}")
+            assert tot == oracle.list_digest(*want)
+        with pytest.raises(slg.SlgError) as e:
+            slg.slg_ensemble_plan_windows(g, s_list, 100, which=len(s_list))
+        assert e.value.code == slg.SLG_EINVAL
+    finally:
+        g.free()
+
+
 def test_ensemble_device_buffers():
     import torch
     h = synth.medium(seed=3, m=5000)

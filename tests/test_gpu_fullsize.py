@@ -1,6 +1,6 @@
 """Full-size parity on the medium workload, in the benchmark's launch configuration.
 
-The medium hypergraph (m = 1,000,000) is built through windows of at most 2^31
+The medium hypergraph (m = 1,000,000) is built through windows of at most 2^33
 pairs into reused device buffers, exactly as bench.py times it. Its s-line
 graphs hold up to 4.8e11 pairs, so the comparison with the oracle is per row:
 for 1,000 seeded random rows and the 100 rows with the most wedges, the
@@ -18,7 +18,7 @@ import paper_2201_11326_gb300 as slg
 
 pytestmark = pytest.mark.gpu
 
-WINDOW = 1 << 31
+WINDOW = 1 << 33
 
 
 @pytest.fixture(scope="module")

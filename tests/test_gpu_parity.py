@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 # bin settings that force one handler onto every row (results must not change)
 FORCED = {
-    "default": (128, 1024, 64, 16, 32),
+    "default": (128, 1024, 64, 4, 32),
     "block_only": (0, 1024, -1, 4, 32),
     "block_one_item_per_row": (0, 1 << 30, -1, 4, 32),  # big items: exercises the split path
     "block_tiny_items": (0, 1, -1, 4, 32),
