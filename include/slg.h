@@ -249,19 +249,24 @@ slg_status slg_set_timing(slg_graph* g, int32_t enable);
 slg_status slg_last_timing(slg_graph* g, float* ms5);
 
 /*
- * Per-handler kernel time accumulated while timing is enabled: ms8[pass*4 +
- * mode] and launches8[pass*4 + mode], pass 0 = counting, 1 = fill, mode 0 =
- * warp table, 1 = CTA table, 2 = CTA dense tiles, 3 = warp dense tiles.
- * reset != 0 zeroes the totals after reading. Either output may be NULL.
+ * Number of handlers (SLG_NMODES): 0 = warp table, 1 = CTA table, 2 = CTA
+ * dense tiles, 3 = warp dense tiles, 4 = CTA sparse accumulator.
+ *
+ * Per-handler kernel time accumulated while timing is enabled:
+ * ms[pass*SLG_NMODES + mode] and launches[pass*SLG_NMODES + mode] (2 *
+ * SLG_NMODES entries each), pass 0 = counting, 1 = fill. reset != 0 zeroes
+ * the totals after reading. Either output may be NULL.
  */
-slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms8, int64_t* launches8);
+#define SLG_NMODES 5
+slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms, int64_t* launches);
 
 /*
- * Work per handler for s (runs the counting pass if needed): out16[mode*4 +
- * c] with c = 0 rows, 1 wedges, 2 incidences (sum of |e_i| over the rows),
- * 3 output pairs. The wedge total over the four handlers is W_s.
+ * Work per handler for s (runs the counting pass if needed): out[mode*4 + c]
+ * (4 * SLG_NMODES entries) with c = 0 rows, 1 wedges, 2 incidences (sum of
+ * |e_i| over the rows), 3 output pairs. The wedge total over the handlers is
+ * W_s.
  */
-slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out16);
+slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out);
 
 /*
  * slg_batch_load -- many hypergraphs, each with its own s, as one handle.
@@ -421,14 +426,20 @@ slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int6
  *     (or S_i <= 4096); dense_min_density < 0 disables it. A dense row with
  *     at most wdense_max_ranges (<= 32; 0 disables) wedge ranges through
  *     non-hub vertices goes to the warp-level dense handler (items of
- *     4096 * dense_item_tiles ids), other dense rows to the CTA-level one
+ *     8192 * dense_item_tiles ids), other dense rows to the CTA-level one
  *     (items of 32768 * dense_item_tiles ids);
+ *   - by a CTA sparse accumulator (8-bit counters over 65536-id tiles and a
+ *     list of the counters touched) when |e_i| <= 255 and W_i >=
+ *     sparse_min_per_tile * ceil(S_i / 65536) (< 0 disables it), in items of
+ *     about sparse_item_wedges wedges;
  *   - otherwise by CTA hash tables, about block_item_wedges wedges per item.
  * Results do not depend on these values; only speed does. Resets the plan.
+ * SLG_ECAPACITY from a later call when a binning needs 2^31 items or more.
  */
 slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_item_wedges,
                         int32_t dense_min_density, int32_t dense_item_tiles,
-                        int32_t wdense_max_ranges);
+                        int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
+                        int32_t sparse_item_wedges);
 
 #ifdef __cplusplus
 }

@@ -77,6 +77,8 @@ BinParams default_bins() {
     b.dense_min_density = 64;  // dense when W_i >= span / 4
     b.dense_item_tiles = 4;
     b.wdense_max_ranges = WD_MAXR;
+    b.sparse_min_per_tile = 64;
+    b.sparse_item_wedges = 65536;
     return b;
 }
 
@@ -652,12 +654,13 @@ slg_status slg_set_timing(slg_graph* h, int32_t enable) {
     return SLG_OK;
 }
 
-slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms8, int64_t* launches8) {
+slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms, int64_t* launches) {
+    static_assert(slg::NMODES == SLG_NMODES, "handler count");
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < slg::NMODES; ++k) {
-            if (ms8) ms8[pass * slg::NMODES + k] = h->mtimer.ms[pass][k];
-            if (launches8) launches8[pass * slg::NMODES + k] = h->mtimer.launches[pass][k];
+            if (ms) ms[pass * slg::NMODES + k] = h->mtimer.ms[pass][k];
+            if (launches) launches[pass * slg::NMODES + k] = h->mtimer.launches[pass][k];
             if (reset) {
                 h->mtimer.ms[pass][k] = 0;
                 h->mtimer.launches[pass][k] = 0;
@@ -666,14 +669,14 @@ slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms8, int64_t* la
     return SLG_OK;
 }
 
-slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out16) {
-    if (!h || !out16) return fail(SLG_EINVAL, "NULL argument");
+slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out) {
+    if (!h || !out) return fail(SLG_EINVAL, "NULL argument");
     API_BEGIN
     ensure_counted(h, s);
     int64_t st[slg::NMODES][4];
     slg::plan_mode_stats(h->g, h->plan, st, h->st);
     for (int k = 0; k < slg::NMODES; ++k)
-        for (int c = 0; c < 4; ++c) out16[k * 4 + c] = st[k][c];
+        for (int c = 0; c < 4; ++c) out[k * 4 + c] = st[k][c];
     API_END
 }
 
@@ -687,11 +690,12 @@ slg_status slg_last_timing(slg_graph* h, float* ms5) {
 
 slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_item_wedges,
                         int32_t dense_min_density, int32_t dense_item_tiles,
-                        int32_t wdense_max_ranges) {
+                        int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
+                        int32_t sparse_item_wedges) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     if (warp_max_wedges < 0 || warp_max_wedges > slg::WARP_TABLE / 2 || block_item_wedges < 1 ||
         dense_item_tiles < 1 || dense_item_tiles > 4096 || wdense_max_ranges < 0 ||
-        wdense_max_ranges > slg::WD_MAXR)
+        wdense_max_ranges > slg::WD_MAXR || sparse_item_wedges < 1)
         return fail(SLG_EINVAL, "bin parameter out of range");
     API_BEGIN
     h->bp.warp_max_wedges = warp_max_wedges;
@@ -699,6 +703,8 @@ slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_ite
     h->bp.dense_min_density = dense_min_density;
     h->bp.dense_item_tiles = dense_item_tiles;
     h->bp.wdense_max_ranges = wdense_max_ranges;
+    h->bp.sparse_min_per_tile = sparse_min_per_tile;
+    h->bp.sparse_item_wedges = sparse_item_wedges;
     h->plan.release(h->st);
     API_END
 }

@@ -1013,6 +1013,236 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     }
 }
 
+// ========================================================== MODE_SPARSE
+//
+// Rows whose partners are spread thinly over a wide id range (wedges through
+// many high-degree vertices, density far below the dense handlers' bar): a
+// sparse accumulator per CTA. One item is a j slice of one row; it is walked
+// in tiles of 65536 ids. Per tile:
+//   1. every wedge of the tile adds 1 to the 8-bit counter of its partner
+//      (|e_i| <= 255 bounds every count); the first increment of a counter
+//      appends it to a list of touched counters;
+//   2. survivors (count >= s) are read off the touched list only (or off the
+//      whole tile when more than SP_TOUCH counters were touched);
+//   3. the fill ranks each survivor by the survivors at lower ids (a bitmap
+//      of the tile and its per-word prefix), so no sort is needed;
+//   4. the touched counters are cleared.
+// Hub vertices are counted like any other here: a partner may share only hubs
+// with e_i, and only a walk over its wedges finds it in a sparse row.
+
+constexpr int SP_WARPS = SP_THREADS / 32;
+constexpr int SP_WORDS = SP_TILE / 4;   // four 8-bit counters per word
+constexpr int SP_BITS = SP_TILE / 32;   // survivor bitmap words
+constexpr int SP_MAXR = 256;            // wedge ranges of a row (|e_i| <= 255)
+static_assert(SP_MAX_SIZE < 256 && SP_MAXR > SP_MAX_SIZE, "8-bit counters");
+static_assert(SP_TILE <= 65536, "touched counters are listed as 16-bit offsets");
+static_assert(SP_BITS == 4 * SP_THREADS, "bitmap prefix: four words per thread");
+constexpr size_t sp_smem(bool fill) {
+    return sizeof(uint32_t) * SP_WORDS + sizeof(uint16_t) * SP_TOUCH +
+           sizeof(int32_t) * 2 * SP_MAXR + (fill ? sizeof(uint32_t) * 2 * SP_BITS : 0);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(SP_THREADS, 2)
+k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+               const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+               const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
+               int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
+               int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
+               int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+    extern __shared__ __align__(16) uint32_t dyn[];
+    uint32_t* ctr = dyn;                                                   // SP_WORDS
+    uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + SP_WORDS);      // SP_TOUCH
+    int32_t* cur = reinterpret_cast<int32_t*>(touched + SP_TOUCH);        // SP_MAXR
+    int32_t* endp = cur + SP_MAXR;                                         // SP_MAXR
+    uint32_t* bm = reinterpret_cast<uint32_t*>(endp + SP_MAXR);           // fill: SP_BITS
+    uint32_t* wpre = bm + SP_BITS;                                         // fill: SP_BITS
+    __shared__ int32_t tmp[SP_WARPS + 1];
+    __shared__ int32_t sh_pos, sh_n, sh_nt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+    // the counters (and the fill's bitmap) start at zero; every tile leaves them so
+    for (int32_t w = tid; w < SP_WORDS; w += SP_THREADS) ctr[w] = 0;
+    if (FILL)
+        for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
+
+    for (;;) {
+        if (tid == 0) {
+            sh_pos = lo + atomicAdd(queue, 1);
+            sh_n = 0;
+            sh_nt = 0;
+        }
+        __syncthreads();
+        const int32_t pos = sh_pos;
+        if (pos >= hi) break;
+        const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) {  // nothing to write (same in every thread)
+            __syncthreads();
+            continue;
+        }
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const int32_t s = rs.s_of(i);
+        const int32_t ib = rs.base_of(i);
+        const int32_t e0 = off[i];
+        const int32_t ne = off[i + 1] - e0;
+        // wedge ranges of the row, cursors at the item's first partner
+        for (int32_t k = tid; k < ne; k += SP_THREADS) {
+            const int32_t e = e0 + k;
+            const int32_t b0 = wbeg[e], t = wend[e];
+            if (t > b0) {
+                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo)
+                                      ? b0 : lower_bound_dev(idxTs, b0, t, it.jlo);
+                if (c < t) {
+                    const int32_t slot = atomicAdd(&sh_n, 1);
+                    if (slot < SP_MAXR) {
+                        cur[slot] = c;
+                        endp[slot] = t;
+                    } else {
+                        atomicOr(err, ERR_TABLE);  // binning admits |e_i| <= 255 only
+                    }
+                }
+            }
+        }
+        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
+        int64_t out_pos = 0;
+        __syncthreads();
+        const int32_t nr = min(sh_n, SP_MAXR);
+        for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += SP_TILE) {
+            const int32_t t1 = min(t0 + SP_TILE, it.jhi);
+            const int32_t span = t1 - t0;
+            // 1. wedges of the tile: one warp per range, 32 entries per step
+            for (int32_t k = warp; k < nr; k += SP_WARPS) {
+                int32_t c = cur[k];
+                const int32_t e = endp[k];
+                for (;;) {
+                    const int32_t p = c + lane;
+                    const int32_t j = p < e ? __ldg(&idxTs[p]) : INT32_MAX;
+                    const bool valid = j < t1;
+                    bool first = false;
+                    int32_t slot = 0;
+                    if (valid) {
+                        slot = j - t0;
+                        const int sh = (slot & 3) << 3;
+                        const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
+                        first = ((old >> sh) & 0xffu) == 0;
+                    }
+                    const unsigned fb = __ballot_sync(0xffffffffu, first);
+                    if (fb) {
+                        int32_t base = 0;
+                        if (lane == 0) base = atomicAdd(&sh_nt, __popc(fb));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const int32_t at = base + __popc(fb & lt);
+                        if (first && at < SP_TOUCH) touched[at] = (uint16_t)slot;
+                    }
+                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
+                    c += n;
+                    if (n < 32) break;
+                }
+                if (lane == 0) cur[k] = c;
+            }
+            __syncthreads();
+            const int32_t nt = sh_nt;
+            const bool listed = nt <= SP_TOUCH;
+            const int32_t nwords = (span + 3) >> 2;
+            // 2. survivors
+            int32_t mine = 0;
+            if (listed) {
+                for (int32_t x = tid; x < nt; x += SP_THREADS) {
+                    const int32_t slot = touched[x];
+                    const int32_t c = (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
+                    if (c >= s) {
+                        ++mine;
+                        if (FILL) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                    }
+                }
+            } else {
+                for (int32_t w = tid; w < nwords; w += SP_THREADS) {
+                    const uint32_t v = ctr[w];
+                    if (!v) continue;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int32_t slot = 4 * w + r;
+                        if (slot < span && (int32_t)((v >> (8 * r)) & 0xffu) >= s) {
+                            ++mine;
+                            if (FILL) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                        }
+                    }
+                }
+            }
+            int32_t tile_total = 0;
+            block_excl_scan<SP_THREADS>(mine, &tile_total, tmp);  // ends with a barrier
+            if (FILL && tile_total > 0) {
+                // 3. rank of a survivor: survivors in earlier bitmap words plus
+                // earlier bits of its own word
+                uint32_t wv[4];
+                int32_t sum = 0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    wv[r] = bm[4 * tid + r];
+                    sum += __popc(wv[r]);
+                }
+                int32_t unused = 0;
+                int32_t acc = block_excl_scan<SP_THREADS>(sum, &unused, tmp);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    wpre[4 * tid + r] = (uint32_t)acc;
+                    acc += __popc(wv[r]);
+                }
+                __syncthreads();
+                const int64_t base = obase + out_pos;
+                auto emit = [&](int32_t slot, int32_t c) {
+                    const uint32_t wb = bm[slot >> 5];
+                    const int64_t p2 =
+                        base + wpre[slot >> 5] + __popc(wb & ((1u << (slot & 31)) - 1u));
+                    if (p2 < limit) {
+                        I[p2] = i - ib;
+                        J[p2] = t0 + slot - ib;
+                        O[p2] = c;
+                    } else {
+                        atomicOr(err, ERR_BOUNDS);
+                    }
+                };
+                if (listed) {
+                    for (int32_t x = tid; x < nt; x += SP_THREADS) {
+                        const int32_t slot = touched[x];
+                        const int32_t c =
+                            (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
+                        if (c >= s) emit(slot, c);
+                    }
+                } else {
+                    for (int32_t w = tid; w < nwords; w += SP_THREADS) {
+                        const uint32_t v = ctr[w];
+                        if (!v) continue;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int32_t slot = 4 * w + r;
+                            const int32_t c = (int32_t)((v >> (8 * r)) & 0xffu);
+                            if (slot < span && c >= s) emit(slot, c);
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
+            }
+            out_pos += tile_total;
+            // 4. clear what the tile used (every read of the counters is done:
+            // the last barrier above follows them)
+            if (listed) {
+                for (int32_t x = tid; x < nt; x += SP_THREADS) ctr[touched[x] >> 2] = 0;
+            } else {
+                for (int32_t w = tid; w < nwords; w += SP_THREADS) ctr[w] = 0;
+            }
+            if (tid == 0) sh_nt = 0;
+            __syncthreads();
+        }
+        if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
+        __syncthreads();
+    }
+}
+
 // =============================================================== digest
 
 // Digest of a window: the pair at window position p belongs to the row whose
@@ -1076,7 +1306,7 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 
 struct Occupancy {
     int sms = 0;
-    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0;
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, sparse_ctas[2] = {};
     int wdense_ctas[2][2] = {};  // [fill][ensemble]
 };
 
@@ -1111,6 +1341,15 @@ void occupancy_init() {
     SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DENSE_SMEM));
+    for (int f = 0; f < 2; ++f) {
+        const size_t smem = sp_smem(f == 1);
+        auto kern = f ? k_sparse_items<true> : k_sparse_items<false>;
+        SLG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        int d = 0;
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, SP_THREADS, smem));
+        o.sparse_ctas[f] = o.sms * (d > 0 ? d : 1);
+    }
     o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
     o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
     o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
@@ -1204,6 +1443,15 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         }
         SLG_LAUNCH_CHECK();
         tick(MODE_WDENSE, 1);
+    }
+    if (want(MODE_SPARSE)) {
+        ran[MODE_SPARSE] = true;
+        tick(MODE_SPARSE, 0);
+        k_sparse_items<FILL><<<oc.sparse_ctas[FILL], SP_THREADS, sp_smem(FILL), st>>>(
+            p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue + MODE_SPARSE, limit, err);
+        SLG_LAUNCH_CHECK();
+        tick(MODE_SPARSE, 1);
     }
     if (timed) {
         for (int k = 0; k < NMODES; ++k) {

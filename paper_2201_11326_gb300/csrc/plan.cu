@@ -138,6 +138,18 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
         r.count = (int32_t)((span + r.step - 1) / r.step);
         return r;
     }
+    const int64_t tiles = (span + SP_TILE - 1) / SP_TILE;
+    if (bp.sparse_min_per_tile >= 0 && size <= SP_MAX_SIZE &&
+        w >= (int64_t)bp.sparse_min_per_tile * tiles) {
+        // uniform j slices of about sparse_item_wedges wedges, at least 1024 ids wide
+        r.mode = MODE_SPARSE;
+        int64_t k = (w + bp.sparse_item_wedges - 1) / bp.sparse_item_wedges;
+        const int64_t kmax = (span + 1023) / 1024;
+        if (k > kmax) k = kmax;
+        if (k < 1) k = 1;
+        r.count = (int32_t)k;
+        return r;
+    }
     r.mode = MODE_BLOCK;
     int64_t k = (w + bp.block_item_wedges - 1) / bp.block_item_wedges;
     if (k > span) k = span;
@@ -308,7 +320,6 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.release(st);
     p.s = s;
     p.rs = RowS{g.srow, g.rbase, s};
-    p.built = true;
     const int64_t nnz = g.nnz;
     const int32_t m = g.m;
     const int T = 256;
@@ -365,6 +376,20 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
                                                    nitem);
         SLG_LAUNCH_CHECK();
     }
+    {
+        // item ids are int32: refuse a binning that would need more
+        int64_t* c64 = dalloc<int64_t>((size_t)m + 1, st);
+        scan_i32_to_i64(nitem, c64, m, st);
+        int64_t total = 0;
+        SLG_CUDA_TRY(cudaMemcpyAsync(&total, c64 + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        SLG_CUDA_TRY(cudaStreamSynchronize(st));
+        dfree(c64, st);
+        if (total > (int64_t)INT32_MAX - 1) {
+            dfree(nitem, st);
+            throw Error{SLG_ECAPACITY, "binning needs more than 2^31 work items: raise "
+                                       "block_item_wedges or sparse_item_wedges"};
+        }
+    }
     scan_i32_to_i32(nitem, p.row_item, m, st);
     dfree(nitem, st);
     int32_t nitems32 = 0;
@@ -410,6 +435,7 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.ioff = dalloc<int64_t>(p.nitems + 1, st);
     p.rowoff = dalloc<int64_t>((size_t)m + 1, st);
     p.counted = false;
+    p.built = true;  // only once complete: a failed build leaves the plan unbuilt
 }
 
 void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st) {

@@ -59,8 +59,10 @@ enum ItemMode : int32_t {
     MODE_WARP = 0,   // whole row, few wedges: one warp, small hash table
     MODE_BLOCK = 1,  // sparse slice: one CTA, shared-memory hash table
     MODE_DENSE = 2,  // dense slice, many non-hub ranges: one CTA, j tiles of 32768
-    MODE_WDENSE = 3, // dense slice, <= 32 non-hub ranges: one warp, j tiles of 2048
-    NMODES = 4
+    MODE_WDENSE = 3, // dense slice, <= 32 non-hub ranges: one warp, j tiles of 4096
+    MODE_SPARSE = 4, // sparse slice of a heavy row (|e_i| <= 255): one CTA, j tiles of
+                     // 65536 8-bit counters and a list of the counters it touched
+    NMODES = 5
 };
 
 struct Item {
@@ -99,6 +101,10 @@ struct BinParams {
     int32_t dense_item_tiles;  // tiles per MODE_DENSE item (x4096 ids per MODE_WDENSE item)
     int32_t wdense_max_ranges; // rows with at most this many non-hub wedge ranges (<= 32)
                                // use the warp-level dense handler; 0 disables it
+    int32_t sparse_min_per_tile;  // a non-dense row with |e_i| <= 255 and at least this many
+                                  // wedges per 65536-id tile of its span goes to MODE_SPARSE
+                                  // (< 0 disables it)
+    int32_t sparse_item_wedges;   // target wedges per MODE_SPARSE item
 };
 
 // ---------------------------------------------------------- kernel sizes
@@ -118,6 +124,10 @@ constexpr int WD_ITEM = 8192;             // j per MODE_WDENSE item = WD_ITEM * 
 constexpr int WD_MAXR = 32;               // non-hub wedge ranges a MODE_WDENSE row may have
 constexpr int DENSE_MAX_SIZE = 65535;     // |e_i| bound for 16-bit counters
 constexpr int ENS_MAX = 16;               // thresholds in one ensemble (Algorithm 3)
+constexpr int SP_THREADS = 512;           // MODE_SPARSE CTA
+constexpr int SP_TILE = 65536;            // j per tile (8-bit counters, 64 KB)
+constexpr int SP_TOUCH = 8192;            // touched counters listed per tile
+constexpr int SP_MAX_SIZE = 255;          // |e_i| bound for 8-bit counters
 
 // --------------------------------------------------------- device helpers
 

@@ -57,7 +57,7 @@ def test_ensemble_medium_recipe_forced_handlers(mode):
     check_ensemble(h, "med6000", [1, 2, 3, 5, 8, 13], FORCED[mode])
 
 
-@pytest.mark.parametrize("mode", ["default", "block_only", "dense_only", "dense_cta_only"])
+@pytest.mark.parametrize("mode", ["default", "block_only", "dense_only", "dense_cta_only", "sparse_only"])
 def test_ensemble_multitile(mode):
     # hub rows whose partners span several j tiles with a ragged tail
     h = synth.striped_hub(3, 70001, 3000, 40)
@@ -140,7 +140,7 @@ def test_ensemble_windows_digests_and_row_offsets():
         g.free()
 
 
-@pytest.mark.parametrize("mode", ["default", "dense_only", "dense_cta_only", "block_only"])
+@pytest.mark.parametrize("mode", ["default", "dense_only", "dense_cta_only", "block_only", "sparse_only"])
 def test_ensemble_one_list_at_a_time(mode):
     # which = t: list t alone, in its own windows, from the shared plan
     h = synth.medium(seed=2, m=6000)

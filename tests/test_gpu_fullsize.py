@@ -90,3 +90,61 @@ def test_medium_full_size_sampled_rows(medium, s):
     if s == 1:
         # every wedge is one unit of some pair's overlap
         assert osum == wedges
+
+
+@pytest.fixture(scope="module")
+def large():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    slg.build.build()
+    h = synth.cached("large_m20000000_seed0", lambda: synth.large(seed=0))
+    return torch, h
+
+
+def test_large_full_size_sampled_rows(large):
+    """The large workload (m = 20,000,000, about 2.7e8 incidences), s in
+    {2, 4, 8, 16}, through windows of 2^33 pairs: per-row counts and digests of
+    120 seeded random rows and the 20 rows with the most wedges at s = 2 equal
+    the oracle's; per-row counts add up to |L_s|; W_s matches its closed form."""
+    torch, h = large
+    dev = torch.device("cuda")
+    s_list = [2, 4, 8, 16]
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    counts, digs = {}, {}
+    try:
+        I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        for s in s_list:
+            pairs, wedges = slg.slg_count(g, s)
+            rowoff = slg.slg_row_offsets(g, s)
+            c = np.diff(rowoff)
+            assert int(c.sum()) == pairs
+            digests = torch.zeros(h.m, dtype=torch.int64, device=dev)
+            splits = slg.slg_plan_windows(g, s, WINDOW)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                P, _ = slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW,
+                                            row_digests=digests[int(r0):int(r1)])
+                assert P == rowoff[r1] - rowoff[r0]
+            counts[s] = c
+            digs[s] = digests.cpu().numpy().view(np.uint64)
+            sz = np.diff(h.off)
+            deg_s = np.bincount(h.idx[np.repeat(sz >= s, sz)], minlength=h.n).astype(np.int64)
+            assert wedges == int((deg_s * (deg_s - 1) // 2).sum())
+    finally:
+        g.free()
+    rng = np.random.default_rng([7, 20])
+    # W_{2,i} (every size is >= 2): for each position p of adj(v), the later
+    # entries of adj(v) are wedges of the row at p
+    offT, idxT = oracle.transpose(h.off, h.idx, h.n)
+    vert = np.repeat(np.arange(h.n, dtype=np.int64), np.diff(offT))
+    later = offT[1:][vert] - np.arange(idxT.size, dtype=np.int64) - 1
+    w = np.bincount(idxT, weights=later, minlength=h.m)
+    heavy = np.argsort(-w, kind="stable")[:20]
+    rows = np.unique(np.concatenate([rng.choice(h.m, size=120, replace=False), heavy]))
+    rows = rows.astype(np.int32)
+    ocount, odig, _ = oracle.rows(h.off, h.idx, rows, s_list)
+    for k, s in enumerate(s_list):
+        assert np.array_equal(counts[s][rows], ocount[:, k]), f"s={s}"
+        assert np.array_equal(digs[s][rows], odig[:, k]), f"s={s}"

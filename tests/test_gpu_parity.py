@@ -18,14 +18,19 @@ pytestmark = pytest.mark.gpu
 
 # bin settings that force one handler onto every row (results must not change)
 FORCED = {
-    "default": (128, 1024, 64, 4, 32),
-    "block_only": (0, 1024, -1, 4, 32),
-    "block_one_item_per_row": (0, 1 << 30, -1, 4, 32),  # big items: exercises the split path
-    "block_tiny_items": (0, 1, -1, 4, 32),
-    "dense_only": (0, 1024, 0, 1, 32),           # warp-level dense where possible
-    "dense_cta_only": (0, 1024, 0, 1, 0),        # CTA-level dense for every dense row
-    "dense_warp_few_ranges": (0, 1024, 0, 3, 2),  # warp dense only for rows with <= 2 ranges
-    "warp_and_block": (128, 256, -1, 4, 32),
+    # (warp_max_wedges, block_item_wedges, dense_min_density, dense_item_tiles,
+    #  wdense_max_ranges, sparse_min_per_tile, sparse_item_wedges)
+    "default": (128, 1024, 64, 4, 32, 64, 65536),
+    "block_only": (0, 1024, -1, 4, 32, -1, 65536),
+    "block_one_item_per_row": (0, 1 << 30, -1, 4, 32, -1, 65536),  # big items: split path
+    "block_tiny_items": (0, 1, -1, 4, 32, -1, 65536),
+    "dense_only": (0, 1024, 0, 1, 32, -1, 65536),           # warp-level dense where possible
+    "dense_cta_only": (0, 1024, 0, 1, 0, -1, 65536),        # CTA-level dense for every dense row
+    "dense_warp_few_ranges": (0, 1024, 0, 3, 2, -1, 65536),  # warp dense only for <= 2 ranges
+    "warp_and_block": (128, 256, -1, 4, 32, -1, 65536),
+    "sparse_only": (0, 1024, -1, 4, 32, 0, 65536),          # sparse accumulator (|e| <= 255)
+    "sparse_tiny_items": (0, 1024, -1, 4, 32, 0, 1),        # one item per 1024 ids
+    "sparse_and_dense": (128, 1024, 64, 4, 32, 0, 4096),
 }
 
 
@@ -113,6 +118,41 @@ def test_forced_handlers_multitile(mode):
     h = synth.striped_hub(3, 70001, 3000, 40)
     for s in (1, 2):
         assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("striped", h, s), f"{mode} s={s}")
+
+
+def _overflow_graph():
+    # row 0 holds vertices 0 and 1: its partners are every 5th and every 7th
+    # row of one 65536-id tile, more than the 8192 touched counters a sparse
+    # tile lists, so that tile's survivors are read off the whole tile
+    m = 65000
+    rng = np.random.default_rng(9)
+    rows = []
+    for i in range(m):
+        r = set(int(x) for x in rng.choice(np.arange(2, 400), size=int(rng.integers(1, 4)),
+                                           replace=False))
+        if i % 5 == 0:
+            r.add(0)
+        if i % 7 == 0:
+            r.add(1)
+        rows.append(sorted(r))
+    off, idx = csr_from_rows(rows)
+    return synth.Hypergraph(off, idx, 400)
+
+
+@pytest.mark.parametrize("mode", ["sparse_only", "sparse_tiny_items", "default"])
+def test_sparse_touched_list_overflow(mode):
+    h = _overflow_graph()
+    for s in (1, 2):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("overflow", h, s), f"{mode} s={s}")
+
+
+@pytest.mark.parametrize("mode", ["default", "sparse_only", "sparse_and_dense", "block_only"])
+def test_large_recipe_scaled_down(mode):
+    # the large workload's recipe (Chung-Lu, degrees Zipf(1.8) capped at 1e5,
+    # log-normal sizes up to 20000) at m = 20000, s as in that workload
+    h = synth.large(m=20000)
+    for s in (2, 4, 8, 16):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("large20000", h, s), f"{mode} s={s}")
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -287,7 +327,7 @@ def _batch_members():
     return hs, s_list
 
 
-@pytest.mark.parametrize("mode", ["default", "block_only", "dense_only", "dense_cta_only"])
+@pytest.mark.parametrize("mode", ["default", "block_only", "dense_only", "dense_cta_only", "sparse_only"])
 def test_batch_members_equal_their_own_lists(mode):
     hs, s_list = _batch_members()
     gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
