@@ -1021,19 +1021,22 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 // in tiles of 65536 ids. Per tile:
 //   1. every wedge of the tile adds 1 to the 8-bit counter of its partner
 //      (|e_i| <= 255 bounds every count); the first increment of a counter
-//      appends it to a list of touched counters;
+//      appends it to a list of touched counters. A warp walks one wedge range
+//      128 entries at a time (four loads in flight per lane);
 //   2. survivors (count >= s) are read off the touched list only (or off the
-//      whole tile when more than SP_TOUCH counters were touched);
+//      whole tile when more than SP_TOUCH counters were touched), and each
+//      counter is cleared as it is read;
 //   3. the fill ranks each survivor by the survivors at lower ids (a bitmap
-//      of the tile and its per-word prefix), so no sort is needed;
-//   4. the touched counters are cleared.
-// Hub vertices are counted like any other here: a partner may share only hubs
-// with e_i, and only a walk over its wedges finds it in a sparse row.
+//      of the tile and its per-word prefix), so no sort is needed.
+// The counting pass needs two CTA barriers per tile. Hub vertices are counted
+// like any other here: a partner may share only hubs with e_i, and only a walk
+// over its wedges finds it in a sparse row.
 
 constexpr int SP_WARPS = SP_THREADS / 32;
 constexpr int SP_WORDS = SP_TILE / 4;   // four 8-bit counters per word
 constexpr int SP_BITS = SP_TILE / 32;   // survivor bitmap words
 constexpr int SP_MAXR = 256;            // wedge ranges of a row (|e_i| <= 255)
+constexpr int SP_UNROLL = 4;            // 32-entry chunks of a range loaded together
 static_assert(SP_MAX_SIZE < 256 && SP_MAXR > SP_MAX_SIZE, "8-bit counters");
 static_assert(SP_TILE <= 65536, "touched counters are listed as 16-bit offsets");
 static_assert(SP_BITS == 4 * SP_THREADS, "bitmap prefix: four words per thread");
@@ -1059,7 +1062,8 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     uint32_t* bm = reinterpret_cast<uint32_t*>(endp + SP_MAXR);           // fill: SP_BITS
     uint32_t* wpre = bm + SP_BITS;                                         // fill: SP_BITS
     __shared__ int32_t tmp[SP_WARPS + 1];
-    __shared__ int32_t sh_pos, sh_n, sh_nt;
+    __shared__ int32_t sh_pos, sh_n;
+    __shared__ int32_t sh_nt[2];  // touched counters of the tile, by tile parity
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
@@ -1072,7 +1076,7 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         if (tid == 0) {
             sh_pos = lo + atomicAdd(queue, 1);
             sh_n = 0;
-            sh_nt = 0;
+            sh_nt[0] = sh_nt[1] = 0;
         }
         __syncthreads();
         const int32_t pos = sh_pos;
@@ -1107,47 +1111,80 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             }
         }
         const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
-        int64_t out_pos = 0;
+        int64_t out_pos = 0;   // fill: the item's pairs before the tile (same in every thread)
+        int32_t my_count = 0;  // counting pass: this thread's survivors so far
         __syncthreads();
         const int32_t nr = min(sh_n, SP_MAXR);
-        for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += SP_TILE) {
+        int par = 0;
+        for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += SP_TILE, par ^= 1) {
             const int32_t t1 = min(t0 + SP_TILE, it.jhi);
             const int32_t span = t1 - t0;
-            // 1. wedges of the tile: one warp per range, 32 entries per step
+            // 1. wedges of the tile: one warp per range, 128 entries per step
             for (int32_t k = warp; k < nr; k += SP_WARPS) {
                 int32_t c = cur[k];
                 const int32_t e = endp[k];
                 for (;;) {
-                    const int32_t p = c + lane;
-                    const int32_t j = p < e ? __ldg(&idxTs[p]) : INT32_MAX;
-                    const bool valid = j < t1;
-                    bool first = false;
-                    int32_t slot = 0;
-                    if (valid) {
-                        slot = j - t0;
-                        const int sh = (slot & 3) << 3;
-                        const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
-                        first = ((old >> sh) & 0xffu) == 0;
+                    int32_t jv[SP_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < SP_UNROLL; ++u) {
+                        const int32_t p = c + 32 * u + lane;
+                        jv[u] = p < e ? __ldg(&idxTs[p]) : INT32_MAX;
                     }
-                    const unsigned fb = __ballot_sync(0xffffffffu, first);
-                    if (fb) {
-                        int32_t base = 0;
-                        if (lane == 0) base = atomicAdd(&sh_nt, __popc(fb));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        const int32_t at = base + __popc(fb & lt);
-                        if (first && at < SP_TOUCH) touched[at] = (uint16_t)slot;
+                    int n = 0;
+#pragma unroll
+                    for (int u = 0; u < SP_UNROLL; ++u) {
+                        const bool valid = jv[u] < t1;
+                        bool first = false;
+                        int32_t slot = 0;
+                        if (valid) {
+                            slot = jv[u] - t0;
+                            const int sh = (slot & 3) << 3;
+                            const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
+                            first = ((old >> sh) & 0xffu) == 0;
+                        }
+                        const unsigned fb = __ballot_sync(0xffffffffu, first);
+                        if (fb) {
+                            int32_t base = 0;
+                            if (lane == 0) base = atomicAdd(&sh_nt[par], __popc(fb));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            const int32_t at = base + __popc(fb & lt);
+                            if (first && at < SP_TOUCH) touched[at] = (uint16_t)slot;
+                        }
+                        n += __popc(__ballot_sync(0xffffffffu, valid));
                     }
-                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
                     c += n;
-                    if (n < 32) break;
+                    if (n < 32 * SP_UNROLL) break;
                 }
                 if (lane == 0) cur[k] = c;
             }
             __syncthreads();
-            const int32_t nt = sh_nt;
+            const int32_t nt = sh_nt[par];
+            if (tid == 0) sh_nt[par ^ 1] = 0;  // for the next tile (last read a tile ago)
             const bool listed = nt <= SP_TOUCH;
             const int32_t nwords = (span + 3) >> 2;
-            // 2. survivors
+            if (!FILL) {
+                // 2. survivors, clearing each counter as it is read
+                if (listed) {
+                    for (int32_t x = tid; x < nt; x += SP_THREADS) {
+                        const int32_t slot = touched[x];
+                        const int sh = (slot & 3) << 3;
+                        const uint32_t old = atomicAnd(&ctr[slot >> 2], ~(0xffu << sh));
+                        my_count += ((int32_t)((old >> sh) & 0xffu) >= s) ? 1 : 0;
+                    }
+                } else {
+                    for (int32_t w = tid; w < nwords; w += SP_THREADS) {
+                        const uint32_t v = ctr[w];
+                        if (!v) continue;
+                        ctr[w] = 0;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            my_count += ((int32_t)((v >> (8 * r)) & 0xffu) >= s) ? 1 : 0;
+                    }
+                }
+                __syncthreads();  // the touched list is refilled by the next tile
+                continue;
+            }
+            // 2. survivors into the bitmap
             int32_t mine = 0;
             if (listed) {
                 for (int32_t x = tid; x < nt; x += SP_THREADS) {
@@ -1155,7 +1192,7 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     const int32_t c = (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
                     if (c >= s) {
                         ++mine;
-                        if (FILL) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                        atomicOr(&bm[slot >> 5], 1u << (slot & 31));
                     }
                 }
             } else {
@@ -1167,78 +1204,75 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         const int32_t slot = 4 * w + r;
                         if (slot < span && (int32_t)((v >> (8 * r)) & 0xffu) >= s) {
                             ++mine;
-                            if (FILL) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
                         }
                     }
                 }
+            }
+            // 3. rank of a survivor: survivors in earlier bitmap words plus
+            // earlier bits of its own word (the scan's barriers order the
+            // bitmap writes above before these reads)
+            uint32_t wv[4];
+            int32_t sum = 0;
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                wv[r] = bm[4 * tid + r];
+                sum += __popc(wv[r]);
             }
             int32_t tile_total = 0;
-            block_excl_scan<SP_THREADS>(mine, &tile_total, tmp);  // ends with a barrier
-            if (FILL && tile_total > 0) {
-                // 3. rank of a survivor: survivors in earlier bitmap words plus
-                // earlier bits of its own word
-                uint32_t wv[4];
-                int32_t sum = 0;
+            int32_t acc = block_excl_scan<SP_THREADS>(sum, &tile_total, tmp);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    wv[r] = bm[4 * tid + r];
-                    sum += __popc(wv[r]);
-                }
-                int32_t unused = 0;
-                int32_t acc = block_excl_scan<SP_THREADS>(sum, &unused, tmp);
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    wpre[4 * tid + r] = (uint32_t)acc;
-                    acc += __popc(wv[r]);
-                }
-                __syncthreads();
-                const int64_t base = obase + out_pos;
-                auto emit = [&](int32_t slot, int32_t c) {
-                    const uint32_t wb = bm[slot >> 5];
-                    const int64_t p2 =
-                        base + wpre[slot >> 5] + __popc(wb & ((1u << (slot & 31)) - 1u));
-                    if (p2 < limit) {
-                        I[p2] = i - ib;
-                        J[p2] = t0 + slot - ib;
-                        O[p2] = c;
-                    } else {
-                        atomicOr(err, ERR_BOUNDS);
-                    }
-                };
-                if (listed) {
-                    for (int32_t x = tid; x < nt; x += SP_THREADS) {
-                        const int32_t slot = touched[x];
-                        const int32_t c =
-                            (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
-                        if (c >= s) emit(slot, c);
-                    }
+            for (int r = 0; r < 4; ++r) {
+                wpre[4 * tid + r] = (uint32_t)acc;
+                acc += __popc(wv[r]);
+            }
+            __syncthreads();
+            const int64_t base = obase + out_pos;
+            auto emit = [&](int32_t slot, int32_t c) {
+                const uint32_t wb = bm[slot >> 5];
+                const int64_t p2 = base + wpre[slot >> 5] + __popc(wb & ((1u << (slot & 31)) - 1u));
+                if (p2 < limit) {
+                    I[p2] = i - ib;
+                    J[p2] = t0 + slot - ib;
+                    O[p2] = c;
                 } else {
-                    for (int32_t w = tid; w < nwords; w += SP_THREADS) {
-                        const uint32_t v = ctr[w];
-                        if (!v) continue;
+                    atomicOr(err, ERR_BOUNDS);
+                }
+            };
+            // survivors are written and every counter of the tile is cleared
+            if (listed) {
+                for (int32_t x = tid; x < nt; x += SP_THREADS) {
+                    const int32_t slot = touched[x];
+                    const int sh = (slot & 3) << 3;
+                    const uint32_t old = atomicAnd(&ctr[slot >> 2], ~(0xffu << sh));
+                    const int32_t c = (int32_t)((old >> sh) & 0xffu);
+                    if (c >= s) emit(slot, c);
+                }
+            } else {
+                for (int32_t w = tid; w < nwords; w += SP_THREADS) {
+                    const uint32_t v = ctr[w];
+                    if (!v) continue;
+                    ctr[w] = 0;
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const int32_t slot = 4 * w + r;
-                            const int32_t c = (int32_t)((v >> (8 * r)) & 0xffu);
-                            if (slot < span && c >= s) emit(slot, c);
-                        }
+                    for (int r = 0; r < 4; ++r) {
+                        const int32_t slot = 4 * w + r;
+                        const int32_t c = (int32_t)((v >> (8 * r)) & 0xffu);
+                        if (slot < span && c >= s) emit(slot, c);
                     }
                 }
-                __syncthreads();
-                for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
             }
             out_pos += tile_total;
-            // 4. clear what the tile used (every read of the counters is done:
-            // the last barrier above follows them)
-            if (listed) {
-                for (int32_t x = tid; x < nt; x += SP_THREADS) ctr[touched[x] >> 2] = 0;
-            } else {
-                for (int32_t w = tid; w < nwords; w += SP_THREADS) ctr[w] = 0;
-            }
-            if (tid == 0) sh_nt = 0;
-            __syncthreads();
+            __syncthreads();  // bitmap reads done; the touched list is refilled next tile
+            if (tile_total > 0)
+                for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
+            // (the next tile's bitmap writes follow its first barrier)
         }
-        if (!FILL && tid == 0) icnt[q] = (int32_t)out_pos;
+        if (!FILL) {
+            int32_t total = 0;
+            block_excl_scan<SP_THREADS>(my_count, &total, tmp);
+            if (tid == 0) icnt[q] = total;
+        }
         __syncthreads();
     }
 }
