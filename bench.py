@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--window", type=int, default=WINDOW, help="pairs per output window")
-    ap.add_argument("--workload", choices=["medium", "batch", "serve", "ensemble"],
+    ap.add_argument("--workload", choices=["medium", "large", "batch", "serve", "ensemble"],
                     default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
     return ap.parse_args()
@@ -74,6 +74,27 @@ def s_values(spec: str):
 def workload(m: int):
     key = f"medium_m{m}_seed0"
     return synth.cached(key, lambda: synth.medium(seed=0, m=m))
+
+
+LARGE_WORKLOAD = ("large hub-heavy: m=20,000,000 hyperedges, n=10,000,000 vertices, sizes "
+                  "log-normal(2.0,1.1) clipped [2,20000], Chung-Lu popularity with vertex degree "
+                  "Zipf(1.8) capped at 100,000, seed 0; s in {2,4,8,16}")
+LARGE_METRIC = "s-line wedges/s (large hub-heavy hypergraph, s in {2,4,8,16}, bit-exact)"
+
+
+def workload_spec(args):
+    """(graph, s list, workload text, metric, CPU-oracle rows) of the timed workload."""
+    if args.workload == "large":
+        m = args.m if args.m != 1_000_000 else 20_000_000
+        h = synth.cached(f"large_m{m}_seed0", lambda: synth.large(seed=0, m=m))
+        s_list = [2, 4, 8, 16] if args.s == "1-8" else s_values(args.s)
+        text = LARGE_WORKLOAD if m == 20_000_000 else f"{LARGE_WORKLOAD} (m={m})"
+        # rows of the large graph meet 20x more partners: a 40-row sample keeps the
+        # CPU baseline to seconds
+        return h, s_list, text, LARGE_METRIC, (40 if args.cpu_rows == 600 else args.cpu_rows)
+    h = workload(args.m)
+    text = WORKLOAD if args.m == 1_000_000 else f"{WORKLOAD} (m={args.m})"
+    return h, s_values(args.s), text, METRIC, args.cpu_rows
 
 
 def host_cores() -> int:
@@ -145,8 +166,9 @@ class Clocks:
 
 # ---------------------------------------------------------------- GPU step
 
-def run_sweep(slg, g, s_list, bufs, stream, per_s):
-    """Counting pass + windowed fill for every s on a loaded graph."""
+def run_sweep(slg, g, s_list, bufs, stream, per_s, mode_work=None):
+    """Counting pass + windowed fill for every s on a loaded graph. With
+    mode_work, each s's per-handler work is recorded after its counting pass."""
     import torch
     I, J, O = bufs
     WINDOW = I.numel()
@@ -155,6 +177,8 @@ def run_sweep(slg, g, s_list, bufs, stream, per_s):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         pairs, wedges = slg.slg_count(g, s)
+        if mode_work is not None:
+            mode_work[s] = slg.slg_mode_stats(g, s)
         splits = slg.slg_plan_windows(g, s, WINDOW)
         for r0, r1 in zip(splits[:-1], splits[1:]):
             slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW)
@@ -177,8 +201,7 @@ def bench_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    s_list = s_values(args.s)
-    h = workload(args.m)
+    h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
     # inputs resident in HBM before the timed region
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)
@@ -188,23 +211,22 @@ def bench_ours(args):
     O = torch.empty_like(I)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    def step(per_s, timing=False):
+    def step(per_s, timing=False, mode_work=None):
         with torch.cuda.stream(stream):
             flush.fill_(0)  # L2 flush: a 512 MiB write
             g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
             if timing:
                 slg.slg_set_timing(g, True)
-            run_sweep(slg, g, s_list, (I, J, O), stream, per_s)
+            run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
             g.free()
         return ks
 
-    for _ in range(args.warmup):
-        step({})
-    # per-handler work of the sweep (for the roofline's algorithmic bytes)
-    g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
-    mode_work = {s: slg.slg_mode_stats(g, s) for s in s_list}
-    g.free()
+    # per-handler work of the sweep (for the roofline's algorithmic bytes),
+    # recorded during the last warm-up step (or the first timed one)
+    mode_work = {}
+    for w in range(args.warmup):
+        step({}, mode_work=mode_work if w == args.warmup - 1 else None)
 
     torch.cuda.synchronize()
     if dist:
@@ -217,8 +239,9 @@ def bench_ours(args):
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t_start.record(stream)
-    for _ in range(args.steps):
-        kstats.append(step(per_s, timing=True))
+    for k in range(args.steps):
+        kstats.append(step(per_s, timing=True,
+                           mode_work=mode_work if (k == 0 and not mode_work) else None))
     t_end.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -300,11 +323,11 @@ def bench_ours(args):
                           "alg_GBps": round(alg / (ms / 1e3) / 1e9, 1)})
 
     out = {
-        "metric": METRIC, "value": value, "unit": "wedges/s", "n_gpus": world,
+        "metric": metric, "value": value, "unit": "wedges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.m == 1_000_000 else f"{WORKLOAD} (m={args.m})",
+        "config": {"workload": wl_text,
                    "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": args.window,
                    "l2": "flushed before each step (512 MiB device write); inputs resident",
                    "parallelism": f"replicas x{world}"},
@@ -318,7 +341,7 @@ def bench_ours(args):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O))
     if rank == 0 and world == 1 and not args.no_cpu:
-        wedges, dt, cores, sample = oracle_sample(h, s_list, args.cpu_rows, seed=1)
+        wedges, dt, cores, sample = oracle_sample(h, s_list, cpu_rows, seed=1)
         out["cpu_baseline"] = {"value": wedges / dt, "unit": "wedges/s", "cores": cores,
                                "kind": "oracle", "sample": sample, "seconds": round(dt, 2)}
     if dist:
@@ -390,9 +413,8 @@ def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    s_list = s_values(args.s)
-    h = workload(args.m)
-    rows = max(16, args.cpu_rows // 4)
+    h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
+    rows = max(8, cpu_rows // 4)
     for k in range(args.warmup):
         oracle_sample(h, s_list, rows, seed=100 + k)
     W = 0
@@ -403,11 +425,11 @@ def bench_reference(args):
         T += dt
     value = W / T
     out = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "wedges/s",
+        "impl": "reference", "metric": metric, "value": value, "unit": "wedges/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": T / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list,
+        "config": {"workload": wl_text, "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list,
                    "parallelism": "cpu oracle, host threads"},
         "cpu_baseline": {"value": value, "unit": "wedges/s", "cores": cores, "kind": "oracle",
                          "sample": f"{rows} random rows per step x s={s_list[0]}..{s_list[-1]}"},
@@ -447,8 +469,12 @@ def bench_batch(args):
     O = torch.empty_like(I)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    tuned_bins = None
+
     def batched():
         b = slg.slg_batch_load(graphs, s_list, stream=stream)
+        if tuned_bins is not None:
+            slg.slg_set_bins(b, *tuned_bins)
         pairs, wedges = slg.slg_count(b, 0)
         for r0, r1 in zip(*(lambda sp: (sp[:-1], sp[1:]))(slg.slg_plan_windows(b, 0, args.window))):
             slg.slg_build_window(b, 0, int(r0), int(r1), I, J, O, args.window)
@@ -479,8 +505,17 @@ def bench_batch(args):
             e1.synchronize()
         return out, e0.elapsed_time(e1), slg.slg_kernel_launches() - l0
 
+    # the autotuner picks the batch's binning once (outside the timed steps)
+    with torch.cuda.stream(stream):
+        b = slg.slg_batch_load(graphs, s_list, stream=stream)
+        t0 = time.perf_counter()
+        tuned, tuned_ms = slg.slg_autotune(b, 0, max_trials=24)
+        tune_s = time.perf_counter() - t0
+        b.free()
     res = {}
-    for name, fn in (("batched", batched), ("sequential", sequential)):
+    for name, fn in (("batched", batched), ("sequential", sequential), ("batched_autotuned", batched)):
+        if name == "batched_autotuned":
+            tuned_bins = tuned
         for _ in range(args.warmup):
             timed(fn)
         times, launches = [], 0
@@ -495,9 +530,10 @@ def bench_batch(args):
     for g in graphs:
         g.free()
     out = {
-        "metric": "batched s-line wedges/s (per-graph s, one batch handle)",
-        "value": res["batched"]["wedges_per_s"], "unit": "wedges/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"]["ms_per_step"],
+        "metric": "batched s-line wedges/s (per-graph s, one batch handle, autotuned bins)",
+        "value": res["batched_autotuned"]["wedges_per_s"], "unit": "wedges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["batched_autotuned"]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD.format(k=k), "graphs": k,
@@ -505,7 +541,9 @@ def bench_batch(args):
                    "nnz": int(sum(h.nnz for h, _ in members)), "window_pairs": args.window,
                    "generation_s": round(gen_s, 1)},
         "batched": res["batched"], "sequential": res["sequential"],
-        "speedup_vs_sequential": res["batched"]["wedges_per_s"] / res["sequential"]["wedges_per_s"],
+        "batched_autotuned": dict(res["batched_autotuned"], bins=tuned, tuning_s=round(tune_s, 1)),
+        "speedup_vs_sequential": (res["batched_autotuned"]["wedges_per_s"]
+                                  / res["sequential"]["wedges_per_s"]),
     }
     print(json.dumps(out), flush=True)
 
@@ -747,6 +785,8 @@ def main():
         bench_serve(args)
     elif args.workload == "ensemble":
         bench_ensemble(args)
+    elif args.workload == "large":
+        bench_ours(args)
     else:
         bench_ours(args)
 

@@ -441,6 +441,27 @@ slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_ite
                         int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
                         int32_t sparse_item_wedges);
 
+/*
+ * slg_autotune -- choose the binning thresholds of slg_set_bins for s on this
+ * graph by measurement (the paper tunes its ranges, chunking and relabelling by
+ * hand, Sections III-F and IV). Coordinate descent from the current thresholds:
+ * each knob in turn is tried over a short list of values, keeping any value
+ * that lowers the time. A trial times, with CUDA events on the graph's stream,
+ * the planning, the counting pass and the fill of sample row windows spread over
+ * the graph (at most 2^26 pairs, written to a 768 MiB scratch buffer).
+ *
+ *   s          : the threshold to tune for (0 for a batch handle).
+ *   max_trials : at most this many trials (the first times the current
+ *                thresholds); a trial costs about one counting pass.
+ *   bins_out   : NULL or 7 int32 entries: the chosen thresholds, in
+ *                slg_set_bins' argument order.
+ *   ms_out     : NULL or the chosen thresholds' trial time in ms.
+ * The thresholds stay set on the handle; results never depend on them.
+ * Errors: SLG_EINVAL for a bad s or max_trials < 1.
+ */
+slg_status slg_autotune(slg_graph* g, int32_t s, int32_t max_trials, int32_t* bins_out,
+                        float* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

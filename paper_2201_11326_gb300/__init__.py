@@ -24,7 +24,7 @@ __all__ = [
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
-    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -102,6 +102,7 @@ _SIGS = {
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
     "slg_kernel_launches": (_i64, []),
@@ -541,3 +542,14 @@ def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 
     _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
                               dense_item_tiles, wdense_max_ranges, sparse_min_per_tile,
                               sparse_item_wedges))
+
+
+def slg_autotune(g: Graph, s: int, max_trials: int = 24):
+    """Pick the binning thresholds for s by timing them on g (kept on g).
+
+    Returns (thresholds in slg_set_bins order, trial time in ms)."""
+    bins = np.zeros(7, np.int32)
+    ms = ctypes.c_float()
+    _check(lib().slg_autotune(g.handle, s, max_trials, bins.ctypes.data_as(_i32p),
+                              ctypes.byref(ms)))
+    return [int(x) for x in bins], ms.value

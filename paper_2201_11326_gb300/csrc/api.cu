@@ -55,18 +55,6 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <typename T>
-T* dalloc(size_t count, cudaStream_t st) {
-    T* p = nullptr;
-    SLG_CUDA_TRY(cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st));
-    return p;
-}
-
-template <typename T>
-void dfree(T*& p, cudaStream_t st) {
-    if (p) cudaFreeAsync(p, st);
-    p = nullptr;
-}
 
 }  // namespace
 
@@ -706,6 +694,23 @@ slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_ite
     h->bp.sparse_min_per_tile = sparse_min_per_tile;
     h->bp.sparse_item_wedges = sparse_item_wedges;
     h->plan.release(h->st);
+    API_END
+}
+
+slg_status slg_autotune(slg_graph* h, int32_t s, int32_t max_trials, int32_t* bins_out,
+                        float* ms_out) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (max_trials < 1) return fail(SLG_EINVAL, "max_trials must be >= 1");
+    API_BEGIN
+    check_s(h, s);
+    slg::autotune(h, s, max_trials, ms_out);
+    if (bins_out) {
+        const slg::BinParams& b = h->bp;
+        const int32_t v[7] = {b.warp_max_wedges,   b.block_item_wedges,   b.dense_min_density,
+                              b.dense_item_tiles,  b.wdense_max_ranges,   b.sparse_min_per_tile,
+                              b.sparse_item_wedges};
+        for (int c = 0; c < 7; ++c) bins_out[c] = v[c];
+    }
     API_END
 }
 

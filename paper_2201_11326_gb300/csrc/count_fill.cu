@@ -25,28 +25,13 @@
 #include <cstdio>
 #include <mutex>
 
+#include "kernel_util.cuh"
 #include "plan.cuh"
 
 namespace slg {
 namespace {
 
 constexpr int32_t EMPTY = -1;
-constexpr int32_t ERR_BOUNDS = 1;  // a fill write fell outside the window
-constexpr int32_t ERR_TABLE = 2;   // a table had no free slot
-constexpr int32_t ERR_DIGEST = 4;  // a pair's row lay outside the window
-
-__device__ __forceinline__ int32_t lower_bound_dev(const int32_t* __restrict__ a, int32_t lo,
-                                                   int32_t hi, int32_t x) {
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (a[mid] < x)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 // Fibonacci hashing of a hyperedge id into a table of 2^(32-shift) slots.
 __device__ __forceinline__ uint32_t slot_of(int32_t j, int shift) {
     return ((uint32_t)j * 2654435761u) >> shift;
@@ -82,36 +67,6 @@ __device__ __forceinline__ int table_add(int32_t* keys, int32_t* cnts, uint32_t 
         h = (h + 1) & mask;
     }
     return -1;
-}
-
-template <int NT>
-__device__ __forceinline__ int32_t block_excl_scan(int32_t x, int32_t* total, int32_t* tmp) {
-    // tmp: NT/32 + 1 ints of shared memory
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t inc = x;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-    }
-    if (lane == 31) tmp[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int32_t v = lane < NT / 32 ? tmp[lane] : 0;
-        int32_t vi = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, vi, d);
-            if (lane >= d) vi += y;
-        }
-        if (lane < NT / 32) tmp[lane] = vi - v;
-        if (lane == NT / 32 - 1) tmp[NT / 32] = vi;
-    }
-    __syncthreads();
-    const int32_t r = tmp[w] + inc - x;
-    *total = tmp[NT / 32];
-    __syncthreads();
-    return r;
 }
 
 // Several thresholds in one launch (an ensemble, Algorithm 3): the counting
@@ -1013,270 +968,6 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     }
 }
 
-// ========================================================== MODE_SPARSE
-//
-// Rows whose partners are spread thinly over a wide id range (wedges through
-// many high-degree vertices, density far below the dense handlers' bar): a
-// sparse accumulator per CTA. One item is a j slice of one row; it is walked
-// in tiles of 65536 ids. Per tile:
-//   1. every wedge of the tile adds 1 to the 8-bit counter of its partner
-//      (|e_i| <= 255 bounds every count); the first increment of a counter
-//      appends it to a list of touched counters. A warp walks one wedge range
-//      128 entries at a time (four loads in flight per lane);
-//   2. survivors (count >= s) are read off the touched list only (or off the
-//      whole tile when more than SP_TOUCH counters were touched), and each
-//      counter is cleared as it is read;
-//   3. the fill ranks each survivor by the survivors at lower ids (a bitmap
-//      of the tile and its per-word prefix), so no sort is needed.
-// The counting pass needs two CTA barriers per tile. Hub vertices are counted
-// like any other here: a partner may share only hubs with e_i, and only a walk
-// over its wedges finds it in a sparse row.
-
-constexpr int SP_WARPS = SP_THREADS / 32;
-constexpr int SP_WORDS = SP_TILE / 4;   // four 8-bit counters per word
-constexpr int SP_BITS = SP_TILE / 32;   // survivor bitmap words
-constexpr int SP_MAXR = 256;            // wedge ranges of a row (|e_i| <= 255)
-constexpr int SP_UNROLL = 4;            // 32-entry chunks of a range loaded together
-static_assert(SP_MAX_SIZE < 256 && SP_MAXR > SP_MAX_SIZE, "8-bit counters");
-static_assert(SP_TILE <= 65536, "touched counters are listed as 16-bit offsets");
-static_assert(SP_BITS == 4 * SP_THREADS, "bitmap prefix: four words per thread");
-constexpr size_t sp_smem(bool fill) {
-    return sizeof(uint32_t) * SP_WORDS + sizeof(uint16_t) * SP_TOUCH +
-           sizeof(int32_t) * 2 * SP_MAXR + (fill ? sizeof(uint32_t) * 2 * SP_BITS : 0);
-}
-
-template <bool FILL>
-__global__ void __launch_bounds__(SP_THREADS, 2)
-k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
-               const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
-               const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
-               const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
-               int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
-               int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
-               int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
-    extern __shared__ __align__(16) uint32_t dyn[];
-    uint32_t* ctr = dyn;                                                   // SP_WORDS
-    uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + SP_WORDS);      // SP_TOUCH
-    int32_t* cur = reinterpret_cast<int32_t*>(touched + SP_TOUCH);        // SP_MAXR
-    int32_t* endp = cur + SP_MAXR;                                         // SP_MAXR
-    uint32_t* bm = reinterpret_cast<uint32_t*>(endp + SP_MAXR);           // fill: SP_BITS
-    uint32_t* wpre = bm + SP_BITS;                                         // fill: SP_BITS
-    __shared__ int32_t tmp[SP_WARPS + 1];
-    __shared__ int32_t sh_pos, sh_n;
-    __shared__ int32_t sh_nt[2];  // touched counters of the tile, by tile parity
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int32_t lo = rank[item_lo], hi = rank[item_hi];
-    // the counters (and the fill's bitmap) start at zero; every tile leaves them so
-    for (int32_t w = tid; w < SP_WORDS; w += SP_THREADS) ctr[w] = 0;
-    if (FILL)
-        for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
-
-    for (;;) {
-        if (tid == 0) {
-            sh_pos = lo + atomicAdd(queue, 1);
-            sh_n = 0;
-            sh_nt[0] = sh_nt[1] = 0;
-        }
-        __syncthreads();
-        const int32_t pos = sh_pos;
-        if (pos >= hi) break;
-        const int32_t q = list[pos];
-        if (FILL && ioff[q + 1] == ioff[q]) {  // nothing to write (same in every thread)
-            __syncthreads();
-            continue;
-        }
-        const Item it = items[q];
-        const int32_t i = it.row;
-        const int32_t s = rs.s_of(i);
-        const int32_t ib = rs.base_of(i);
-        const int32_t e0 = off[i];
-        const int32_t ne = off[i + 1] - e0;
-        // wedge ranges of the row, cursors at the item's first partner
-        for (int32_t k = tid; k < ne; k += SP_THREADS) {
-            const int32_t e = e0 + k;
-            const int32_t b0 = wbeg[e], t = wend[e];
-            if (t > b0) {
-                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo)
-                                      ? b0 : lower_bound_dev(idxTs, b0, t, it.jlo);
-                if (c < t) {
-                    const int32_t slot = atomicAdd(&sh_n, 1);
-                    if (slot < SP_MAXR) {
-                        cur[slot] = c;
-                        endp[slot] = t;
-                    } else {
-                        atomicOr(err, ERR_TABLE);  // binning admits |e_i| <= 255 only
-                    }
-                }
-            }
-        }
-        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
-        int64_t out_pos = 0;   // fill: the item's pairs before the tile (same in every thread)
-        int32_t my_count = 0;  // counting pass: this thread's survivors so far
-        __syncthreads();
-        const int32_t nr = min(sh_n, SP_MAXR);
-        int par = 0;
-        for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += SP_TILE, par ^= 1) {
-            const int32_t t1 = min(t0 + SP_TILE, it.jhi);
-            const int32_t span = t1 - t0;
-            // 1. wedges of the tile: one warp per range, 128 entries per step
-            for (int32_t k = warp; k < nr; k += SP_WARPS) {
-                int32_t c = cur[k];
-                const int32_t e = endp[k];
-                for (;;) {
-                    int32_t jv[SP_UNROLL];
-#pragma unroll
-                    for (int u = 0; u < SP_UNROLL; ++u) {
-                        const int32_t p = c + 32 * u + lane;
-                        jv[u] = p < e ? __ldg(&idxTs[p]) : INT32_MAX;
-                    }
-                    int n = 0;
-#pragma unroll
-                    for (int u = 0; u < SP_UNROLL; ++u) {
-                        const bool valid = jv[u] < t1;
-                        bool first = false;
-                        int32_t slot = 0;
-                        if (valid) {
-                            slot = jv[u] - t0;
-                            const int sh = (slot & 3) << 3;
-                            const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
-                            first = ((old >> sh) & 0xffu) == 0;
-                        }
-                        const unsigned fb = __ballot_sync(0xffffffffu, first);
-                        if (fb) {
-                            int32_t base = 0;
-                            if (lane == 0) base = atomicAdd(&sh_nt[par], __popc(fb));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            const int32_t at = base + __popc(fb & lt);
-                            if (first && at < SP_TOUCH) touched[at] = (uint16_t)slot;
-                        }
-                        n += __popc(__ballot_sync(0xffffffffu, valid));
-                    }
-                    c += n;
-                    if (n < 32 * SP_UNROLL) break;
-                }
-                if (lane == 0) cur[k] = c;
-            }
-            __syncthreads();
-            const int32_t nt = sh_nt[par];
-            if (tid == 0) sh_nt[par ^ 1] = 0;  // for the next tile (last read a tile ago)
-            const bool listed = nt <= SP_TOUCH;
-            const int32_t nwords = (span + 3) >> 2;
-            if (!FILL) {
-                // 2. survivors, clearing each counter as it is read
-                if (listed) {
-                    for (int32_t x = tid; x < nt; x += SP_THREADS) {
-                        const int32_t slot = touched[x];
-                        const int sh = (slot & 3) << 3;
-                        const uint32_t old = atomicAnd(&ctr[slot >> 2], ~(0xffu << sh));
-                        my_count += ((int32_t)((old >> sh) & 0xffu) >= s) ? 1 : 0;
-                    }
-                } else {
-                    for (int32_t w = tid; w < nwords; w += SP_THREADS) {
-                        const uint32_t v = ctr[w];
-                        if (!v) continue;
-                        ctr[w] = 0;
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            my_count += ((int32_t)((v >> (8 * r)) & 0xffu) >= s) ? 1 : 0;
-                    }
-                }
-                __syncthreads();  // the touched list is refilled by the next tile
-                continue;
-            }
-            // 2. survivors into the bitmap
-            int32_t mine = 0;
-            if (listed) {
-                for (int32_t x = tid; x < nt; x += SP_THREADS) {
-                    const int32_t slot = touched[x];
-                    const int32_t c = (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
-                    if (c >= s) {
-                        ++mine;
-                        atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                    }
-                }
-            } else {
-                for (int32_t w = tid; w < nwords; w += SP_THREADS) {
-                    const uint32_t v = ctr[w];
-                    if (!v) continue;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int32_t slot = 4 * w + r;
-                        if (slot < span && (int32_t)((v >> (8 * r)) & 0xffu) >= s) {
-                            ++mine;
-                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                        }
-                    }
-                }
-            }
-            // 3. rank of a survivor: survivors in earlier bitmap words plus
-            // earlier bits of its own word (the scan's barriers order the
-            // bitmap writes above before these reads)
-            uint32_t wv[4];
-            int32_t sum = 0;
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                wv[r] = bm[4 * tid + r];
-                sum += __popc(wv[r]);
-            }
-            int32_t tile_total = 0;
-            int32_t acc = block_excl_scan<SP_THREADS>(sum, &tile_total, tmp);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                wpre[4 * tid + r] = (uint32_t)acc;
-                acc += __popc(wv[r]);
-            }
-            __syncthreads();
-            const int64_t base = obase + out_pos;
-            auto emit = [&](int32_t slot, int32_t c) {
-                const uint32_t wb = bm[slot >> 5];
-                const int64_t p2 = base + wpre[slot >> 5] + __popc(wb & ((1u << (slot & 31)) - 1u));
-                if (p2 < limit) {
-                    I[p2] = i - ib;
-                    J[p2] = t0 + slot - ib;
-                    O[p2] = c;
-                } else {
-                    atomicOr(err, ERR_BOUNDS);
-                }
-            };
-            // survivors are written and every counter of the tile is cleared
-            if (listed) {
-                for (int32_t x = tid; x < nt; x += SP_THREADS) {
-                    const int32_t slot = touched[x];
-                    const int sh = (slot & 3) << 3;
-                    const uint32_t old = atomicAnd(&ctr[slot >> 2], ~(0xffu << sh));
-                    const int32_t c = (int32_t)((old >> sh) & 0xffu);
-                    if (c >= s) emit(slot, c);
-                }
-            } else {
-                for (int32_t w = tid; w < nwords; w += SP_THREADS) {
-                    const uint32_t v = ctr[w];
-                    if (!v) continue;
-                    ctr[w] = 0;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int32_t slot = 4 * w + r;
-                        const int32_t c = (int32_t)((v >> (8 * r)) & 0xffu);
-                        if (slot < span && c >= s) emit(slot, c);
-                    }
-                }
-            }
-            out_pos += tile_total;
-            __syncthreads();  // bitmap reads done; the touched list is refilled next tile
-            if (tile_total > 0)
-                for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
-            // (the next tile's bitmap writes follow its first barrier)
-        }
-        if (!FILL) {
-            int32_t total = 0;
-            block_excl_scan<SP_THREADS>(my_count, &total, tmp);
-            if (tid == 0) icnt[q] = total;
-        }
-        __syncthreads();
-    }
-}
-
 // =============================================================== digest
 
 // Digest of a window: the pair at window position p belongs to the row whose
@@ -1375,15 +1066,7 @@ void occupancy_init() {
     SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DENSE_SMEM));
-    for (int f = 0; f < 2; ++f) {
-        const size_t smem = sp_smem(f == 1);
-        auto kern = f ? k_sparse_items<true> : k_sparse_items<false>;
-        SLG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        int d = 0;
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, SP_THREADS, smem));
-        o.sparse_ctas[f] = o.sms * (d > 0 ? d : 1);
-    }
+    sparse_setup(o.sms, o.sparse_ctas);
     o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
     o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
     o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
@@ -1481,10 +1164,8 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
     if (want(MODE_SPARSE)) {
         ran[MODE_SPARSE] = true;
         tick(MODE_SPARSE, 0);
-        k_sparse_items<FILL><<<oc.sparse_ctas[FILL], SP_THREADS, sp_smem(FILL), st>>>(
-            p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue + MODE_SPARSE, limit, err);
-        SLG_LAUNCH_CHECK();
+        launch_sparse(FILL, oc.sparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J, O,
+                      queue + MODE_SPARSE, limit, err, st);
         tick(MODE_SPARSE, 1);
     }
     if (timed) {

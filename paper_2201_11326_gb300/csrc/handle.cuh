@@ -41,4 +41,8 @@ namespace slg {
 // own plan and stream, so that several s of one graph can run concurrently.
 slg_graph* make_view(const slg_graph* base, cudaStream_t st);
 
+// Chooses h->bp for s by timing binnings on h (autotune.cu); the plan is left
+// released.
+void autotune(slg_graph* h, int32_t s, int32_t max_trials, float* best_ms);
+
 }  // namespace slg

@@ -264,18 +264,6 @@ __global__ void k_sum_rows(const int64_t* __restrict__ rowoff, int32_t k, int32_
     }
 }
 
-template <typename T>
-T* dalloc(size_t count, cudaStream_t st) {
-    T* p = nullptr;
-    SLG_CUDA_TRY(cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st));
-    return p;
-}
-
-template <typename T>
-void dfree(T*& p, cudaStream_t st) {
-    if (p) SLG_CUDA_TRY(cudaFreeAsync(p, st));
-    p = nullptr;
-}
 
 }  // namespace
 

@@ -126,6 +126,13 @@ void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStr
 void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
                        const int64_t* seg, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
                        ModeTimer* mt, cudaStream_t st);
+// Sparse-accumulator handler (sparse.cu): kernel attributes and CTAs per
+// launch (count, fill), and one launch over the MODE_SPARSE items.
+void sparse_setup(int sms, int ctas[2]);
+void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
+                   int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
+                   int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
+                   int32_t* err, cudaStream_t st);
 // Per-handler totals over rows: rows, wedges, incidences, pairs (needs counts).
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).

@@ -48,6 +48,21 @@ void count_launch();
         SLG_CUDA_TRY(cudaGetLastError());     \
     } while (0)
 
+// Stream-ordered device allocation (released in stream order; a null pointer
+// is ignored, and a failed release is not reported: it runs on cleanup paths).
+template <typename T>
+T* dalloc(size_t count, cudaStream_t st) {
+    T* p = nullptr;
+    SLG_CUDA_TRY(cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st));
+    return p;
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+}
+
 // ------------------------------------------------------------ work items
 //
 // A work item is one row i restricted to candidate partners j in [jlo, jhi).

@@ -361,3 +361,37 @@ def test_batch_members_equal_their_own_lists(mode):
         b.free()
         for g in gs:
             g.free()
+
+
+def test_autotune_keeps_results():
+    # the autotuner only changes how rows are binned; lists must stay identical
+    h = synth.medium(seed=2, m=6000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        bins, ms = slg.slg_autotune(g, 2, max_trials=8)
+        assert len(bins) == 7 and ms > 0
+        assert bins[3] >= 1 and bins[6] >= 1
+        assert_same(slg.slg_build(g, 2), oracle_list("med6000", h, 2), f"autotuned {bins}")
+        assert_same(slg.slg_build(g, 3), oracle_list("med6000", h, 3), f"autotuned {bins}")
+        with pytest.raises(slg.SlgError) as e:
+            slg.slg_autotune(g, 0, max_trials=4)
+        assert e.value.code == slg.SLG_EINVAL
+    finally:
+        g.free()
+
+
+def test_autotune_batch_handle():
+    hs, s_list = _batch_members()
+    graphs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    b = slg.slg_batch_load(graphs, s_list)
+    try:
+        bins, _ = slg.slg_autotune(b, 0, max_trials=6)
+        base = slg.slg_batch_pair_offsets(b)
+        I, J, O = slg.slg_build(b, 0)
+        for k, (h, s) in enumerate(zip(hs, s_list)):
+            got = (I[base[k]:base[k + 1]], J[base[k]:base[k + 1]], O[base[k]:base[k + 1]])
+            assert_same(got, oracle.slg(h.off, h.idx, s), f"member {k} autotuned {bins}")
+    finally:
+        b.free()
+        for g in graphs:
+            g.free()
