@@ -250,14 +250,15 @@ slg_status slg_last_timing(slg_graph* g, float* ms5);
 
 /*
  * Number of handlers (SLG_NMODES): 0 = warp table, 1 = CTA table, 2 = CTA
- * dense tiles, 3 = warp dense tiles, 4 = CTA sparse accumulator.
+ * dense tiles, 3 = warp dense tiles, 4 = CTA sparse accumulator, 5 = warp
+ * sparse accumulator.
  *
  * Per-handler kernel time accumulated while timing is enabled:
  * ms[pass*SLG_NMODES + mode] and launches[pass*SLG_NMODES + mode] (2 *
  * SLG_NMODES entries each), pass 0 = counting, 1 = fill. reset != 0 zeroes
  * the totals after reading. Either output may be NULL.
  */
-#define SLG_NMODES 5
+#define SLG_NMODES 6
 slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms, int64_t* launches);
 
 /*
@@ -428,10 +429,12 @@ slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int6
  *     non-hub vertices goes to the warp-level dense handler (items of
  *     8192 * dense_item_tiles ids), other dense rows to the CTA-level one
  *     (items of 32768 * dense_item_tiles ids);
- *   - by a CTA sparse accumulator (8-bit counters over 65536-id tiles and a
- *     list of the counters touched) when |e_i| <= 255 and W_i >=
- *     sparse_min_per_tile * ceil(S_i / 65536) (< 0 disables it), in items of
- *     about sparse_item_wedges wedges;
+ *   - by a sparse accumulator (8-bit counters over id tiles and a list of the
+ *     counters touched) when |e_i| <= 255 and W_i >= sparse_min_per_tile *
+ *     ceil(S_i / 65536) (< 0 disables it), in items of about
+ *     sparse_item_wedges wedges: one warp with 4096-id tiles when |e_i| <=
+ *     wsparse_max_size (<= 32; 0 disables it), else one CTA with 65536-id
+ *     tiles;
  *   - otherwise by CTA hash tables, about block_item_wedges wedges per item.
  * Results do not depend on these values; only speed does. Resets the plan.
  * SLG_ECAPACITY from a later call when a binning needs 2^31 items or more.
@@ -439,7 +442,7 @@ slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int6
 slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_item_wedges,
                         int32_t dense_min_density, int32_t dense_item_tiles,
                         int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
-                        int32_t sparse_item_wedges);
+                        int32_t sparse_item_wedges, int32_t wsparse_max_size);
 
 /*
  * slg_autotune -- choose the binning thresholds of slg_set_bins for s on this
@@ -453,7 +456,7 @@ slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_ite
  *   s          : the threshold to tune for (0 for a batch handle).
  *   max_trials : at most this many trials (the first times the current
  *                thresholds); a trial costs about one counting pass.
- *   bins_out   : NULL or 7 int32 entries: the chosen thresholds, in
+ *   bins_out   : NULL or 8 int32 entries: the chosen thresholds, in
  *                slg_set_bins' argument order.
  *   ms_out     : NULL or the chosen thresholds' trial time in ms.
  * The thresholds stay set on the handle; results never depend on them.

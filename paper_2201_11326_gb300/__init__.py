@@ -101,7 +101,7 @@ _SIGS = {
                                          _i64, _i64p, _u64p, _vp]),
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
-    "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
     "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
@@ -388,8 +388,8 @@ def slg_last_timing(g: Graph):
     return list(ms)
 
 
-NMODES = 5
-MODE_NAMES = ("warp", "block", "dense", "wdense", "sparse")
+NMODES = 6
+MODE_NAMES = ("warp", "block", "dense", "wdense", "sparse", "wsparse")
 
 
 def slg_kernel_stats(g: Graph, reset: bool = False):
@@ -538,17 +538,17 @@ def slg_scan_counts_noalloc(counts, offsets, stream=None):
 def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 1024,
                  dense_min_density: int = 64, dense_item_tiles: int = 4,
                  wdense_max_ranges: int = 32, sparse_min_per_tile: int = 64,
-                 sparse_item_wedges: int = 65536):
+                 sparse_item_wedges: int = 65536, wsparse_max_size: int = 32):
     _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
                               dense_item_tiles, wdense_max_ranges, sparse_min_per_tile,
-                              sparse_item_wedges))
+                              sparse_item_wedges, wsparse_max_size))
 
 
 def slg_autotune(g: Graph, s: int, max_trials: int = 24):
     """Pick the binning thresholds for s by timing them on g (kept on g).
 
     Returns (thresholds in slg_set_bins order, trial time in ms)."""
-    bins = np.zeros(7, np.int32)
+    bins = np.zeros(8, np.int32)
     ms = ctypes.c_float()
     _check(lib().slg_autotune(g.handle, s, max_trials, bins.ctypes.data_as(_i32p),
                               ctypes.byref(ms)))

@@ -67,6 +67,7 @@ BinParams default_bins() {
     b.wdense_max_ranges = WD_MAXR;
     b.sparse_min_per_tile = 64;
     b.sparse_item_wedges = 65536;
+    b.wsparse_max_size = WS_MAXE;
     return b;
 }
 
@@ -679,11 +680,12 @@ slg_status slg_last_timing(slg_graph* h, float* ms5) {
 slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_item_wedges,
                         int32_t dense_min_density, int32_t dense_item_tiles,
                         int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
-                        int32_t sparse_item_wedges) {
+                        int32_t sparse_item_wedges, int32_t wsparse_max_size) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     if (warp_max_wedges < 0 || warp_max_wedges > slg::WARP_TABLE / 2 || block_item_wedges < 1 ||
         dense_item_tiles < 1 || dense_item_tiles > 4096 || wdense_max_ranges < 0 ||
-        wdense_max_ranges > slg::WD_MAXR || sparse_item_wedges < 1)
+        wdense_max_ranges > slg::WD_MAXR || sparse_item_wedges < 1 || wsparse_max_size < 0 ||
+        wsparse_max_size > slg::WS_MAXE)
         return fail(SLG_EINVAL, "bin parameter out of range");
     API_BEGIN
     h->bp.warp_max_wedges = warp_max_wedges;
@@ -693,6 +695,7 @@ slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_ite
     h->bp.wdense_max_ranges = wdense_max_ranges;
     h->bp.sparse_min_per_tile = sparse_min_per_tile;
     h->bp.sparse_item_wedges = sparse_item_wedges;
+    h->bp.wsparse_max_size = wsparse_max_size;
     h->plan.release(h->st);
     API_END
 }
@@ -706,10 +709,10 @@ slg_status slg_autotune(slg_graph* h, int32_t s, int32_t max_trials, int32_t* bi
     slg::autotune(h, s, max_trials, ms_out);
     if (bins_out) {
         const slg::BinParams& b = h->bp;
-        const int32_t v[7] = {b.warp_max_wedges,   b.block_item_wedges,   b.dense_min_density,
-                              b.dense_item_tiles,  b.wdense_max_ranges,   b.sparse_min_per_tile,
-                              b.sparse_item_wedges};
-        for (int c = 0; c < 7; ++c) bins_out[c] = v[c];
+        const int32_t v[8] = {b.warp_max_wedges,     b.block_item_wedges, b.dense_min_density,
+                              b.dense_item_tiles,    b.wdense_max_ranges, b.sparse_min_per_tile,
+                              b.sparse_item_wedges,  b.wsparse_max_size};
+        for (int c = 0; c < 8; ++c) bins_out[c] = v[c];
     }
     API_END
 }

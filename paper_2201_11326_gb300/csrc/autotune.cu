@@ -101,6 +101,7 @@ void autotune(slg_graph* h, int32_t s, int32_t max_trials, float* best_ms_out) {
         {&BinParams::wdense_max_ranges, {8, 16, 32}},
         {&BinParams::block_item_wedges, {256, 1024, 4096}},
         {&BinParams::warp_max_wedges, {32, 64, 128}},
+        {&BinParams::wsparse_max_size, {0, 16, 32}},
     };
     BinParams best = h->bp;
     float best_ms = 0;

@@ -1031,7 +1031,7 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 
 struct Occupancy {
     int sms = 0;
-    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, sparse_ctas[2] = {};
+    int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, sparse_ctas[2] = {}, wsparse_ctas[2] = {};
     int wdense_ctas[2][2] = {};  // [fill][ensemble]
 };
 
@@ -1067,6 +1067,7 @@ void occupancy_init() {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DENSE_SMEM));
     sparse_setup(o.sms, o.sparse_ctas);
+    wsparse_setup(o.sms, o.wsparse_ctas);
     o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
     o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
     o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
@@ -1167,6 +1168,13 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         launch_sparse(FILL, oc.sparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J, O,
                       queue + MODE_SPARSE, limit, err, st);
         tick(MODE_SPARSE, 1);
+    }
+    if (want(MODE_WSPARSE)) {
+        ran[MODE_WSPARSE] = true;
+        tick(MODE_WSPARSE, 0);
+        launch_wsparse(FILL, oc.wsparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J,
+                       O, queue + MODE_WSPARSE, limit, err, st);
+        tick(MODE_WSPARSE, 1);
     }
     if (timed) {
         for (int k = 0; k < NMODES; ++k) {

@@ -142,7 +142,7 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
     if (bp.sparse_min_per_tile >= 0 && size <= SP_MAX_SIZE &&
         w >= (int64_t)bp.sparse_min_per_tile * tiles) {
         // uniform j slices of about sparse_item_wedges wedges, at least 1024 ids wide
-        r.mode = MODE_SPARSE;
+        r.mode = size <= bp.wsparse_max_size ? MODE_WSPARSE : MODE_SPARSE;
         int64_t k = (w + bp.sparse_item_wedges - 1) / bp.sparse_item_wedges;
         const int64_t kmax = (span + 1023) / 1024;
         if (k > kmax) k = kmax;

@@ -129,6 +129,11 @@ void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_
 // Sparse-accumulator handler (sparse.cu): kernel attributes and CTAs per
 // launch (count, fill), and one launch over the MODE_SPARSE items.
 void sparse_setup(int sms, int ctas[2]);
+void wsparse_setup(int sms, int ctas[2]);
+void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
+                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
+                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
+                    int32_t* err, cudaStream_t st);
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,

@@ -77,7 +77,8 @@ enum ItemMode : int32_t {
     MODE_WDENSE = 3, // dense slice, <= 32 non-hub ranges: one warp, j tiles of 4096
     MODE_SPARSE = 4, // sparse slice of a heavy row (|e_i| <= 255): one CTA, j tiles of
                      // 65536 8-bit counters and a list of the counters it touched
-    NMODES = 5
+    MODE_WSPARSE = 5,// the same for rows with |e_i| <= 32: one warp, j tiles of 4096
+    NMODES = 6
 };
 
 struct Item {
@@ -119,7 +120,9 @@ struct BinParams {
     int32_t sparse_min_per_tile;  // a non-dense row with |e_i| <= 255 and at least this many
                                   // wedges per 65536-id tile of its span goes to MODE_SPARSE
                                   // (< 0 disables it)
-    int32_t sparse_item_wedges;   // target wedges per MODE_SPARSE item
+    int32_t sparse_item_wedges;   // target wedges per MODE_SPARSE / MODE_WSPARSE item
+    int32_t wsparse_max_size;     // sparse rows with |e_i| <= this (<= 32) use the warp-level
+                                  // accumulator; 0 disables it
 };
 
 // ---------------------------------------------------------- kernel sizes
@@ -143,6 +146,7 @@ constexpr int SP_THREADS = 512;           // MODE_SPARSE CTA
 constexpr int SP_TILE = 65536;            // j per tile (8-bit counters, 64 KB)
 constexpr int SP_TOUCH = 8192;            // touched counters listed per tile
 constexpr int SP_MAX_SIZE = 255;          // |e_i| bound for 8-bit counters
+constexpr int WS_MAXE = 32;               // |e_i| bound of MODE_WSPARSE (one range per lane)
 
 // --------------------------------------------------------- device helpers
 

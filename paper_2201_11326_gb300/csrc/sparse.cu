@@ -315,6 +315,264 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     }
 }
 
+// ========================================================= MODE_WSPARSE
+//
+// The sparse accumulator at warp granularity, for sparse rows with at most 32
+// vertices (one wedge range per lane): a warp owns an item and a private tile
+// of 4096 8-bit counters, so many tiles are in flight per SM and no CTA barrier
+// is ever taken. Per tile (which starts at the smallest next partner of any
+// range, so empty stretches of the id range cost nothing):
+//   1. ranges with a partner inside the tile load 32 entries each, four
+//      ranges per round, and count them; a counter's first increment appends
+//      it to the warp's touched list;
+//   2. survivors are read off the touched list (or the whole tile when it
+//      overflows); the counting pass adds them up, the fill marks them in a
+//      bitmap of the tile;
+//   3. fill: the bitmap is walked in id order, four partners per lane, and
+//      survivors go through a ring to 128-byte-aligned chunk stores, as in the
+//      warp dense handler;
+//   4. the touched counters are cleared.
+
+constexpr int WS_WARPS = 16;
+constexpr int WS_TILE = 4096;
+constexpr int WS_WORDS = WS_TILE / 4;   // four 8-bit counters per word
+constexpr int WS_BITS = WS_TILE / 32;   // survivor bitmap words (fill)
+constexpr int WS_TOUCH = 256;           // touched counters listed per tile
+constexpr int WS_RING = 256;            // fill: survivors waiting for an aligned store
+constexpr int WS_GROUP = 4;             // ranges loaded together per round
+static_assert(WS_BITS == 4 * 32, "the bitmap walk takes four partners per lane and round");
+static_assert(WS_MAXE <= 32 && WS_MAXE < 256, "one range per lane; 8-bit counts");
+// fill: the ring keeps ids (32 bits) and counts (8 bits) in separate arrays
+constexpr size_t ws_warp_words(bool fill) {
+    return WS_WORDS + WS_TOUCH / 2 + (fill ? WS_BITS + WS_RING + WS_RING / 4 : 0);
+}
+constexpr size_t ws_smem(bool fill) { return sizeof(uint32_t) * ws_warp_words(fill) * WS_WARPS; }
+
+template <bool FILL>
+__global__ void __launch_bounds__(WS_WARPS * 32, FILL ? 2 : 3)
+k_wsparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
+                const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
+                const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
+                const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
+                int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
+                int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
+                int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+    extern __shared__ __align__(16) uint32_t dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* ctr = dyn + (size_t)warp * ws_warp_words(FILL);           // WS_WORDS
+    uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + WS_WORDS);    // WS_TOUCH
+    uint32_t* bm = reinterpret_cast<uint32_t*>(touched + WS_TOUCH);     // fill: WS_BITS
+    int32_t* ring_j = reinterpret_cast<int32_t*>(bm + WS_BITS);          // fill: WS_RING
+    uint8_t* ring_o = reinterpret_cast<uint8_t*>(ring_j + WS_RING);      // fill: WS_RING
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t lo = rank[item_lo], hi = rank[item_hi];
+    for (int32_t w = lane; w < WS_WORDS; w += 32) ctr[w] = 0;
+    if (FILL)
+        for (int32_t w = lane; w < WS_BITS; w += 32) bm[w] = 0;
+    __syncwarp();
+
+    for (;;) {
+        int32_t pos = 0;
+        if (lane == 0) pos = lo + atomicAdd(queue, 1);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (pos >= hi) break;
+        const int32_t q = list[pos];
+        if (FILL && ioff[q + 1] == ioff[q]) continue;  // nothing to write
+        const Item it = items[q];
+        const int32_t i = it.row;
+        const int32_t s = rs.s_of(i);
+        const int32_t ib = rs.base_of(i);
+        const int32_t e0 = off[i];
+        const int32_t ne = off[i + 1] - e0;
+        if (ne > 32 && lane == 0) atomicOr(err, ERR_TABLE);  // binning admits |e_i| <= 32
+        // lane k holds the wedge range of the row's k-th vertex, cursor at jlo
+        int32_t cur = 0, end = 0, nxt = INT32_MAX;
+        if (lane < ne) {
+            const int32_t e = e0 + lane;
+            const int32_t b0 = wbeg[e], t = wend[e];
+            if (t > b0) {
+                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo)
+                                      ? b0 : lower_bound_dev(idxTs, b0, t, it.jlo);
+                if (c < t) {
+                    cur = c;
+                    end = t;
+                    nxt = __ldg(&idxTs[c]);
+                }
+            }
+        }
+        int64_t wpos = FILL ? ioff[q] - ioff[item_lo] : 0;  // next output position
+        int32_t rhead = 0, rcount = 0;
+        int32_t need = FILL ? 32 - (int32_t)((reinterpret_cast<uintptr_t>(I + wpos) >> 2) & 31) : 32;
+        int32_t my_count = 0;
+        for (;;) {
+            const int32_t t0 = __reduce_min_sync(0xffffffffu, nxt);  // next partner of any range
+            if (t0 >= it.jhi) break;
+            const int32_t t1 = min(t0 + WS_TILE, it.jhi);
+            const int32_t span = t1 - t0;
+            // 1. wedges of the tile
+            unsigned act = __ballot_sync(0xffffffffu, nxt < t1);
+            int32_t nt = 0;  // counters touched (same in every lane)
+            while (act) {
+                int32_t kk[WS_GROUP], vv[WS_GROUP];
+                unsigned aa = act;
+#pragma unroll
+                for (int g = 0; g < WS_GROUP; ++g) {
+                    int32_t k = -1;
+                    if (aa) {
+                        k = __ffs(aa) - 1;
+                        aa &= aa - 1u;
+                    }
+                    kk[g] = k;
+                    const int32_t c = __shfl_sync(0xffffffffu, cur, k & 31);
+                    const int32_t e = __shfl_sync(0xffffffffu, end, k & 31);
+                    const int32_t p = c + lane;
+                    vv[g] = (k >= 0 && p < e) ? __ldg(&idxTs[p]) : INT32_MAX;
+                }
+#pragma unroll
+                for (int g = 0; g < WS_GROUP; ++g) {
+                    const int32_t k = kk[g];
+                    if (k < 0) break;
+                    const bool valid = vv[g] < t1;
+                    bool first = false;
+                    int32_t slot = 0;
+                    if (valid) {
+                        slot = vv[g] - t0;
+                        const int sh = (slot & 3) << 3;
+                        const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
+                        first = ((old >> sh) & 0xffu) == 0;
+                    }
+                    const unsigned fb = __ballot_sync(0xffffffffu, first);
+                    if (fb) {
+                        const int32_t at = nt + __popc(fb & lt);
+                        if (first && at < WS_TOUCH) touched[at] = (uint16_t)slot;
+                        nt += __popc(fb);
+                    }
+                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
+                    // the first entry not taken is the range's next partner
+                    const int32_t nx = __shfl_sync(0xffffffffu, vv[g], n & 31);
+                    if (lane == k) {
+                        cur += n;
+                        if (n < 32) nxt = nx;
+                    }
+                    if (n < 32) act &= ~(1u << k);
+                }
+            }
+            __syncwarp();
+            const bool listed = nt <= WS_TOUCH;
+            const int32_t nwords = (span + 3) >> 2;
+            // 2. survivors
+            if (listed) {
+                for (int32_t x = lane; x < nt; x += 32) {
+                    const int32_t slot = touched[x];
+                    const int32_t c = (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
+                    if (c >= s) {
+                        if (FILL)
+                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                        else
+                            ++my_count;
+                    }
+                }
+            } else {
+                for (int32_t w = lane; w < nwords; w += 32) {
+                    const uint32_t v = ctr[w];
+                    if (!v) continue;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int32_t slot = 4 * w + r;
+                        if (slot < span && (int32_t)((v >> (8 * r)) & 0xffu) >= s) {
+                            if (FILL)
+                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                            else
+                                ++my_count;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (FILL) {
+                // 3. survivors in id order: round r covers partners 128r .. 128r+127,
+                // lane l the four partners 128r + 4l .. 128r + 4l + 3 (one counter word);
+                // only rounds whose four bitmap words hold a survivor are visited
+                const uint32_t b4 = bm[4 * lane] | bm[4 * lane + 1] | bm[4 * lane + 2] | bm[4 * lane + 3];
+                for (unsigned rounds = __ballot_sync(0xffffffffu, b4 != 0); rounds;
+                     rounds &= rounds - 1u) {
+                    const int32_t r = __ffs(rounds) - 1;
+                    const uint32_t nib = (bm[4 * r + (lane >> 3)] >> ((lane & 7) * 4)) & 0xfu;
+                    const uint32_t cw = nib ? ctr[32 * r + lane] : 0u;
+                    const int32_t mine = __popc(nib);
+                    int32_t inc = mine;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (lane >= d) inc += y;
+                    }
+                    const int32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+                    int32_t slot = rhead + rcount + inc - mine;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if ((nib >> b) & 1u) {
+                            ring_j[slot & (WS_RING - 1)] = t0 + 128 * r + 4 * lane + b;
+                            ring_o[slot & (WS_RING - 1)] = (uint8_t)((cw >> (8 * b)) & 0xffu);
+                            ++slot;
+                        }
+                    }
+                    rcount += tot;
+                    __syncwarp();
+                    while (rcount >= need) {
+                        if (lane < need) {
+                            const int32_t x = (rhead + lane) & (WS_RING - 1);
+                            const int64_t p2 = wpos + lane;
+                            if (p2 < limit) {
+                                I[p2] = i - ib;
+                                J[p2] = ring_j[x] - ib;
+                                O[p2] = ring_o[x];
+                            } else {
+                                atomicOr(err, ERR_BOUNDS);
+                            }
+                        }
+                        rhead = (rhead + need) & (WS_RING - 1);
+                        rcount -= need;
+                        wpos += need;
+                        need = 32;
+                    }
+                    __syncwarp();
+                }
+                if (b4) {  // clear this lane's four words
+                    bm[4 * lane] = 0;
+                    bm[4 * lane + 1] = 0;
+                    bm[4 * lane + 2] = 0;
+                    bm[4 * lane + 3] = 0;
+                }
+            }
+            // 4. clear what the tile used (every read above is done)
+            if (listed) {
+                for (int32_t x = lane; x < nt; x += 32) ctr[touched[x] >> 2] = 0;
+            } else {
+                for (int32_t w = lane; w < nwords; w += 32) ctr[w] = 0;
+            }
+            __syncwarp();
+        }
+        if (FILL && rcount > 0) {  // the item's last, partial chunk
+            if (lane < rcount) {
+                const int32_t x = (rhead + lane) & (WS_RING - 1);
+                const int64_t p2 = wpos + lane;
+                if (p2 < limit) {
+                    I[p2] = i - ib;
+                    J[p2] = ring_j[x] - ib;
+                    O[p2] = ring_o[x];
+                } else {
+                    atomicOr(err, ERR_BOUNDS);
+                }
+            }
+            __syncwarp();
+        }
+        if (!FILL) {
+            const int32_t total = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)my_count);
+            if (lane == 0) icnt[q] = total;
+        }
+    }
+}
+
 }  // namespace
 
 void sparse_setup(int sms, int ctas[2]) {
@@ -327,6 +585,33 @@ void sparse_setup(int sms, int ctas[2]) {
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, SP_THREADS, smem));
         ctas[f] = sms * (d > 0 ? d : 1);
     }
+}
+
+void wsparse_setup(int sms, int ctas[2]) {
+    for (int f = 0; f < 2; ++f) {
+        const size_t smem = ws_smem(f == 1);
+        auto kern = f ? k_wsparse_items<true> : k_wsparse_items<false>;
+        SLG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        int d = 0;
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, WS_WARPS * 32, smem));
+        ctas[f] = sms * (d > 0 ? d : 1);
+    }
+}
+
+void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
+                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
+                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
+                    int32_t* err, cudaStream_t st) {
+    if (fill)
+        k_wsparse_items<true><<<ctas, WS_WARPS * 32, ws_smem(true), st>>>(
+            p.items, p.mode_list[MODE_WSPARSE], p.mode_rank[MODE_WSPARSE], item_lo, item_hi,
+            g.off, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
+    else
+        k_wsparse_items<false><<<ctas, WS_WARPS * 32, ws_smem(false), st>>>(
+            p.items, p.mode_list[MODE_WSPARSE], p.mode_rank[MODE_WSPARSE], item_lo, item_hi,
+            g.off, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
+    SLG_LAUNCH_CHECK();
 }
 
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,

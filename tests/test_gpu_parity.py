@@ -19,18 +19,19 @@ pytestmark = pytest.mark.gpu
 # bin settings that force one handler onto every row (results must not change)
 FORCED = {
     # (warp_max_wedges, block_item_wedges, dense_min_density, dense_item_tiles,
-    #  wdense_max_ranges, sparse_min_per_tile, sparse_item_wedges)
-    "default": (128, 1024, 64, 4, 32, 64, 65536),
-    "block_only": (0, 1024, -1, 4, 32, -1, 65536),
-    "block_one_item_per_row": (0, 1 << 30, -1, 4, 32, -1, 65536),  # big items: split path
-    "block_tiny_items": (0, 1, -1, 4, 32, -1, 65536),
-    "dense_only": (0, 1024, 0, 1, 32, -1, 65536),           # warp-level dense where possible
-    "dense_cta_only": (0, 1024, 0, 1, 0, -1, 65536),        # CTA-level dense for every dense row
-    "dense_warp_few_ranges": (0, 1024, 0, 3, 2, -1, 65536),  # warp dense only for <= 2 ranges
-    "warp_and_block": (128, 256, -1, 4, 32, -1, 65536),
-    "sparse_only": (0, 1024, -1, 4, 32, 0, 65536),          # sparse accumulator (|e| <= 255)
-    "sparse_tiny_items": (0, 1024, -1, 4, 32, 0, 1),        # one item per 1024 ids
-    "sparse_and_dense": (128, 1024, 64, 4, 32, 0, 4096),
+    #  wdense_max_ranges, sparse_min_per_tile, sparse_item_wedges, wsparse_max_size)
+    "default": (128, 1024, 64, 4, 32, 64, 65536, 32),
+    "block_only": (0, 1024, -1, 4, 32, -1, 65536, 32),
+    "block_one_item_per_row": (0, 1 << 30, -1, 4, 32, -1, 65536, 32),  # big items: split path
+    "block_tiny_items": (0, 1, -1, 4, 32, -1, 65536, 32),
+    "dense_only": (0, 1024, 0, 1, 32, -1, 65536, 32),           # warp-level dense where possible
+    "dense_cta_only": (0, 1024, 0, 1, 0, -1, 65536, 32),        # CTA-level dense for every dense row
+    "dense_warp_few_ranges": (0, 1024, 0, 3, 2, -1, 65536, 32),  # warp dense only for <= 2 ranges
+    "warp_and_block": (128, 256, -1, 4, 32, -1, 65536, 32),
+    "sparse_only": (0, 1024, -1, 4, 32, 0, 65536, 32),          # warp sparse (|e| <= 32), else CTA
+    "sparse_cta_only": (0, 1024, -1, 4, 32, 0, 65536, 0),       # CTA sparse for |e| <= 255
+    "sparse_tiny_items": (0, 1024, -1, 4, 32, 0, 1, 32),        # one item per 1024 ids
+    "sparse_and_dense": (128, 1024, 64, 4, 32, 0, 4096, 32),
 }
 
 
@@ -139,14 +140,15 @@ def _overflow_graph():
     return synth.Hypergraph(off, idx, 400)
 
 
-@pytest.mark.parametrize("mode", ["sparse_only", "sparse_tiny_items", "default"])
+@pytest.mark.parametrize("mode", ["sparse_only", "sparse_cta_only", "sparse_tiny_items", "default"])
 def test_sparse_touched_list_overflow(mode):
     h = _overflow_graph()
     for s in (1, 2):
         assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("overflow", h, s), f"{mode} s={s}")
 
 
-@pytest.mark.parametrize("mode", ["default", "sparse_only", "sparse_and_dense", "block_only"])
+@pytest.mark.parametrize("mode", ["default", "sparse_only", "sparse_cta_only", "sparse_and_dense",
+                                  "block_only"])
 def test_large_recipe_scaled_down(mode):
     # the large workload's recipe (Chung-Lu, degrees Zipf(1.8) capped at 1e5,
     # log-normal sizes up to 20000) at m = 20000, s as in that workload
@@ -369,7 +371,7 @@ def test_autotune_keeps_results():
     g = slg.slg_load(h.off, h.idx, h.m, h.n)
     try:
         bins, ms = slg.slg_autotune(g, 2, max_trials=8)
-        assert len(bins) == 7 and ms > 0
+        assert len(bins) == 8 and ms > 0
         assert bins[3] >= 1 and bins[6] >= 1
         assert_same(slg.slg_build(g, 2), oracle_list("med6000", h, 2), f"autotuned {bins}")
         assert_same(slg.slg_build(g, 3), oracle_list("med6000", h, 3), f"autotuned {bins}")
