@@ -744,7 +744,10 @@ def bench_serve(args):
                 "s_edges_per_s": st["pairs_per_s"], "span_s": round(st["span_s"], 2)}
 
     res = {}
-    arms = (("served", dict(workers=8, policy=1, small_workers=2, small_wedges=2_000_000_000)),
+    arms = (("served", dict(workers=8, policy=1, small_workers=2, small_wedges=2_000_000_000,
+                            batch_max=8)),
+            ("served_unbatched", dict(workers=8, policy=1, small_workers=2,
+                                      small_wedges=2_000_000_000)),
             ("served_fifo", dict(workers=8, policy=0)),
             ("one_at_a_time", dict(workers=1, policy=0)))
     for name, kw in arms:
@@ -767,10 +770,12 @@ def bench_serve(args):
         "higher_is_better": False, "dtype": "int32", "data": "synthetic",
         "config": {"workload": SERVE_WORKLOAD, "queries_per_rate": nq, "rates": rates,
                    "workers": 8, "policy": "least predicted W_s first, 2 of 8 workers for "
-                   "queries with W_s <= 2e9", "memory_budget_GiB": 64, "window_pairs": 1 << 28,
+                   "queries with W_s <= 2e9, up to 8 such queries per batch",
+                   "memory_budget_GiB": 64, "window_pairs": 1 << 28,
                    "max_result_pairs": 1 << 26, "generation_s": round(gen_s, 1),
                    "rows": int(sum(h.m for h in hs)), "nnz": int(sum(h.nnz for h in hs))},
-        "served": served, "served_fifo": res["served_fifo"], "one_at_a_time": loop,
+        "served": served, "served_unbatched": res["served_unbatched"],
+        "served_fifo": res["served_fifo"], "one_at_a_time": loop,
     }
     print(json.dumps(out), flush=True)
 

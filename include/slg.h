@@ -322,7 +322,15 @@ slg_status slg_batch_pair_offsets(slg_graph* b, int64_t* pair_base);
  * taken in submission order (policy 0) or smallest predicted W_s first
  * (policy 1), skipping one that does not fit yet; small_workers of the workers
  * take only queries predicted at most small_wedges wedges, so that short
- * queries are not queued behind long ones.
+ * queries are not queued behind long ones. With batch_max > 1, a worker that
+ * takes a small query (W_s <= small_wedges, s <= max_s) also takes up to
+ * batch_max - 1 more pending small queries that fit, of any graphs and s, and
+ * runs them as one batch (slg_batch_load: one plan, one counting pass, one
+ * fill); each query's result, counts and digest are the same as when it runs
+ * alone. A batch finishes as a whole, so its members are the smallest pending
+ * small queries, each predicted at most 4 times the first query's W_s (or at
+ * most 2^26 wedges). Queries that arrive while others run join the next batch
+ * (continuous batching).
  */
 typedef struct slg_server slg_server;
 
@@ -335,8 +343,8 @@ typedef struct {
     int32_t digest;           /* nonzero: compute each result's digest (slg_build_window) */
     int32_t policy;           /* 0: submission order; 1: smallest predicted W_s first */
     int32_t small_workers;    /* workers that only take queries with W_s <= small_wedges */
-    int32_t reserved0;
-    int64_t small_wedges;     /* threshold for the small-query workers */
+    int32_t batch_max;        /* small queries run together, at most this many (<= 1: none) */
+    int64_t small_wedges;     /* threshold of small queries (small workers, batching) */
 } slg_serve_cfg;
 
 typedef struct {

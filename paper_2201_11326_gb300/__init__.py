@@ -62,7 +62,7 @@ class ServeCfg(ctypes.Structure):
                 ("max_result_pairs", ctypes.c_int64), ("workers", ctypes.c_int32),
                 ("max_s", ctypes.c_int32), ("digest", ctypes.c_int32),
                 ("policy", ctypes.c_int32), ("small_workers", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("small_wedges", ctypes.c_int64)]
+                ("batch_max", ctypes.c_int32), ("small_wedges", ctypes.c_int64)]
 
 
 class ServeResult(ctypes.Structure):
@@ -455,9 +455,9 @@ class Server:
 
     def __init__(self, memory_budget: int, window_pairs: int, max_result_pairs: int,
                  workers: int = 4, max_s: int = 16, digest: bool = True, policy: int = 0,
-                 small_workers: int = 0, small_wedges: int = 0):
+                 small_workers: int = 0, small_wedges: int = 0, batch_max: int = 0):
         cfg = ServeCfg(memory_budget, window_pairs, max_result_pairs, workers, max_s,
-                       1 if digest else 0, policy, small_workers, 0, small_wedges)
+                       1 if digest else 0, policy, small_workers, batch_max, small_wedges)
         h = _vp()
         _check(lib().slg_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h.value
@@ -477,9 +477,10 @@ class Server:
 
 def slg_serve_create(memory_budget: int, window_pairs: int, max_result_pairs: int,
                      workers: int = 4, max_s: int = 16, digest: bool = True, policy: int = 0,
-                     small_workers: int = 0, small_wedges: int = 0) -> Server:
+                     small_workers: int = 0, small_wedges: int = 0,
+                     batch_max: int = 0) -> Server:
     return Server(memory_budget, window_pairs, max_result_pairs, workers, max_s, digest, policy,
-                  small_workers, small_wedges)
+                  small_workers, small_wedges, batch_max)
 
 
 def slg_serve_destroy(srv: Server):

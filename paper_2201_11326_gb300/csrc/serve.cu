@@ -12,7 +12,9 @@
 // computed for every graph and s <= max_s at registration. Results larger
 // than max_result_pairs are streamed through the worker's window and return
 // their counts and digest only. Queries are taken in arrival order, skipping a
-// query whose reservation does not fit until memory is released.
+// query whose reservation does not fit until memory is released. Small queries
+// may be run several at a time as one batch (the disjoint union with per-row s,
+// slg_batch_load), which shares one plan, counting pass and fill among them.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -27,6 +29,9 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// a query this small (predicted wedges) may join any batch of small queries
+constexpr int64_t BATCH_TINY_WEDGES = (int64_t)1 << 26;
 
 struct ServeQuery {
     int32_t graph = 0, s = 0;
@@ -134,6 +139,81 @@ void run_query(slg_server* S, Worker& W, ServeQuery& Q) {
     SLG_CUDA_TRY(cudaStreamSynchronize(W.st));
 }
 
+// Several small queries as one batch on the worker: the batch's list (every
+// member's list in member order, member-local ids) is filled into the
+// worker's window in one pass; each member's pairs, digest (the sum of its
+// rows' digests) and, when kept, its slice of the window are taken from there.
+// Returns false, leaving the queries untouched, when the lists together do
+// not fit the window.
+bool run_batch(slg_server* S, Worker& W, std::vector<ServeQuery>& Qs) {
+    const int32_t k = (int32_t)Qs.size();
+    std::vector<slg_graph*> gs((size_t)k);
+    std::vector<int32_t> ss((size_t)k);
+    for (int32_t b = 0; b < k; ++b) {
+        gs[(size_t)b] = S->graphs[(size_t)Qs[(size_t)b].graph];
+        ss[(size_t)b] = Qs[(size_t)b].s;
+    }
+    slg_graph* bh = nullptr;
+    slg_status rc = slg_batch_load(gs.data(), ss.data(), k, W.st, &bh);
+    if (rc != SLG_OK) throw slg::Error{rc, slg_last_error()};
+    struct Free {
+        slg_graph* v;
+        ~Free() { slg_free(v); }
+    } guard{bh};
+    int64_t total = 0;
+    rc = slg_count(bh, 0, &total, nullptr);
+    if (rc != SLG_OK) throw slg::Error{rc, slg_last_error()};
+    if (total > S->cfg.window_pairs) return false;
+    std::vector<int64_t> pbase((size_t)k + 1);
+    std::vector<int32_t> rbase((size_t)k + 1);
+    int32_t kk = 0;
+    if ((rc = slg_batch_pair_offsets(bh, pbase.data())) != SLG_OK ||
+        (rc = slg_batch_info(bh, &kk, rbase.data())) != SLG_OK)
+        throw slg::Error{rc, slg_last_error()};
+    const int32_t M = bh->g.m;
+    uint64_t* rowdig = nullptr;
+    if (S->cfg.digest) SLG_CUDA_TRY(cudaMallocAsync((void**)&rowdig, sizeof(uint64_t) * ((size_t)M + 1), W.st));
+    struct FreeDev {
+        uint64_t* p;
+        cudaStream_t st;
+        ~FreeDev() { if (p) cudaFreeAsync(p, st); }
+    } guard2{rowdig, W.st};
+    if (rowdig) SLG_CUDA_TRY(cudaMemsetAsync(rowdig, 0, sizeof(uint64_t) * ((size_t)M + 1), W.st));
+    int64_t P = 0;
+    rc = slg_build_window(bh, 0, 0, M, W.wI, W.wJ, W.wO, S->cfg.window_pairs, &P, nullptr, rowdig);
+    if (rc != SLG_OK) throw slg::Error{rc, slg_last_error()};
+    std::vector<uint64_t> dig(rowdig ? (size_t)M : 0);
+    if (rowdig)
+        SLG_CUDA_TRY(cudaMemcpyAsync(dig.data(), rowdig, sizeof(uint64_t) * (size_t)M,
+                                     cudaMemcpyDeviceToHost, W.st));
+    for (int32_t b = 0; b < k; ++b) {
+        ServeQuery& Q = Qs[(size_t)b];
+        Q.pairs = pbase[(size_t)b + 1] - pbase[(size_t)b];
+        Q.wedges = predicted_wedges(S, Q.graph, Q.s);  // exact: s <= max_s
+        if (Q.reserved > 0 && Q.pairs <= S->cfg.max_result_pairs) {
+            const size_t n = (size_t)std::max<int64_t>(Q.pairs, 1);
+            SLG_CUDA_TRY(cudaMallocAsync((void**)&Q.I, sizeof(int32_t) * n, W.st));
+            SLG_CUDA_TRY(cudaMallocAsync((void**)&Q.J, sizeof(int32_t) * n, W.st));
+            SLG_CUDA_TRY(cudaMallocAsync((void**)&Q.O, sizeof(int32_t) * n, W.st));
+            Q.materialized = true;
+            const size_t bytes = sizeof(int32_t) * (size_t)Q.pairs;
+            if (bytes) {
+                const int64_t at = pbase[(size_t)b];
+                SLG_CUDA_TRY(cudaMemcpyAsync(Q.I, W.wI + at, bytes, cudaMemcpyDeviceToDevice, W.st));
+                SLG_CUDA_TRY(cudaMemcpyAsync(Q.J, W.wJ + at, bytes, cudaMemcpyDeviceToDevice, W.st));
+                SLG_CUDA_TRY(cudaMemcpyAsync(Q.O, W.wO + at, bytes, cudaMemcpyDeviceToDevice, W.st));
+            }
+        }
+    }
+    SLG_CUDA_TRY(cudaStreamSynchronize(W.st));
+    for (int32_t b = 0; b < k && rowdig; ++b) {
+        uint64_t d = 0;
+        for (int32_t r = rbase[(size_t)b]; r < rbase[(size_t)b + 1]; ++r) d += dig[(size_t)r];
+        Qs[(size_t)b].digest = d;
+    }
+    return true;
+}
+
 void free_result(ServeQuery& Q, cudaStream_t st) {
     if (Q.I) cudaFreeAsync(Q.I, st);
     if (Q.J) cudaFreeAsync(Q.J, st);
@@ -144,6 +224,7 @@ void free_result(ServeQuery& Q, cudaStream_t st) {
 void worker_loop(slg_server* S, size_t wi) {
     Worker& W = S->workers[wi];
     cudaSetDevice(S->device);
+    std::vector<uint64_t> tickets;
     for (;;) {
         uint64_t ticket = 0;
         {
@@ -169,39 +250,88 @@ void worker_loop(slg_server* S, size_t wi) {
                 }
                 S->cv_work.wait(lk);
             }
-            ServeQuery& Q = S->q[ticket];
-            S->mem_in_use += Q.reserved;
+            tickets.assign(1, ticket);
+            int64_t held = S->q[ticket].reserved;
+            // a small query takes other pending small queries along (any graph, any s)
+            auto small = [&](const ServeQuery& X) {
+                return X.work <= S->cfg.small_wedges && X.s <= S->cfg.max_s;
+            };
+            if (S->cfg.batch_max > 1 && small(S->q[ticket])) {
+                // members of similar size: a batch finishes as a whole, so the
+                // smallest pending queries go first, each predicted at most four
+                // times the first query's work (or tiny outright)
+                const int64_t cap = std::max<int64_t>(4 * S->q[ticket].work, BATCH_TINY_WEDGES);
+                std::vector<std::pair<int64_t, uint64_t>> cand;
+                for (uint64_t t : S->pending) {
+                    const ServeQuery& X = S->q[t];
+                    if (small(X) && X.work <= cap) cand.emplace_back(X.work, t);
+                }
+                std::sort(cand.begin(), cand.end());
+                for (const auto& c : cand) {
+                    if ((int32_t)tickets.size() >= S->cfg.batch_max) break;
+                    const ServeQuery& X = S->q[c.second];
+                    if (S->mem_in_use + held + X.reserved > S->cfg.memory_budget) continue;
+                    held += X.reserved;
+                    tickets.push_back(c.second);
+                    S->pending.erase(std::find(S->pending.begin(), S->pending.end(), c.second));
+                }
+            }
+            const Clock::time_point now = Clock::now();
+            for (uint64_t t : tickets) {
+                ServeQuery& Q = S->q[t];
+                S->mem_in_use += Q.reserved;
+                Q.started = true;
+                Q.t_start = now;
+            }
             S->mem_peak = std::max(S->mem_peak, S->mem_in_use);
-            Q.started = true;
-            Q.t_start = Clock::now();
-            S->busy += 1;
+            S->busy += (int)tickets.size();
         }
-        ServeQuery local;
+        std::vector<ServeQuery> local(tickets.size());
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            local = S->q[ticket];
+            for (size_t x = 0; x < tickets.size(); ++x) local[x] = S->q[tickets[x]];
         }
-        try {
-            run_query(S, W, local);
-            local.status = SLG_OK;
-        } catch (const slg::Error& e) {
-            local.status = e.code;
-            local.error = e.msg;
-            free_result(local, W.st);
-            local.materialized = false;
+        bool batched = false;
+        if (local.size() > 1) {
+            try {
+                batched = run_batch(S, W, local);
+                for (ServeQuery& Q : local) Q.status = SLG_OK;
+            } catch (const slg::Error&) {
+                for (ServeQuery& Q : local) {  // run them one by one instead
+                    free_result(Q, W.st);
+                    Q.materialized = false;
+                    Q.digest = 0;
+                }
+                batched = false;
+            }
         }
-        {
+        if (!batched) {
+            for (ServeQuery& Q : local) {
+                try {
+                    run_query(S, W, Q);
+                    Q.status = SLG_OK;
+                } catch (const slg::Error& e) {
+                    Q.status = e.code;
+                    Q.error = e.msg;
+                    free_result(Q, W.st);
+                    Q.materialized = false;
+                }
+            }
+        }
+        for (size_t x = 0; x < tickets.size(); ++x) {
+            const uint64_t ticket_x = tickets[x];
+            ServeQuery& local_x = local[x];
             std::lock_guard<std::mutex> lk(S->mu);
-            ServeQuery& Q = S->q[ticket];
-            Q.status = local.status;
-            Q.error = local.error;
-            Q.pairs = local.pairs;
-            Q.wedges = local.wedges;
-            Q.digest = local.digest;
-            Q.I = local.I;
-            Q.J = local.J;
-            Q.O = local.O;
-            Q.materialized = local.materialized;
+            ServeQuery& Q = S->q[ticket_x];
+            Q.status = local_x.status;
+            Q.error = local_x.error;
+            Q.pairs = local_x.pairs;
+            Q.wedges = local_x.wedges;
+            Q.digest = local_x.digest;
+            Q.I = local_x.I;
+            Q.J = local_x.J;
+            Q.O = local_x.O;
+            Q.materialized = local_x.materialized;
             Q.t_done = Clock::now();
             Q.done = true;
             // a kept result holds its exact size until released; the rest returns

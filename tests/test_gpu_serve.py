@@ -138,3 +138,33 @@ def test_poll_timeout(graphs):
         assert slg.slg_serve_poll(srv, second, 120000)["status"] == 0
     finally:
         srv.close()
+
+
+def test_batched_small_queries_match_oracle(graphs):
+    # continuous batching: small queries of different graphs and s run as one batch;
+    # each result (kept list, pairs, W_s, digest) must be what it is alone
+    hs, gs = graphs
+    srv = slg.Server(memory_budget=8 << 30, window_pairs=1 << 24, max_result_pairs=1 << 22,
+                     workers=2, max_s=8, policy=1, small_workers=1, small_wedges=1 << 40,
+                     batch_max=8)
+    try:
+        ids = [slg.slg_serve_register(srv, g) for g in gs]
+        rng = np.random.default_rng(17)
+        queries = [(int(rng.integers(0, len(gs))), int(rng.integers(1, 9))) for _ in range(48)]
+        tickets = [slg.slg_serve_submit(srv, ids[g], s) for g, s in queries]
+        for t, (g, s) in zip(tickets, queries):
+            r = slg.slg_serve_poll(srv, t, 120000)
+            h = hs[g]
+            wI, wJ, wO = oracle.slg_par(h.off, h.idx, s)
+            assert r["status"] == 0 and r["pairs"] == wI.size, (g, s)
+            assert r["digest"] == oracle.list_digest(wI, wJ, wO), (g, s)
+            sz = np.diff(h.off)
+            deg = np.bincount(h.idx[np.repeat(sz >= s, sz)], minlength=h.n).astype(np.int64)
+            assert r["wedges"] == int((deg * (deg - 1) // 2).sum()), (g, s)
+            if r["materialized"]:
+                I, J, O = slg.slg_serve_fetch(srv, t, r["pairs"])
+                assert np.array_equal(I, wI) and np.array_equal(J, wJ) and np.array_equal(O, wO)
+            slg.slg_serve_release(srv, t)
+        assert slg.slg_serve_stats(srv)["completed"] == len(queries)
+    finally:
+        srv.close()
