@@ -294,7 +294,10 @@ def bench_ours(args):
     kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>" if names[dom[1]] in ("dense", "wdense")
              else f"k_{names[dom[1]]}_items<{fill_flag}>")
     achieved = dom[2] / (dom[3] / 1e3) / 1e9 if dom[3] > 0 else 0.0
-    traffic = profiled_traffic(kname, dom[2] / max(dom[4], 1))
+    pairs_per_launch = (pairs_mode[dom[1]] / max(dom[4], 1)) if dom[0] == "fill" else 0
+    traffic = profiled_traffic(kname, dom[2] / max(dom[4], 1), pairs_per_launch)
+    ms_launch = dom[3] / max(dom[4], 1)
+    dram_gbs = traffic / (ms_launch / 1e3) / 1e9 if traffic and ms_launch > 0 else None
     # the output writes alone: 12 B per pair of the dominant kernel's handler
     write_gbs = (12 * pairs_mode[dom[1]] / (dom[3] / 1e3) / 1e9
                  if dom[0] == "fill" and dom[3] > 0 else None)
@@ -307,6 +310,9 @@ def bench_ours(args):
                 "kernel_share_of_step": round(dom[3] / (elapsed_ms / args.steps), 4),
                 "output_write_GBps": round(write_gbs, 1) if write_gbs else None,
                 "output_write_frac": round(write_gbs / hbm_peak, 4) if write_gbs else None,
+                "pairs_per_launch": int(pairs_per_launch),
+                "dram_GBps": round(dram_gbs, 1) if dram_gbs else None,
+                "dram_frac": round(dram_gbs / hbm_peak, 4) if dram_gbs else None,
                 "model": "algorithmic bytes = 4 B/wedge + 8 B/incidence + 12 B/pair written"}
     kernels_ms = {f"{ps}_{names[k]}": round(ms_tot[pi][k] / args.steps, 1)
                   for pi, ps in enumerate(("count", "fill")) for k in range(NM)}
@@ -384,13 +390,15 @@ def e2e(args, slg, h, s_list, stream, bufs):
             "note": "lists stay in the device window; host reads |L_s| and row offsets"}
 
 
-def profiled_traffic(kname: str, alg_bytes_per_launch: float):
+def profiled_traffic(kname: str, alg_bytes_per_launch: float, pairs_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, if it matches.
 
-    profiles/traffic.json maps kernel name -> {"dram_over_alg": r,
-    "source_sha": sha of count_fill.cu when captured}. The ratio of measured
-    DRAM bytes to algorithmic bytes on the captured case is scaled to this
-    launch; null when no capture exists or the kernel source has changed.
+    profiles/traffic.json maps kernel name -> the DRAM bytes the kernel moved
+    per output pair on the captured case ("dram_per_pair"; its DRAM bytes are
+    the output writes, so they grow with the pairs written) or, for older
+    records, per algorithmic byte ("dram_over_alg"), and "source_sha", the
+    hash of the kernel source when captured. Scaled to this launch; null when
+    no capture exists or the kernel source has changed.
     """
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -403,6 +411,8 @@ def profiled_traffic(kname: str, alg_bytes_per_launch: float):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if rec.get("source_sha") != sha:
         return None
+    if "dram_per_pair" in rec:
+        return int(rec["dram_per_pair"] * pairs_per_launch)
     return int(rec["dram_over_alg"] * alg_bytes_per_launch)
 
 

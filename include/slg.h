@@ -441,8 +441,8 @@ slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int6
  *     counters touched) when |e_i| <= 255 and W_i >= sparse_min_per_tile *
  *     ceil(S_i / 65536) (< 0 disables it), in items of about
  *     sparse_item_wedges wedges: one warp with 4096-id tiles when |e_i| <=
- *     wsparse_max_size (<= 32; 0 disables it), else one CTA with 65536-id
- *     tiles;
+ *     wsparse_max_size (<= 32; 0 disables it), 32 * W_i < S_i and s >= 2,
+ *     else one CTA with 65536-id tiles;
  *   - otherwise by CTA hash tables, about block_item_wedges wedges per item.
  * Results do not depend on these values; only speed does. Resets the plan.
  * SLG_ECAPACITY from a later call when a binning needs 2^31 items or more.

@@ -114,7 +114,7 @@ struct RowItems {
 };
 
 __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, int32_t nnh,
-                             BinParams bp) {
+                             int32_t s, BinParams bp) {
     RowItems r{MODE_WARP, 0, 0};
     if (w <= 0) return r;
     const int64_t span = (int64_t)hi - lo + 1;
@@ -142,7 +142,12 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
     if (bp.sparse_min_per_tile >= 0 && size <= SP_MAX_SIZE &&
         w >= (int64_t)bp.sparse_min_per_tile * tiles) {
         // uniform j slices of about sparse_item_wedges wedges, at least 1024 ids wide
-        r.mode = size <= bp.wsparse_max_size ? MODE_WSPARSE : MODE_SPARSE;
+        // the warp-level accumulator only where its 4096-id tiles stay sparse
+        // (below one wedge per 32 ids) and survivors are rare (s >= 2: at s = 1
+        // every partner is one, and the CTA's bitmap ranking writes them
+        // faster); other rows keep the CTA's wider tiles
+        r.mode = (size <= bp.wsparse_max_size && 32 * w < span && s >= 2) ? MODE_WSPARSE
+                                                                            : MODE_SPARSE;
         int64_t k = (w + bp.sparse_item_wedges - 1) / bp.sparse_item_wedges;
         const int64_t kmax = (span + 1023) / 1024;
         if (k > kmax) k = kmax;
@@ -160,17 +165,19 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
 
 __global__ void k_item_count(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                              const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
-                             const int32_t* __restrict__ nnh, int32_t m, BinParams bp,
+                             const int32_t* __restrict__ nnh, int32_t m, RowS rs, BinParams bp,
                              int32_t* __restrict__ nitem) {
-    GRID_STRIDE(i, m) nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], bp).count;
+    GRID_STRIDE(i, m) {
+        nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp).count;
+    }
 }
 
 __global__ void k_item_emit(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                             const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
-                            const int32_t* __restrict__ nnh, int32_t m, BinParams bp,
+                            const int32_t* __restrict__ nnh, int32_t m, RowS rs, BinParams bp,
                             const int32_t* __restrict__ row_item, Item* __restrict__ items) {
     GRID_STRIDE(i, m) {
-        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], bp);
+        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp);
         if (r.count == 0) continue;
         const int64_t lo = jmin[i], end = (int64_t)jmax[i] + 1, span = end - lo;
         Item* out = items + row_item[i];
@@ -360,7 +367,7 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     int32_t* nitem = dalloc<int32_t>(m, st);
     p.row_item = dalloc<int32_t>((size_t)m + 1, st);
     if (m) {
-        k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, bp,
+        k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, p.rs, bp,
                                                    nitem);
         SLG_LAUNCH_CHECK();
     }
@@ -391,7 +398,7 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.wedges = (int64_t)wtot_h;
     p.items = dalloc<Item>(p.nitems, st);
     if (m) {
-        k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, bp,
+        k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, p.rs, bp,
                                                   p.row_item, p.items);
         SLG_LAUNCH_CHECK();
     }

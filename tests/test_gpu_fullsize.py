@@ -92,6 +92,49 @@ def test_medium_full_size_sampled_rows(medium, s):
         assert osum == wedges
 
 
+def test_medium_full_size_ensemble(medium):
+    """s = 1..8 as one ensemble (Algorithm 3) on the medium workload, one list at
+    a time through 2^33-pair windows as the ensemble benchmark runs it: per-row
+    counts and digests of every list on 600 seeded random rows and the 50 rows
+    with the most wedges equal the oracle's, and each list's row counts add up
+    to its |L_s| from the single-s path."""
+    torch, h = medium
+    dev = torch.device("cuda")
+    s_list = list(range(1, 9))
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        pairs, w1 = slg.slg_ensemble_count(g, s_list)
+        rowoff = slg.slg_ensemble_row_offsets(g, s_list)
+        I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        digs = []
+        for t in range(len(s_list)):
+            assert int(rowoff[t, -1]) == pairs[t]
+            d = torch.zeros(h.m, dtype=torch.int64, device=dev)
+            splits = slg.slg_ensemble_plan_windows(g, s_list, WINDOW, which=t)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                (P,), _ = slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O,
+                                                        WINDOW, row_digests=d[int(r0):int(r1)],
+                                                        which=t)
+                assert P == rowoff[t, r1] - rowoff[t, r0]
+            digs.append(d.cpu().numpy().view(np.uint64))
+        single = [slg.slg_count(g, s)[0] for s in (1, 5, 8)]
+    finally:
+        g.free()
+    assert single == [pairs[0], pairs[4], pairs[7]]
+    rng = np.random.default_rng([7, 99])
+    w = row_wedges(h, 1)
+    heavy = np.argsort(-w, kind="stable")[:50]
+    rows = np.unique(np.concatenate([rng.choice(h.m, size=600, replace=False), heavy]))
+    rows = rows.astype(np.int32)
+    ocount, odig, osum = oracle.rows(h.off, h.idx, rows, s_list)
+    assert np.array_equal(osum[:, 0], w[rows])
+    for t in range(len(s_list)):
+        assert np.array_equal(np.diff(rowoff[t])[rows], ocount[:, t]), f"list {t}"
+        assert np.array_equal(digs[t][rows], odig[:, t]), f"list {t}"
+
+
 @pytest.fixture(scope="module")
 def large():
     torch = pytest.importorskip("torch")
