@@ -390,6 +390,19 @@ def e2e(args, slg, h, s_list, stream, bufs):
             "note": "lists stay in the device window; host reads |L_s| and row offsets"}
 
 
+def kernel_source_sha(kname: str) -> str:
+    """Hash of the source a kernel is built from: for the warp dense handler, its
+    section of count_fill.cu (from its section banner to the next one) and the
+    shared device helpers; for any other kernel, all of count_fill.cu."""
+    csrc = os.path.join(ROOT, "paper_2201_11326_gb300", "csrc")
+    text = open(os.path.join(csrc, "count_fill.cu"), "rb").read()
+    if kname.startswith("k_wdense_items"):
+        a = text.index(b"// " + b"=" * 58 + b" MODE_WDENSE")
+        b = text.index(b"\n// =", a + 1)
+        text = text[a:b] + open(os.path.join(csrc, "kernel_util.cuh"), "rb").read()
+    return hashlib.sha256(text).hexdigest()[:16]
+
+
 def profiled_traffic(kname: str, alg_bytes_per_launch: float, pairs_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, if it matches.
 
@@ -398,7 +411,7 @@ def profiled_traffic(kname: str, alg_bytes_per_launch: float, pairs_per_launch: 
     the output writes, so they grow with the pairs written) or, for older
     records, per algorithmic byte ("dram_over_alg"), and "source_sha", the
     hash of the kernel source when captured. Scaled to this launch; null when
-    no capture exists or the kernel source has changed.
+    no capture exists or the kernel's source (kernel_source_sha) has changed.
     """
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -407,9 +420,7 @@ def profiled_traffic(kname: str, alg_bytes_per_launch: float, pairs_per_launch: 
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2201_11326_gb300", "csrc", "count_fill.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != sha:
+    if rec.get("source_sha") != kernel_source_sha(kname):
         return None
     if "dram_per_pair" in rec:
         return int(rec["dram_per_pair"] * pairs_per_launch)
