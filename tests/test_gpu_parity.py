@@ -397,3 +397,21 @@ def test_autotune_batch_handle():
         b.free()
         for g in graphs:
             g.free()
+
+
+def test_output_arrays_at_any_alignment():
+    # I, J and O as slices of one buffer at offsets 0, 1 and 3 ints: the fill may
+    # not assume that they share an alignment
+    import torch
+    h = synth.medium(seed=2, m=6000)
+    want = oracle_list("med6000", h, 1)
+    P = want[0].size
+    buf = torch.zeros(3 * P + 8, dtype=torch.int32, device="cuda")
+    I, J, O = buf[0:P], buf[P + 1:2 * P + 1], buf[2 * P + 3:3 * P + 3]
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        got, _ = slg.slg_build_window(g, 1, 0, h.m, I, J, O, P)
+    finally:
+        g.free()
+    assert got == P
+    assert_same((I.cpu().numpy(), J.cpu().numpy(), O.cpu().numpy()), want, "offset slices")
