@@ -391,16 +391,22 @@ def e2e(args, slg, h, s_list, stream, bufs):
 
 
 def kernel_source_sha(kname: str) -> str:
-    """Hash of the source a kernel is built from: for the warp dense handler, its
-    section of count_fill.cu (from its section banner to the next one) and the
-    shared device helpers; for any other kernel, all of count_fill.cu."""
+    """Hash of the code a kernel is built from, comments and blank lines left out:
+    for the warp dense handler, its section of count_fill.cu (from its section
+    banner to the next one) and the shared device helpers; for any other kernel,
+    all of count_fill.cu."""
     csrc = os.path.join(ROOT, "paper_2201_11326_gb300", "csrc")
     text = open(os.path.join(csrc, "count_fill.cu"), "rb").read()
     if kname.startswith("k_wdense_items"):
         a = text.index(b"// " + b"=" * 58 + b" MODE_WDENSE")
         b = text.index(b"\n// =", a + 1)
         text = text[a:b] + open(os.path.join(csrc, "kernel_util.cuh"), "rb").read()
-    return hashlib.sha256(text).hexdigest()[:16]
+    code = []
+    for line in text.decode().splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            code.append(line)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(kname: str, alg_bytes_per_launch: float, pairs_per_launch: float):

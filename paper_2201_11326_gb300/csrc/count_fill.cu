@@ -6,7 +6,8 @@
 // (for k in H^T.Adj[i], for j in H.Adj[k]: L[i,j] += 1) with the Boolean
 // filter applied per row. The paper keeps the counts in a per-thread
 // std::unordered_map; here a work item (row i, partners j in [jlo, jhi))
-// keeps them on chip in one of three forms:
+// keeps them on chip in one of these forms (the sparse accumulators, for rows
+// spread thinly over a wide id range, are in sparse.cu):
 //
 //   MODE_WARP   one warp, a 256-slot open-addressing table in shared memory
 //               (rows with at most 128 wedges, so the table never fills);
@@ -16,7 +17,9 @@
 //               overflows and nothing spills off chip;
 //   MODE_DENSE  one CTA per slice walking 32768-wide j tiles in order: the
 //               hub part of each overlap is a popcount of two 32-bit hub
-//               masks, the rest direct-addressed 16-bit counters (see below).
+//               masks, the rest direct-addressed 16-bit counters (see below);
+//   MODE_WDENSE the same at warp granularity with 8-bit counters, for dense
+//               rows with at most 32 non-hub wedge ranges.
 //
 // Both passes run the same code: the counting pass stores the number of
 // partners per item, a scan turns those into output offsets, and the fill
@@ -596,11 +599,11 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 
 // ========================================================== MODE_WDENSE
 //
-// The dense handler at warp granularity, for rows with at most 64 non-hub
+// The dense handler at warp granularity, for rows with at most 32 non-hub
 // wedge ranges (almost every dense row): one warp owns a slice, a j tile of
-// 8-bit counters (4096 ids when counting, 2048 when filling, so that the fill
-// keeps three CTAs per SM) and two non-hub cursors per lane, so no CTA
-// barrier is ever needed. A non-hub count is at most 64 and a hub count at
+// 4096 8-bit counters (three CTAs per SM when counting, two when filling,
+// whose ring takes more shared memory) and one non-hub cursor per lane, so no
+// CTA barrier is ever needed. A non-hub count is at most 32 and a hub count at
 // most 32, so every overlap fits a byte below 128. Counter of partner t0 + c:
 // byte c % 4 of word c / 4, so a lane's four consecutive partners share one
 // word. Tiles start at multiples of 32 ids. Per tile:
