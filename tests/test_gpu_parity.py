@@ -415,3 +415,30 @@ def test_output_arrays_at_any_alignment():
         g.free()
     assert got == P
     assert_same((I.cpu().numpy(), J.cpu().numpy(), O.cpu().numpy()), want, "offset slices")
+
+
+@pytest.mark.parametrize("mode", ["default", "sparse_only", "sparse_cta_only"])
+def test_counter_width_boundaries(mode):
+    # rows at the 8-bit counters' limit: copies of a 255-vertex row (overlap 255 fits
+    # a byte), copies of a 256-vertex row (too large for the sparse accumulators:
+    # the binning sends them elsewhere), 32-vertex copies for the warp accumulator,
+    # all spread over a wide id range so that they count as sparse rows
+    rng = np.random.default_rng(12)
+    n = 3000
+    big255 = sorted(rng.choice(n, 255, replace=False).tolist())
+    big256 = sorted(rng.choice(n, 256, replace=False).tolist())
+    mid32 = sorted(rng.choice(n, 32, replace=False).tolist())
+    rows = []
+    for r in range(20000):
+        if r in (5, 10000, 19990):
+            rows.append(big255)
+        elif r in (7, 15000):
+            rows.append(big256)
+        elif r in (9, 7500, 19999):
+            rows.append(mid32)
+        else:
+            rows.append(sorted(rng.choice(n, int(rng.integers(1, 4)), replace=False).tolist()))
+    off, idx = csr_from_rows(rows)
+    h = synth.Hypergraph(off, idx, n)
+    for s in (1, 2, 32, 255, 256):
+        assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("width", h, s), f"{mode} s={s}")
