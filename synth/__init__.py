@@ -340,12 +340,15 @@ def cache_dir() -> str:
 
 
 def save(h: Hypergraph, path: str) -> None:
+    # a temporary file per process, renamed into place: processes that build the
+    # same graph at once (ranks on one host) never read a partial file
     hdr = np.array([h.m, h.n, h.nnz], np.int64)
-    with open(path + ".tmp", "wb") as f:
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "wb") as f:
         hdr.tofile(f)
         h.off.astype(np.int32).tofile(f)
         h.idx.astype(np.int32).tofile(f)
-    os.replace(path + ".tmp", path)
+    os.replace(tmp, path)
 
 
 def load(path: str, name: str = "") -> Hypergraph:
