@@ -68,3 +68,19 @@ def test_library_links_no_oracle():
     import subprocess
     out = subprocess.run(["nm", "-D", slg.library_path()], capture_output=True, text=True).stdout
     assert "oracle_" not in out
+
+
+def test_no_gpu_means_an_error_not_a_cpu_fallback(lib):
+    # without a CUDA device the library reports a CUDA error; nothing is computed on the CPU
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    off = (ctypes.c_int32 * 3)(0, 2, 3)
+    idx = (ctypes.c_int32 * 3)(0, 1, 1)
+    out = ctypes.c_void_p()
+    rc = lib.slg_load(off, idx, 2, 2, None, ctypes.byref(out))
+    assert rc in (slg.SLG_ECUDA, slg.SLG_ENOMEM) and not out.value
+    assert lib.slg_last_error()  # with a message
+    import numpy as np
+    with pytest.raises(slg.SlgError):
+        slg.slg_load(np.array([0, 2, 3], np.int32), np.array([0, 1, 1], np.int32), 2, 2)
