@@ -136,7 +136,7 @@ constexpr int DENSE_THREADS = 512;        // MODE_DENSE CTA
 constexpr int DENSE_TILE = 32768;         // j per tile (16-bit counters)
 constexpr int DENSE_MAXE = 1024;          // incidences a dense row may have
 constexpr int MAX_HUBS = 32;              // vertices summarised by per-row bit masks
-constexpr int WD_WARPS = 16;              // warps per CTA in MODE_WDENSE
+constexpr int WD_WARPS = 12;              // warps per CTA in MODE_WDENSE
 constexpr int WD_TILE = 4096;             // j per warp tile (8-bit counters, 4 KB)
 constexpr int WD_ITEM = 8192;             // j per MODE_WDENSE item = WD_ITEM * dense_item_tiles
 constexpr int WD_MAXR = 32;               // non-hub wedge ranges a MODE_WDENSE row may have
