@@ -182,8 +182,8 @@ slg_status slg_plan_windows(slg_graph* g, int32_t s, int64_t cap, int32_t* row_s
  * for several thresholds s_list[0] < s_list[1] < ... < s_list[k-1]. Algorithm
  * 3 counts the overlaps once (pruned by the smallest s) and then filters the
  * counted pairs once per threshold. Here one plan, pruned by s_list[0], serves
- * every list: one counting pass counts every list, and the fills write either
- * every list of a row window in one pass or one list at a time.
+ * every list: one counting pass counts every list, and the fills write the
+ * lists of a row window one after another, or one selected list.
  *
  * Every ensemble call takes the same (s_list, k), with 1 <= k <=
  * SLG_ENSEMBLE_MAX and s_list strictly ascending, s_list[0] >= 1. The counts
@@ -220,8 +220,8 @@ slg_status slg_ensemble_plan_windows(slg_graph* g, const int32_t* s_list, int32_
  *
  * which = SLG_ENSEMBLE_ALL: every list, back to back in I, J, O (cap entries
  * each, host or device, all of one kind): list t occupies positions seg_t ..
- * seg_t + pairs[t] - 1, seg_t = pairs[0] + ... + pairs[t-1]. The dense
- * handlers write all lists in one pass over the overlaps.
+ * seg_t + pairs[t] - 1, seg_t = pairs[0] + ... + pairs[t-1]. Each list is
+ * filled from the shared plan and counts by its own pass.
  * which = t in [0, k): list t alone, at positions 0 .. pairs[0] - 1.
  * Each list is the contiguous slice of its canonical list (sorted by (i, j)).
  *
@@ -262,11 +262,19 @@ slg_status slg_last_timing(slg_graph* g, float* ms5);
 slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms, int64_t* launches);
 
 /*
- * Work per handler for s (runs the counting pass if needed): out[mode*4 + c]
- * (4 * SLG_NMODES entries) with c = 0 rows, 1 wedges, 2 incidences (sum of
- * |e_i| over the rows), 3 output pairs. The wedge total over the handlers is
- * W_s.
+ * Work per handler for s (runs the counting pass if needed):
+ * out[mode * SLG_MODE_STATS_COLS + c] (SLG_MODE_STATS_COLS * SLG_NMODES
+ * entries), summed over the rows the handler takes, with c =
+ *   0 rows, 1 wedges, 2 incidences (sum of |e_i|), 3 output pairs,
+ *   4 wedges through non-hub vertices (the dense handlers read adj_s entries
+ *     for these only; a hub's share of an overlap is a popcount of two hub
+ *     masks),
+ *   5 candidate partners the dense handlers' extraction scans in the counting
+ *     pass (one 4-byte hub mask read each; 0 for the other handlers),
+ *   6 the same for the fill, which skips work items without pairs.
+ * The wedge total over the handlers is W_s.
  */
+#define SLG_MODE_STATS_COLS 7
 slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out);
 
 /*
@@ -304,6 +312,43 @@ slg_status slg_batch_info(const slg_graph* b, int32_t* k, int32_t* row_base);
 /* pair_base[0..k] (host): member b's pairs occupy positions pair_base[b] ..
  * pair_base[b+1]-1 of the batch's list. Runs the counting pass if needed. */
 slg_status slg_batch_pair_offsets(slg_graph* b, int64_t* pair_base);
+
+/*
+ * slg_batch -- the s-line graphs of k hypergraphs, each with its own
+ * threshold, in one call: for every member b, Algorithm 2's statement (input
+ * (H_b, s[b]), output the edge list of L_{s[b]}(H_b), Section III-C), with the
+ * members run together as one batch (slg_batch_load: one plan, one counting
+ * pass and one fill per window over all members).
+ *
+ *   gs, s, k : as slg_batch_load; the device work runs on gs[0]'s stream.
+ *   results  : k entries. Before the call the caller sets want_list (nonzero:
+ *              return the member's list); the call fills in the rest.
+ *
+ * Per member: pairs = |L_s|, wedges = W_s, digest = the digest of the whole
+ * list as slg_build_window defines it (member-local ids, so it equals what
+ * the member's own handle gives). With want_list, I/J/O receive host arrays of
+ * `pairs` int32 entries allocated by the library (canonical order, member-local
+ * ids; NULL when pairs = 0); release them with slg_result_free. Lists pass
+ * through a device window of at most 2^27 pairs (or the largest row).
+ * Errors: as slg_batch_load; SLG_ENOMEM also when a wanted list does not fit
+ * host memory (no member then keeps a list). On any error every result's
+ * status holds the error and no list is kept.
+ */
+typedef struct {
+    int32_t want_list;  /* in: nonzero to receive the list in I/J/O */
+    slg_status status;  /* out */
+    int64_t pairs;      /* out: |L_s(H)| */
+    int64_t wedges;     /* out: W_s */
+    uint64_t digest;    /* out: digest of the whole list */
+    int32_t* I;         /* out: host arrays (library-allocated) or NULL */
+    int32_t* J;
+    int32_t* O;
+} slg_result;
+
+slg_status slg_batch(slg_graph* const* gs, const int32_t* s, int32_t k, slg_result* results);
+
+/* Release the lists of a result (I, J, O become NULL). NULL is ignored. */
+void slg_result_free(slg_result* r);
 
 /*
  * Serving: s-line queries (graph, s) over resident hypergraphs.
@@ -355,6 +400,7 @@ typedef struct {
     uint64_t digest;      /* digest of the whole list (if cfg.digest) */
     double latency_us;    /* submit -> done */
     double queue_us;      /* submit -> start */
+    int32_t batch_size;   /* queries of the batch it ran in (1: it ran alone) */
 } slg_serve_result;
 
 typedef struct {
@@ -365,6 +411,11 @@ typedef struct {
     int64_t peak_memory;                    /* bytes of kept results, at most */
     int64_t pending;
     int64_t running;
+    int64_t batched;          /* queries completed inside a batch of two or more */
+    int64_t batches;          /* such batches */
+    int64_t batch_overflows;  /* batches whose lists exceeded the window: run one by one */
+    int64_t batch_failures;   /* batches that failed and were run one by one (the last
+                                 reason is then in slg_last_error after this call) */
 } slg_serve_stats_t;
 
 /* Create a server on the current device (starts the worker threads). */
@@ -407,8 +458,8 @@ int64_t slg_kernel_launches(void);
  * 264 KiB array compiled into the library, present on every GPU that loads
  * it until the process exits.
  *
- *   counts  : n int32 per-row counts, device memory.
- *   offsets : n+1 int64 outputs, device memory (caller-owned).
+ *   counts  : n int32 per-row counts, memory of the current device.
+ *   offsets : n+1 int64 outputs, memory of the current device (caller-owned).
  *   n       : 0 <= n <= 67,108,864; larger n fails with SLG_EINVAL and
  *             launches nothing.
  *   stream  : cudaStream_t (as void*) for the kernels; the call returns
@@ -416,12 +467,14 @@ int64_t slg_kernel_launches(void);
  *
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture begins. All calls on a device share the one
+ * before any stream capture begins. The address is cached for the life of
+ * the process: do not use this call after resetting the device
+ * (cudaDeviceReset), which invalidates it. All calls on a device share the one
  * array: every call writes each tile sum before reading it, so nothing needs
  * clearing, but calls whose kernels overlap on the GPU (e.g. on two
  * streams) race on it and must be serialised by the caller.
- * Errors: SLG_EINVAL (size above the limit, NULL or host pointers),
- * SLG_ECUDA.
+ * Errors: SLG_EINVAL (size above the limit, NULL or host pointers, or
+ * memory of a device other than the current one), SLG_ECUDA.
  */
 slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* offsets, int64_t n,
                                    void* stream);

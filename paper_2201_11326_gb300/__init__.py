@@ -22,7 +22,7 @@ __all__ = [
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
-    "slg_batch_info", "slg_batch_pair_offsets", "slg_dual", "slg_ensemble_count",
+    "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
     "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
@@ -57,6 +57,12 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 
+class BatchResult(ctypes.Structure):
+    _fields_ = [("want_list", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("pairs", ctypes.c_int64), ("wedges", ctypes.c_int64),
+                ("digest", ctypes.c_uint64), ("I", _i32p), ("J", _i32p), ("O", _i32p)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_int64), ("window_pairs", ctypes.c_int64),
                 ("max_result_pairs", ctypes.c_int64), ("workers", ctypes.c_int32),
@@ -69,7 +75,7 @@ class ServeResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("materialized", ctypes.c_int32),
                 ("pairs", ctypes.c_int64), ("wedges", ctypes.c_int64),
                 ("digest", ctypes.c_uint64), ("latency_us", ctypes.c_double),
-                ("queue_us", ctypes.c_double)]
+                ("queue_us", ctypes.c_double), ("batch_size", ctypes.c_int32)]
 
 
 class ServeStats(ctypes.Structure):
@@ -78,7 +84,9 @@ class ServeStats(ctypes.Structure):
                 ("max_us", ctypes.c_double), ("span_s", ctypes.c_double),
                 ("queries_per_s", ctypes.c_double), ("pairs_per_s", ctypes.c_double),
                 ("wedges_per_s", ctypes.c_double), ("peak_memory", ctypes.c_int64),
-                ("pending", ctypes.c_int64), ("running", ctypes.c_int64)]
+                ("pending", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("batched", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batch_overflows", ctypes.c_int64), ("batch_failures", ctypes.c_int64)]
 
 
 _SIGS = {
@@ -111,6 +119,8 @@ _SIGS = {
     "slg_dual": (_i32, [_vp, _vp, ctypes.POINTER(_vp)]),
     "slg_batch_info": (_i32, [_vp, _i32p, _i32p]),
     "slg_batch_pair_offsets": (_i32, [_vp, _i64p]),
+    "slg_batch": (_i32, [ctypes.POINTER(_vp), _i32p, _i32, ctypes.POINTER(BatchResult)]),
+    "slg_result_free": (None, [ctypes.POINTER(BatchResult)]),
     "slg_serve_create": (_i32, [ctypes.POINTER(ServeCfg), ctypes.POINTER(_vp)]),
     "slg_serve_destroy": (None, [_vp]),
     "slg_serve_register": (_i32, [_vp, _vp, _i32p]),
@@ -400,11 +410,18 @@ def slg_kernel_stats(g: Graph, reset: bool = False):
     return ([list(ms[0:NMODES]), list(ms[NMODES:])], [list(ln[0:NMODES]), list(ln[NMODES:])])
 
 
+MODE_STATS_COLS = 7
+MODE_STATS_NAMES = ("rows", "wedges", "incidences", "pairs", "nonhub_wedges",
+                    "scanned_count", "scanned_fill")
+
+
 def slg_mode_stats(g: Graph, s: int):
-    """[[rows, wedges, incidences, pairs] per handler (MODE_NAMES)]."""
-    out = (ctypes.c_int64 * (4 * NMODES))()
+    """[[rows, wedges, incidences, pairs, nonhub_wedges, scanned_count, scanned_fill]
+    per handler (MODE_NAMES)]; see include/slg.h."""
+    c = MODE_STATS_COLS
+    out = (ctypes.c_int64 * (c * NMODES))()
     _check(lib().slg_mode_stats(g.handle, s, out))
-    return [list(out[4 * k:4 * k + 4]) for k in range(NMODES)]
+    return [list(out[c * k:c * k + c]) for k in range(NMODES)]
 
 
 def slg_kernel_launches() -> int:
@@ -447,6 +464,35 @@ def slg_batch_pair_offsets(g: Graph) -> np.ndarray:
     k = len(slg_batch_info(g)) - 1
     out = np.zeros(k + 1, np.int64)
     _check(lib().slg_batch_pair_offsets(g.handle, out.ctypes.data_as(_i64p)))
+    return out
+
+
+def slg_batch(graphs, s_list, want_lists=False):
+    """s-line graphs of many graphs, each with its own s, in one call.
+
+    Returns one dict per member: pairs, wedges, digest and, when want_lists
+    (a bool, or one bool per member), the list as numpy arrays I, J, O
+    (member-local ids, canonical order)."""
+    k = len(graphs)
+    arr = (_vp * k)(*[g.handle for g in graphs])
+    s_arr = np.ascontiguousarray(s_list, dtype=np.int32)
+    want = [bool(want_lists)] * k if isinstance(want_lists, bool) else [bool(x) for x in want_lists]
+    res = (BatchResult * k)()
+    for b in range(k):
+        res[b].want_list = 1 if want[b] else 0
+    _check(lib().slg_batch(arr, s_arr.ctypes.data_as(_i32p), k, res))
+    out = []
+    for b in range(k):
+        r = res[b]
+        d = {"status": r.status, "pairs": r.pairs, "wedges": r.wedges, "digest": r.digest}
+        if want[b]:
+            n = r.pairs
+            for name in ("I", "J", "O"):
+                p = getattr(r, name)
+                d[name] = (np.ctypeslib.as_array(p, shape=(n,)).copy() if n and p
+                           else np.zeros(0, np.int32))
+            lib().slg_result_free(ctypes.byref(r))
+        out.append(d)
     return out
 
 
@@ -521,7 +567,10 @@ def slg_serve_release(srv: Server, ticket: int):
 def slg_serve_stats(srv: Server, reset: bool = False) -> dict:
     st = ServeStats()
     _check(lib().slg_serve_stats(srv._h, 1 if reset else 0, ctypes.byref(st)))
-    return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+    out = {k: getattr(st, k) for k, _ in ServeStats._fields_}
+    if st.batch_failures:
+        out["batch_error"] = (lib().slg_last_error() or b"").decode()
+    return out
 
 
 def slg_scan_counts_noalloc(counts, offsets, stream=None):

@@ -3,6 +3,7 @@
 // Host orchestration only: every step of the computation runs in the kernels
 // of transpose.cu, plan.cu, count_fill.cu and scan.cu. There is no CPU path.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <atomic>
@@ -44,6 +45,11 @@ __global__ void k_size_range(const int32_t* __restrict__ size, int32_t m,
     }
 }
 
+}  // namespace
+
+// Device memory the kernels may write: managed memory, or device memory of
+// the current device. Device memory of another GPU is refused (an error, not
+// a host copy: the kernels cannot reach it without a peer mapping).
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -52,8 +58,16 @@ bool is_device_ptr(const void* p) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    SLG_CUDA_TRY(cudaGetDevice(&dev));
+    if (a.device != dev)
+        throw Error{SLG_EINVAL, "an array lies in another GPU's memory than the current device's"};
+    return true;
 }
+
+namespace {
 
 
 }  // namespace
@@ -599,11 +613,15 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
         SLG_CUDA_TRY(cudaMemsetAsync(dd, 0, sizeof(unsigned long long) * nd, h->st));
     }
     h->timer.mark(3, h->st);
-    if (which < 0)
-        slg::run_fill_ensemble(h->g, p, q0, q1, seg, dI, dJ, dO, P, &h->mtimer, h->st);
-    else
-        slg::run_fill(h->g, p, p.rs_for(p.ens.s[which]), p.ens.ioff + which * (ni + 1), q0, q1,
-                      dI, dJ, dO, P, &h->mtimer, h->st);
+    // each selected list from the shared plan with its own threshold, into its
+    // segment (one fused pass over all lists was measured slower: the lists
+    // after the first went out as partial-line stores)
+    for (int32_t t = t0; t < t1; ++t) {
+        const int32_t u = t - t0;
+        slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
+                      dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], &h->mtimer,
+                      h->st);
+    }
     h->timer.mark(4, h->st);
     if (dd) {
         for (int32_t t = t0; t < t1; ++t) {
@@ -662,10 +680,11 @@ slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out) {
     if (!h || !out) return fail(SLG_EINVAL, "NULL argument");
     API_BEGIN
     ensure_counted(h, s);
-    int64_t st[slg::NMODES][4];
+    static_assert(slg::MS_COLS == SLG_MODE_STATS_COLS, "mode statistics columns");
+    int64_t st[slg::NMODES][slg::MS_COLS];
     slg::plan_mode_stats(h->g, h->plan, st, h->st);
     for (int k = 0; k < slg::NMODES; ++k)
-        for (int c = 0; c < 4; ++c) out[k * 4 + c] = st[k][c];
+        for (int c = 0; c < slg::MS_COLS; ++c) out[k * slg::MS_COLS + c] = st[k][c];
     API_END
 }
 
@@ -826,6 +845,135 @@ slg_status slg_batch_pair_offsets(slg_graph* h, int64_t* pair_base) {
     slg::dfree(rb, h->st);
     slg::dfree(po, h->st);
     API_END
+}
+
+void slg_result_free(slg_result* r) {
+    if (!r) return;
+    free(r->I);
+    free(r->J);
+    free(r->O);
+    r->I = r->J = r->O = nullptr;
+}
+
+slg_status slg_batch(slg_graph* const* gs, const int32_t* s, int32_t k, slg_result* res) {
+    if (!res) return fail(SLG_EINVAL, "results is NULL");
+    if (k < 1 || !gs || !s) return fail(SLG_EINVAL, "need k >= 1 graphs and their s");
+    for (int32_t b = 0; b < k; ++b) {
+        res[b].status = SLG_OK;
+        res[b].pairs = res[b].wedges = 0;
+        res[b].digest = 0;
+        res[b].I = res[b].J = res[b].O = nullptr;
+    }
+    auto fail_all = [&](slg_status code) {
+        for (int32_t b = 0; b < k; ++b) {
+            slg_result_free(&res[b]);
+            res[b].status = code;
+        }
+        return code;
+    };
+    if (!gs[0]) return fail_all(fail(SLG_EINVAL, "NULL member graph"));
+    slg_graph* h = nullptr;
+    slg_status rc = slg_batch_load(gs, s, k, gs[0]->st, &h);
+    if (rc != SLG_OK) return fail_all(rc);
+    cudaStream_t st = h->st;
+    int32_t* rb_dev = nullptr;
+    long long* wsum = nullptr;
+    unsigned long long *dsum = nullptr, *rowdig = nullptr;
+    int32_t *dI = nullptr, *dJ = nullptr, *dO = nullptr;
+    try {
+        ensure_counted(h, 0);
+        const int32_t M = h->g.m;
+        const std::vector<int32_t>& rb = h->batch_row_base;
+        std::vector<int64_t> pbase((size_t)k + 1);
+        rc = slg_batch_pair_offsets(h, pbase.data());
+        if (rc != SLG_OK) throw Error{rc, slg::g_last_error};
+        // every row's digest, then per-member sums of W and digests
+        rowdig = slg::dalloc<unsigned long long>((size_t)M + 1, st);
+        SLG_CUDA_TRY(cudaMemsetAsync(rowdig, 0, sizeof(unsigned long long) * ((size_t)M + 1), st));
+        const int64_t total = h->plan.pairs;
+        const int64_t maxrow = slg::plan_max_row(h->g, h->plan.rowoff, st);
+        const int64_t cap = std::max<int64_t>(maxrow, std::min<int64_t>(total, (int64_t)1 << 27));
+        if (total > 0) {
+            dI = slg::dalloc<int32_t>((size_t)cap, st);
+            dJ = slg::dalloc<int32_t>((size_t)cap, st);
+            dO = slg::dalloc<int32_t>((size_t)cap, st);
+        }
+        for (int32_t b = 0; b < k; ++b) {
+            const int64_t n = pbase[(size_t)b + 1] - pbase[(size_t)b];
+            if (!res[b].want_list || n == 0) continue;
+            res[b].I = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            res[b].J = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            res[b].O = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            if (!res[b].I || !res[b].J || !res[b].O)
+                throw Error{SLG_ENOMEM, "no host memory for a member's list"};
+        }
+        std::vector<int32_t> splits((size_t)M + 2, 0);
+        int32_t nw = 0;
+        if (M > 0) {
+            rc = slg_plan_windows(h, 0, std::max<int64_t>(cap, 1), splits.data(), M + 1, &nw);
+            if (rc != SLG_OK) throw Error{rc, slg::g_last_error};
+        }
+        for (int32_t w = 0; w < nw; ++w) {
+            const int32_t r0 = splits[(size_t)w], r1 = splits[(size_t)w + 1];
+            int64_t Pw = 0;
+            rc = slg_build_window(h, 0, r0, r1, dI, dJ, dO, cap, &Pw, nullptr,
+                                  reinterpret_cast<uint64_t*>(rowdig) + r0);
+            if (rc != SLG_OK) throw Error{rc, slg::g_last_error};
+            if (Pw == 0) continue;
+            // the window's list is the slice [wbase, wbase + Pw) of the batch's
+            int64_t wbase = 0;
+            SLG_CUDA_TRY(cudaMemcpyAsync(&wbase, h->plan.rowoff + r0, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st));
+            SLG_CUDA_TRY(cudaStreamSynchronize(st));
+            const int32_t b0 = (int32_t)(std::upper_bound(rb.begin(), rb.end(), r0) - rb.begin()) - 1;
+            for (int32_t b = std::max(b0, 0); b < k && rb[(size_t)b] < r1; ++b) {
+                if (!res[b].I) continue;
+                const int64_t a = std::max(pbase[(size_t)b], wbase);
+                const int64_t z = std::min(pbase[(size_t)b + 1], wbase + Pw);
+                if (z <= a) continue;
+                const size_t bytes = sizeof(int32_t) * (size_t)(z - a);
+                const int64_t to = a - pbase[(size_t)b], from = a - wbase;
+                copy_out(res[b].I + to, dI + from, bytes, st);
+                copy_out(res[b].J + to, dJ + from, bytes, st);
+                copy_out(res[b].O + to, dO + from, bytes, st);
+            }
+            SLG_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        rb_dev = slg::dalloc<int32_t>((size_t)k + 1, st);
+        wsum = slg::dalloc<long long>((size_t)k, st);
+        dsum = slg::dalloc<unsigned long long>((size_t)k, st);
+        SLG_CUDA_TRY(cudaMemcpyAsync(rb_dev, rb.data(), sizeof(int32_t) * ((size_t)k + 1),
+                                     cudaMemcpyHostToDevice, st));
+        slg::launch_member_sums(h->plan.W, rowdig, rb_dev, k, wsum, dsum, st);
+        std::vector<long long> wh((size_t)k);
+        std::vector<unsigned long long> dh((size_t)k);
+        copy_out(wh.data(), wsum, sizeof(long long) * (size_t)k, st);
+        copy_out(dh.data(), dsum, sizeof(unsigned long long) * (size_t)k, st);
+        SLG_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int32_t b = 0; b < k; ++b) {
+            res[b].pairs = pbase[(size_t)b + 1] - pbase[(size_t)b];
+            res[b].wedges = (int64_t)wh[(size_t)b];
+            res[b].digest = (uint64_t)dh[(size_t)b];
+        }
+    } catch (const Error& e) {
+        rc = e.code;
+        slg::set_error(e.code, e.msg);
+    }
+    slg::dfree(dI, st);
+    slg::dfree(dJ, st);
+    slg::dfree(dO, st);
+    slg::dfree(rowdig, st);
+    slg::dfree(rb_dev, st);
+    slg::dfree(wsum, st);
+    slg::dfree(dsum, st);
+    const std::string msg = slg::g_last_error;
+    slg_free(h);
+    if (rc != SLG_OK) {
+        slg::g_last_error = msg;
+        return fail_all(rc);
+    }
+    slg::g_last_error.clear();
+    return SLG_OK;
 }
 
 slg_status slg_dual(slg_graph* h, void* stream, slg_graph** out) {

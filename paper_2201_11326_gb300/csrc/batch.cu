@@ -52,7 +52,53 @@ __global__ void k_gather_offsets(const int64_t* __restrict__ rowoff,
         out[b] = rowoff[row_base[b]];
 }
 
+// One CTA per member b: the sums of W[r] and dig[r] (mod 2^64) over its rows
+// row_base[b] .. row_base[b+1]-1.
+__global__ void k_member_sums(const int64_t* __restrict__ W,
+                              const unsigned long long* __restrict__ dig,
+                              const int32_t* __restrict__ row_base,
+                              long long* __restrict__ wsum, unsigned long long* __restrict__ dsum) {
+    constexpr int NT = 256;
+    __shared__ long long sw[NT / 32];
+    __shared__ unsigned long long sd[NT / 32];
+    const int b = blockIdx.x;
+    long long w = 0;
+    unsigned long long d = 0;
+    for (int64_t r = (int64_t)row_base[b] + threadIdx.x; r < row_base[b + 1]; r += NT) {
+        w += W[r];
+        if (dig) d += dig[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sw[threadIdx.x >> 5] = w;
+        sd[threadIdx.x >> 5] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tw = 0;
+        unsigned long long td = 0;
+        for (int x = 0; x < NT / 32; ++x) {
+            tw += sw[x];
+            td += sd[x];
+        }
+        wsum[b] = tw;
+        dsum[b] = td;
+    }
+}
+
 }  // namespace
+
+void launch_member_sums(const int64_t* W, const unsigned long long* rowdig,
+                        const int32_t* row_base_dev, int32_t k, long long* wsum_dev,
+                        unsigned long long* dsum_dev, cudaStream_t st) {
+    if (k <= 0) return;
+    k_member_sums<<<(unsigned)k, 256, 0, st>>>(W, rowdig, row_base_dev, wsum_dev, dsum_dev);
+    SLG_LAUNCH_CHECK();
+}
 
 void launch_concat(const BatchPart* parts_dev, int32_t k, int32_t M, int32_t N, int64_t NNZ,
                    const GraphDev& out, cudaStream_t st) {

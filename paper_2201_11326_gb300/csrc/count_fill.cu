@@ -72,15 +72,14 @@ __device__ __forceinline__ int table_add(int32_t* keys, int32_t* cnts, uint32_t 
     return -1;
 }
 
-// Several thresholds in one launch (an ensemble, Algorithm 3): the counting
-// pass counts every list's partners, the fill writes every list.
+// Several thresholds in one counting launch (an ensemble, Algorithm 3): the
+// counting pass counts every list's partners. (Each list is then filled by
+// the single-threshold kernels.)
 struct EnsArgs {
     int32_t k = 0;                   // number of lists (0: one threshold, from RowS)
     int32_t s[ENS_MAX] = {};         // thresholds, strictly ascending
     uint32_t bias[ENS_MAX] = {};     // 0x01010101 * (128 - min(s[t], 128)), see below
-    int64_t seg[ENS_MAX] = {};       // fill: first position of list t in I/J/O
-    const int64_t* ioff = nullptr;   // fill: per-item offsets of list t at [t * stride]
-    int32_t* icnt = nullptr;         // count: per-item counts of list t at [t * stride]
+    int32_t* icnt = nullptr;         // per-item counts of list t at [t * stride]
     int64_t stride = 0;
 };
 
@@ -419,6 +418,7 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     // ensemble: survivors of lists 1.. per warp segment of the current tile
     __shared__ int32_t wtot_e[ENS ? NW : 1][ENS ? ENS_MAX : 1];
     __shared__ int32_t sh_pos, sh_nnh;
+    static_assert(!(FILL && ENS), "ensemble lists are filled one at a time");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
@@ -459,13 +459,9 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         }
         const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
         int64_t out_pos = 0;
-        // ensemble: lane t (t >= 1) of every warp keeps list t's position
-        // (fill: the item's next output position before this tile; count: the
-        // item's survivors so far)
+        // ensemble count: lane t (t >= 1) of every warp keeps list t's
+        // survivors of the item so far
         int64_t ens_pos = 0;
-        if (ENS && FILL && lane > 0 && lane < ea.k)
-            ens_pos = ea.seg[lane] + ea.ioff[lane * ea.stride + q] -
-                      ea.ioff[lane * ea.stride + item_lo];
         __syncthreads();
         const int32_t nnh = sh_nnh;
         for (int32_t t0 = it.jlo; t0 < it.jhi; t0 += DENSE_TILE) {
@@ -531,19 +527,14 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 before += (w < warp) ? v : 0;
                 tile_total += v;
             }
-            int32_t ebefore = 0, etotal = 0;  // lane t: list t
+            int32_t etotal = 0;  // lane t: list t
             if (ENS && lane > 0 && lane < ea.k) {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const int32_t v = wtot_e[w][lane];
-                    ebefore += (w < warp) ? v : 0;
-                    etotal += v;
-                }
+                for (int w = 0; w < NW; ++w) etotal += wtot_e[w][lane];
             }
             if (FILL) {
                 // pass 2: write survivors at their ordered positions
                 int64_t base = obase + out_pos + before;
-                int64_t ebase = ens_pos + ebefore;  // lane t: list t
                 for (int32_t r = 0; r < DENSE_SEG / 32; ++r) {
                     const unsigned bal = __shfl_sync(0xffffffffu, r < 32 ? bs0 : bs1, r & 31);
                     if (bal == 0) continue;
@@ -562,25 +553,6 @@ k_dense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         }
                     }
                     base += __popc(bal);
-                    if (ENS) {
-                        for (int t = 1; t < ea.k; ++t) {
-                            const bool ft = mine && o >= ea.s[t];
-                            const unsigned bt = __ballot_sync(0xffffffffu, ft);
-                            if (bt == 0) break;
-                            const int64_t bt_base = __shfl_sync(0xffffffffu, ebase, t);
-                            if (ft) {
-                                const int64_t p2 = bt_base + __popc(bt & lt);
-                                if (p2 < limit) {
-                                    I[p2] = i - ib;
-                                    J[p2] = t0 + ci - ib;
-                                    O[p2] = o;
-                                } else {
-                                    atomicOr(err, ERR_BOUNDS);
-                                }
-                            }
-                            if (lane == t) ebase += __popc(bt);
-                        }
-                    }
                 }
             }
             out_pos += tile_total;
@@ -635,48 +607,6 @@ static_assert(WD_TILE % (128 * WD_CBLK) == 0 && WD_TILE_FILL % (128 * WD_CBLK) =
 static_assert(MAX_HUBS + WD_MAXR < 128, "byte-wise overlap sums must stay below 128");
 static_assert(WD_MAXR % 32 == 0 && WD_SLOTS >= 1 && WD_SLOTS <= 2, "cursors per lane");
 
-// Ensemble fill: the entries e (valid in the lanes with `valid`, ascending j
-// across lanes) of list 0 that were just stored also go to every list t >= 1
-// whose threshold they reach. Lane t holds list t's next position. Lists are
-// taken four at a time so that their ballots and broadcasts overlap; the lists
-// are nested (s ascending), so a group whose first list takes nothing ends it.
-constexpr int ENS_GROUP = 4;
-
-__device__ __forceinline__ void ens_append(int2 e, bool valid, int64_t& ens_pos, int32_t li,
-                                           int32_t ib, int lane, unsigned lt, const EnsArgs& ea,
-                                           int32_t* __restrict__ I, int32_t* __restrict__ J,
-                                           int32_t* __restrict__ O, int64_t limit,
-                                           int32_t* __restrict__ err) {
-    for (int t0 = 1; t0 < ea.k; t0 += ENS_GROUP) {
-        unsigned bal[ENS_GROUP];
-#pragma unroll
-        for (int u = 0; u < ENS_GROUP; ++u) {
-            const int t = t0 + u;
-            bal[u] = __ballot_sync(0xffffffffu, valid && t < ea.k && e.y >= ea.s[t & (ENS_MAX - 1)]);
-        }
-        if (bal[0] == 0) break;
-        int64_t base[ENS_GROUP];
-#pragma unroll
-        for (int u = 0; u < ENS_GROUP; ++u) base[u] = __shfl_sync(0xffffffffu, ens_pos, (t0 + u) & 31);
-#pragma unroll
-        for (int u = 0; u < ENS_GROUP; ++u) {
-            if ((bal[u] >> lane) & 1u) {
-                const int64_t p2 = base[u] + __popc(bal[u] & lt);
-                if (p2 < limit) {
-                    I[p2] = li;
-                    J[p2] = e.x - ib;
-                    O[p2] = e.y;
-                } else {
-                    atomicOr(err, ERR_BOUNDS);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < ENS_GROUP; ++u)
-            if (lane == t0 + u) ens_pos += __popc(bal[u]);
-    }
-}
-
 template <bool FILL, bool ENS>
 __global__ void __launch_bounds__(WD_WARPS * 32, (FILL || ENS) ? 3 : 4)
 k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
@@ -695,6 +625,7 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     uint32_t* ctr = dyn + (size_t)warp * wd_warp_words(FILL);
     int32_t* stage = reinterpret_cast<int32_t*>(ctr + WORDS);  // [0..63] cursor, [64..127] end
     int2* ring = reinterpret_cast<int2*>(stage + WD_STAGE_WORDS);  // fill only
+    static_assert(!(FILL && ENS), "ensemble lists are filled one at a time");
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
 
@@ -754,13 +685,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         }
         __syncwarp();
 
-        // ensemble: lane t keeps list t's next output position (fill) or
-        // count (counting pass); lists 1.. of a fill take their entries from
-        // list 0's ring as it is flushed
+        // ensemble count: lane t keeps list t's count
         int64_t ens_pos = 0;
-        if (ENS && FILL && lane > 0 && lane < ea.k)
-            ens_pos = ea.seg[lane] + ea.ioff[lane * ea.stride + q] -
-                      ea.ioff[lane * ea.stride + item_lo];
         // fill: survivors collect in the ring and leave it in chunks that end
         // on 128-byte boundaries of I (the first chunk is shorter)
         int64_t wpos = FILL ? ioff[q] - ioff[item_lo] : 0;  // next output position
@@ -912,9 +838,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     rcount += tot;
                     __syncwarp();
                     while (rcount >= need) {
-                        int2 e = make_int2(0, 0);
                         if (lane < need) {
-                            e = ring[(rhead + lane) & (WD_RING - 1)];
+                            const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
                             const int64_t p2 = wpos + lane;
                             if (p2 < limit) {
                                 I[p2] = i - ib;
@@ -924,8 +849,6 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                                 atomicOr(err, ERR_BOUNDS);
                             }
                         }
-                        if (ENS) ens_append(e, lane < need, ens_pos, i - ib, ib, lane, lt, ea, I, J,
-                                            O, limit, err);
                         rhead = (rhead + need) & (WD_RING - 1);
                         rcount -= need;
                         wpos += need;
@@ -946,9 +869,8 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             __syncwarp();
         }
         if (FILL && rcount > 0) {  // the slice's last, partial chunk
-            int2 e = make_int2(0, 0);
             if (lane < rcount) {
-                e = ring[(rhead + lane) & (WD_RING - 1)];
+                const int2 e = ring[(rhead + lane) & (WD_RING - 1)];
                 const int64_t p2 = wpos + lane;
                 if (p2 < limit) {
                     I[p2] = i - ib;
@@ -958,8 +880,6 @@ k_wdense_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     atomicOr(err, ERR_BOUNDS);
                 }
             }
-            if (ENS) ens_append(e, lane < rcount, ens_pos, i - ib, ib, lane, lt, ea, I, J, O, limit,
-                                err);
             __syncwarp();
         }
         if (!FILL && ENS) {
@@ -1067,15 +987,11 @@ void occupancy_init() {
     SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<false, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)DENSE_SMEM));
-    SLG_CUDA_TRY(cudaFuncSetAttribute(k_dense_items<true, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)DENSE_SMEM));
     sparse_setup(o.sms, o.sparse_ctas);
     wsparse_setup(o.sms, o.wsparse_ctas);
     o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
     o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
     o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
-    o.wdense_ctas[1][1] = wdense_setup<true, true>(o.sms);
     int a = 0, b = 0, c = 0;
     SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_warp_items<true>,
                                                                WARP_CTA_WARPS * 32, 0));
@@ -1094,13 +1010,15 @@ Occupancy& occupancy() {
 }
 
 constexpr unsigned ALL_MODES = (1u << NMODES) - 1u;
-// ensemble launches: handlers with a fused form, and those run once per list
+// ensemble counting launches: handlers with a fused form, and those run once
+// per list
 constexpr unsigned ENS_FUSED = (1u << MODE_DENSE) | (1u << MODE_WDENSE);
 constexpr unsigned ENS_PER_LIST = ALL_MODES & ~ENS_FUSED;
 
 // One launch per handler in `modes` that has items. queue: NMODES work-queue
-// heads (zeroed, used once); err: the shared error flag. With `ea`, the warp
-// dense handler runs its ensemble form (every list in one launch).
+// heads (zeroed, used once); err: the shared error flag. With `ea` (counting
+// pass only), the dense handlers run their ensemble form (every list in one
+// launch).
 template <bool FILL>
 void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
                   int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
@@ -1135,10 +1053,11 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         ran[MODE_DENSE] = true;
         tick(MODE_DENSE, 0);
         if (ea) {
-            k_dense_items<FILL, true><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
-                p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi,
-                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
-                O, queue + MODE_DENSE, limit, err, *ea);
+            if constexpr (!FILL)
+                k_dense_items<false, true><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
+                    p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi,
+                    g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I,
+                    J, O, queue + MODE_DENSE, limit, err, *ea);
         } else {
             k_dense_items<FILL, false><<<oc.dense_ctas, DENSE_THREADS, DENSE_SMEM, st>>>(
                 p.items, p.mode_list[MODE_DENSE], p.mode_rank[MODE_DENSE], item_lo, item_hi,
@@ -1153,10 +1072,11 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         tick(MODE_WDENSE, 0);
         const size_t smem = FILL ? WD_SMEM_FILL : WD_SMEM;
         if (ea) {
-            k_wdense_items<FILL, true><<<oc.wdense_ctas[FILL][1], WD_WARPS * 32, smem, st>>>(
-                p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi,
-                g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J,
-                O, queue + MODE_WDENSE, limit, err, *ea);
+            if constexpr (!FILL)
+                k_wdense_items<false, true><<<oc.wdense_ctas[0][1], WD_WARPS * 32, smem, st>>>(
+                    p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi,
+                    g.off, g.idx, g.hubidx, g.hubmask, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I,
+                    J, O, queue + MODE_WDENSE, limit, err, *ea);
         } else {
             k_wdense_items<FILL, false><<<oc.wdense_ctas[FILL][0], WD_WARPS * 32, smem, st>>>(
                 p.items, p.mode_list[MODE_WDENSE], p.mode_rank[MODE_WDENSE], item_lo, item_hi,
@@ -1261,27 +1181,6 @@ void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStr
     launch_items<false>(g, p, p.rs_for(p.ens.s[0]), 0, (int32_t)ni, nullptr, nullptr, nullptr,
                         nullptr, nullptr, 0, sc, err, mt, st, ENS_FUSED, &ea);
     check_scratch(sc, st, "ensemble counting pass", NMODES * k);
-}
-
-void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
-                       const int64_t* seg, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
-                       ModeTimer* mt, cudaStream_t st) {
-    if (item_hi <= item_lo) return;
-    const int32_t k = p.ens.k;
-    const int64_t ni = p.nitems;
-    int32_t* sc = new_scratch(st, NMODES * k);
-    int32_t* err = sc + NMODES * k;
-    for (int32_t t = 0; t < k; ++t)
-        launch_items<true>(g, p, p.rs_for(p.ens.s[t]), item_lo, item_hi, nullptr,
-                           p.ens.ioff + t * (ni + 1), I + seg[t], J + seg[t], O + seg[t],
-                           seg[t + 1] - seg[t], sc + NMODES * t, err, mt, st, ENS_PER_LIST);
-    EnsArgs ea = ens_args(p);
-    ea.ioff = p.ens.ioff;
-    ea.stride = ni + 1;
-    for (int32_t t = 0; t < k; ++t) ea.seg[t] = seg[t];
-    launch_items<true>(g, p, p.rs_for(p.ens.s[0]), item_lo, item_hi, nullptr, p.ens.ioff, I, J, O,
-                       limit, sc, err, mt, st, ENS_FUSED, &ea);
-    check_scratch(sc, st, "ensemble fill pass", NMODES * k);
 }
 
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,

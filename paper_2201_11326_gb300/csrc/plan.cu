@@ -244,19 +244,42 @@ __global__ void k_max_row(const int64_t* __restrict__ rowoff, int32_t m,
     if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
 
-// Per-handler totals: a row's items all share one mode.
+// Per-handler totals: a row's items all share one mode. Columns (MS_COLS):
+// rows, wedges, incidences, pairs, wedges through non-hub vertices, and the
+// candidate partners the dense handlers' extraction scans (one hub mask read
+// each) in the counting pass and in the fill (which skips items without pairs).
 __global__ void k_mode_stats(const int32_t* __restrict__ row_item, const Item* __restrict__ items,
                              const int64_t* __restrict__ W, const int32_t* __restrict__ size,
-                             const int64_t* __restrict__ rowoff, int32_t m,
+                             const int64_t* __restrict__ rowoff, const int64_t* __restrict__ ioff,
+                             const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                             const int32_t* __restrict__ hubidx, const int32_t* __restrict__ wbeg,
+                             const int32_t* __restrict__ wend, int32_t m,
                              unsigned long long* __restrict__ out) {
     GRID_STRIDE(i, m) {
-        const int32_t q = row_item[i];
-        if (row_item[i + 1] == q) continue;
-        const int mode = items[q].mode;
-        atomicAdd(&out[mode * 4 + 0], 1ull);
-        atomicAdd(&out[mode * 4 + 1], (unsigned long long)W[i]);
-        atomicAdd(&out[mode * 4 + 2], (unsigned long long)size[i]);
-        atomicAdd(&out[mode * 4 + 3], (unsigned long long)(rowoff[i + 1] - rowoff[i]));
+        const int32_t q0 = row_item[i], q1 = row_item[i + 1];
+        if (q1 == q0) continue;
+        const int mode = items[q0].mode;
+        unsigned long long nonhub = 0, scan_c = 0, scan_f = 0;
+        for (int32_t e = off[i]; e < off[i + 1]; ++e)
+            if (hubidx[idx[e]] < 0) nonhub += (unsigned long long)(wend[e] - wbeg[e]);
+        if (mode == MODE_DENSE || mode == MODE_WDENSE) {
+            for (int32_t q = q0; q < q1; ++q) {
+                const Item it = items[q];
+                // the warp handler starts its tiles at a multiple of 32 ids
+                const int32_t a = mode == MODE_WDENSE ? (it.jlo & ~31) : it.jlo;
+                const unsigned long long n = (unsigned long long)(it.jhi - a);
+                scan_c += n;
+                if (ioff[q + 1] != ioff[q]) scan_f += n;
+            }
+        }
+        unsigned long long* o = out + mode * MS_COLS;
+        atomicAdd(&o[0], 1ull);
+        atomicAdd(&o[1], (unsigned long long)W[i]);
+        atomicAdd(&o[2], (unsigned long long)size[i]);
+        atomicAdd(&o[3], (unsigned long long)(rowoff[i + 1] - rowoff[i]));
+        atomicAdd(&o[4], nonhub);
+        atomicAdd(&o[5], scan_c);
+        atomicAdd(&o[6], scan_f);
     }
 }
 
@@ -473,20 +496,22 @@ void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, Mod
     e.counted = true;
 }
 
-void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st) {
-    unsigned long long* d = dalloc<unsigned long long>(NMODES * 4, st);
-    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NMODES * 4, st));
+void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_COLS],
+                     cudaStream_t st) {
+    unsigned long long* d = dalloc<unsigned long long>(NMODES * MS_COLS, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NMODES * MS_COLS, st));
     if (g.m) {
         k_mode_stats<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.size,
-                                                         p.rowoff, g.m, d);
+                                                         p.rowoff, p.ioff, g.off, g.idx,
+                                                         g.hubidx, p.wbeg, p.wend, g.m, d);
         SLG_LAUNCH_CHECK();
     }
-    unsigned long long h[NMODES * 4];
+    unsigned long long h[NMODES * MS_COLS];
     SLG_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
     SLG_CUDA_TRY(cudaStreamSynchronize(st));
     dfree(d, st);
     for (int k = 0; k < NMODES; ++k)
-        for (int c = 0; c < 4; ++c) out[k][c] = (int64_t)h[k * 4 + c];
+        for (int c = 0; c < MS_COLS; ++c) out[k][c] = (int64_t)h[k * MS_COLS + c];
 }
 
 int64_t plan_max_row(const GraphDev& g, const int64_t* rowoff, cudaStream_t st) {

@@ -48,6 +48,11 @@ struct BatchPart {
 // hubidx[N]).
 void launch_concat(const BatchPart* parts_dev, int32_t k, int32_t M, int32_t N, int64_t NNZ,
                    const GraphDev& out, cudaStream_t st);
+// Per member b of a batch: wsum[b] = sum of W over its rows, dsum[b] = sum of
+// rowdig over its rows (mod 2^64; rowdig may be null, dsum is then 0).
+void launch_member_sums(const int64_t* W, const unsigned long long* rowdig,
+                        const int32_t* row_base_dev, int32_t k, long long* wsum_dev,
+                        unsigned long long* dsum_dev, cudaStream_t st);
 // out[b] = rowoff[row_base[b]] for b = 0..k
 void launch_gather_offsets(const int64_t* rowoff, const int32_t* row_base_dev, int32_t k,
                            int64_t* out_dev, cudaStream_t st);
@@ -119,13 +124,9 @@ void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTim
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
               cudaStream_t st);
-// Ensemble passes over the plan's items (p.ens.k lists, thresholds p.ens.s):
-// counts into p.ens.icnt; the fill writes list t of items [item_lo, item_hi)
-// at I/J/O + seg[t] (seg[k] = total).
+// Ensemble counting pass over the plan's items (p.ens.k lists, thresholds
+// p.ens.s): counts into p.ens.icnt. Lists are filled one at a time by run_fill.
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st);
-void run_fill_ensemble(const GraphDev& g, const Plan& p, int32_t item_lo, int32_t item_hi,
-                       const int64_t* seg, int32_t* I, int32_t* J, int32_t* O, int64_t limit,
-                       ModeTimer* mt, cudaStream_t st);
 // Sparse-accumulator handler (sparse.cu): kernel attributes and CTAs per
 // launch (count, fill), and one launch over the MODE_SPARSE items.
 void sparse_setup(int sms, int ctas[2]);
@@ -138,8 +139,11 @@ void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS r
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
                    int32_t* err, cudaStream_t st);
-// Per-handler totals over rows: rows, wedges, incidences, pairs (needs counts).
-void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][4], cudaStream_t st);
+// Per-handler totals over rows (needs counts): rows, wedges, incidences, pairs,
+// non-hub wedges, partners scanned by the dense extraction (count, fill).
+constexpr int MS_COLS = 7;
+void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_COLS],
+                     cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,

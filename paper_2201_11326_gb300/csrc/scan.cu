@@ -191,13 +191,21 @@ long long* noalloc_sums_on(int dev) {
     return g_noalloc_addr[dev];
 }
 
+// Device memory of the current device (or managed memory): the kernels may
+// not dereference another GPU's memory, which needs no peer mapping to exist.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -210,7 +218,7 @@ extern "C" slg_status slg_scan_counts_noalloc(const int32_t* counts, int64_t* of
             throw Error{SLG_EINVAL, "n must be in [0, 67108864] for the no-allocation scan"};
         if (!offsets || (n > 0 && !counts)) throw Error{SLG_EINVAL, "NULL argument"};
         if (!on_device(offsets) || (n > 0 && !on_device(counts)))
-            throw Error{SLG_EINVAL, "counts and offsets must be device memory"};
+            throw Error{SLG_EINVAL, "counts and offsets must be memory of the current device"};
         int dev = 0;
         SLG_CUDA_TRY(cudaGetDevice(&dev));
         long long* sums1 = noalloc_sums_on(dev);

@@ -42,6 +42,7 @@ struct ServeQuery {
     bool started = false, done = false, materialized = false;
     int64_t pairs = 0, wedges = 0;
     uint64_t digest = 0;
+    int32_t batch_size = 1;  // queries of the batch this one ran in (1: alone)
     int32_t *I = nullptr, *J = nullptr, *O = nullptr;
     std::string error;
 };
@@ -75,6 +76,8 @@ struct slg_server {
     // statistics since the last reset
     std::vector<double> lat_us;
     int64_t done_pairs = 0, done_wedges = 0, completed = 0;
+    int64_t batched = 0, batches = 0, batch_overflows = 0, batch_failures = 0;
+    std::string batch_error;  // the last batch failure's message
     Clock::time_point first_submit, last_done;
     bool any_submit = false;
 };
@@ -291,18 +294,35 @@ void worker_loop(slg_server* S, size_t wi) {
             std::lock_guard<std::mutex> lk(S->mu);
             for (size_t x = 0; x < tickets.size(); ++x) local[x] = S->q[tickets[x]];
         }
-        bool batched = false;
+        bool batched = false, failed = false;
+        std::string why;
         if (local.size() > 1) {
             try {
                 batched = run_batch(S, W, local);
-                for (ServeQuery& Q : local) Q.status = SLG_OK;
-            } catch (const slg::Error&) {
+                for (ServeQuery& Q : local) {
+                    Q.status = SLG_OK;
+                    Q.batch_size = batched ? (int32_t)local.size() : 1;
+                }
+            } catch (const slg::Error& e) {
                 for (ServeQuery& Q : local) {  // run them one by one instead
                     free_result(Q, W.st);
                     Q.materialized = false;
                     Q.digest = 0;
+                    Q.batch_size = 1;
                 }
                 batched = false;
+                failed = true;
+                why = e.msg;
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (batched) {
+                S->batches += 1;
+                S->batched += (int64_t)local.size();
+            } else if (failed) {
+                S->batch_failures += 1;
+                S->batch_error = why;
+            } else {
+                S->batch_overflows += 1;  // the lists together exceeded the window
             }
         }
         if (!batched) {
@@ -328,6 +348,7 @@ void worker_loop(slg_server* S, size_t wi) {
             Q.pairs = local_x.pairs;
             Q.wedges = local_x.wedges;
             Q.digest = local_x.digest;
+            Q.batch_size = local_x.batch_size;
             Q.I = local_x.I;
             Q.J = local_x.J;
             Q.O = local_x.O;
@@ -500,6 +521,7 @@ slg_status slg_serve_poll(slg_server* S, uint64_t ticket, int32_t timeout_ms,
     out->digest = Q.digest;
     out->latency_us = us_between(Q.t_submit, Q.t_done);
     out->queue_us = us_between(Q.t_submit, Q.t_start);
+    out->batch_size = Q.batch_size;
     if (Q.status != SLG_OK) return sfail(Q.status, Q.error);
     return SLG_OK;
 }
@@ -569,9 +591,15 @@ slg_status slg_serve_stats(slg_server* S, int32_t reset, slg_serve_stats_t* out)
     out->peak_memory = S->mem_peak;
     out->pending = (int64_t)S->pending.size();
     out->running = S->busy;
+    out->batched = S->batched;
+    out->batches = S->batches;
+    out->batch_overflows = S->batch_overflows;
+    out->batch_failures = S->batch_failures;
+    if (S->batch_failures) slg::set_error(SLG_OK, "last batch failure: " + S->batch_error);
     if (reset) {
         S->lat_us.clear();
         S->completed = S->done_pairs = S->done_wedges = 0;
+        S->batched = S->batches = S->batch_overflows = S->batch_failures = 0;
         S->any_submit = false;
         S->mem_peak = S->mem_in_use;
     }

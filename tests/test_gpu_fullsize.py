@@ -191,3 +191,172 @@ def test_large_full_size_sampled_rows(large):
     for k, s in enumerate(s_list):
         assert np.array_equal(counts[s][rows], ocount[:, k]), f"s={s}"
         assert np.array_equal(digs[s][rows], odig[:, k]), f"s={s}"
+
+
+# ------------------------------------------------------- the batched workload
+
+@pytest.fixture(scope="module")
+def batch_full():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    slg.build.build()
+    return torch, [synth.batch_member(b) for b in range(4096)]
+
+
+def test_batch_full_size_sampled_rows(batch_full):
+    """The 4,096-graph batch exactly as the batch benchmark runs it (one batch
+    handle, autotuned bins, windows of 2^33 pairs): each member's pair count
+    equals its own slg_count, the batch's W is the sum of the members', and
+    per-row counts and digests of 1,000 seeded random rows and the 100 rows with
+    the most wedges (spread over the members) equal the oracle's on the owning
+    member (rows are independent units of Algorithm 2, so sampled rows are a
+    sound check)."""
+    torch, members = batch_full
+    dev = torch.device("cuda")
+    hs = [h for h, _ in members]
+    s_list = [s for _, s in members]
+    gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    b = slg.slg_batch_load(gs, s_list)
+    try:
+        slg.slg_autotune(b, 0, max_trials=24)
+        pairs, wedges = slg.slg_count(b, 0)
+        rb = slg.slg_batch_info(b)
+        pb = slg.slg_batch_pair_offsets(b)
+        rowoff = slg.slg_row_offsets(b, 0)
+        counts = np.diff(rowoff)
+        assert int(counts.sum()) == pairs == int(pb[-1])
+        I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        digests = torch.zeros(b.m, dtype=torch.int64, device=dev)
+        splits = slg.slg_plan_windows(b, 0, WINDOW)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            P, _ = slg.slg_build_window(b, 0, int(r0), int(r1), I, J, O, WINDOW,
+                                        row_digests=digests[int(r0):int(r1)])
+            assert P == rowoff[r1] - rowoff[r0]
+        dig = digests.cpu().numpy().view(np.uint64)
+        del I, J, O
+        own_w = 0
+        for k, (g, s) in enumerate(zip(gs, s_list)):
+            p, w = slg.slg_count(g, s)
+            assert int(pb[k + 1] - pb[k]) == p, k
+            own_w += w
+        assert wedges == own_w
+    finally:
+        b.free()
+        for g in gs:
+            g.free()
+    # 1000 random rows of the whole batch, and the 100 heaviest rows of the 64
+    # largest members (the members of the largest m hold the heaviest rows)
+    rng = np.random.default_rng([7, 4096])
+    rows = set(rng.choice(int(rb[-1]), size=1000, replace=False).tolist())
+    big = np.argsort([-h.m for h in hs], kind="stable")[:64]
+    heavy = []
+    for k in big:
+        w = row_wedges(hs[k], s_list[k])
+        top = np.argsort(-w, kind="stable")[:100]
+        heavy += [(int(w[i]), int(rb[k]) + int(i)) for i in top]
+    rows |= {r for _, r in sorted(heavy, reverse=True)[:100]}
+    rows = np.array(sorted(rows), np.int64)
+    owner = np.searchsorted(rb, rows, side="right") - 1
+    for k in np.unique(owner):
+        sel = rows[owner == k]
+        h = hs[k]
+        oc, od, _ = oracle.rows(h.off, h.idx, (sel - rb[k]).astype(np.int32), [s_list[k]])
+        assert np.array_equal(counts[sel], oc[:, 0]), k
+        assert np.array_equal(dig[sel], od[:, 0]), k
+
+
+# -------------------------------------------------------- the served workload
+
+SERVE_CFG = dict(memory_budget=64 << 30, window_pairs=1 << 28, max_result_pairs=1 << 26,
+                 workers=8, max_s=16, digest=True, policy=1, small_workers=2,
+                 small_wedges=2_000_000_000, batch_max=8)
+ORACLE_FULL_M = 40000  # graphs up to this size are checked on every row
+
+
+def test_served_set_full_size():
+    """The 64 resident graphs of the served workload (8 with m = 1,000,000 and 56
+    with m log-uniform in [1e3, 1e5]) behind the served benchmark's server
+    configuration, with one or two queries per graph submitted together so
+    that they mix (and small ones batch). Every query's |L_s| and list digest
+    must be exact: against the oracle over all rows for the graphs with m <=
+    40,000, and for the larger ones against the library's own windowed build,
+    whose per-row counts and digests are then checked against the oracle on
+    300 seeded random rows and the 20 rows with the most wedges."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    slg.build.build()
+    dev = torch.device("cuda")
+    hs = [synth.served_member(g) for g in range(64)]
+    gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    rng = np.random.default_rng([5, 64])
+    queries = []
+    for g in range(64):
+        for s in rng.choice(np.arange(1, 17), size=1 if g < 8 else 2, replace=False):
+            queries.append((g, int(s)))
+    order = rng.permutation(len(queries))
+    got = {}
+    try:
+        srv = slg.Server(**SERVE_CFG)
+        try:
+            ids = [slg.slg_serve_register(srv, g) for g in gs]
+            tickets = [(queries[q], slg.slg_serve_submit(srv, ids[queries[q][0]], queries[q][1]))
+                       for q in order]
+            for (g, s), t in tickets:
+                r = slg.slg_serve_poll(srv, t, 1_800_000)
+                assert r["status"] == 0, (g, s)
+                got[(g, s)] = (r["pairs"], r["digest"], r["wedges"])
+                slg.slg_serve_release(srv, t)
+            st = slg.slg_serve_stats(srv)
+        finally:
+            srv.close()
+        assert st["completed"] == len(queries) and st["batch_failures"] == 0
+        # W_s of every query from its closed form
+        for (g, s), (_, _, w) in got.items():
+            h = hs[g]
+            sz = np.diff(h.off)
+            deg = np.bincount(h.idx[np.repeat(sz >= s, sz)], minlength=h.n).astype(np.int64)
+            assert w == int((deg * (deg - 1) // 2).sum()), (g, s)
+        # whole lists against the oracle
+        for g in range(64):
+            h = hs[g]
+            mine = sorted(s for (gg, s) in got if gg == g)
+            if h.m > ORACLE_FULL_M:
+                continue
+            oc, od, _ = oracle.rows(h.off, h.idx, None, mine)
+            for t, s in enumerate(mine):
+                assert got[(g, s)][0] == int(oc[:, t].sum()), (g, s)
+                assert got[(g, s)][1] == int(od[:, t].astype(np.uint64).sum(dtype=np.uint64)), (g, s)
+        # the larger graphs: the served result against the windowed build, and the
+        # windowed build's sampled rows against the oracle
+        win = 1 << 31
+        I = torch.empty(win, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        for (g, s) in sorted(got):
+            h = hs[g]
+            if h.m <= ORACLE_FULL_M:
+                continue
+            rowoff = slg.slg_row_offsets(gs[g], s)
+            digests = torch.zeros(h.m, dtype=torch.int64, device=dev)
+            splits = slg.slg_plan_windows(gs[g], s, win)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                slg.slg_build_window(gs[g], s, int(r0), int(r1), I, J, O, win,
+                                     row_digests=digests[int(r0):int(r1)])
+            dig = digests.cpu().numpy().view(np.uint64)
+            counts = np.diff(rowoff)
+            assert got[(g, s)][0] == int(counts.sum()), (g, s)
+            assert got[(g, s)][1] == int(dig.sum(dtype=np.uint64)), (g, s)
+            r2 = np.random.default_rng([7, g, s])
+            w = row_wedges(h, s)
+            rows = np.unique(np.concatenate([r2.choice(h.m, size=300, replace=False),
+                                             np.argsort(-w, kind="stable")[:20]])).astype(np.int32)
+            oc, od, _ = oracle.rows(h.off, h.idx, rows, [s])
+            assert np.array_equal(counts[rows], oc[:, 0]), (g, s)
+            assert np.array_equal(dig[rows], od[:, 0]), (g, s)
+    finally:
+        for g in gs:
+            g.free()

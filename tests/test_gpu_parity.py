@@ -442,3 +442,55 @@ def test_counter_width_boundaries(mode):
     h = synth.Hypergraph(off, idx, n)
     for s in (1, 2, 32, 255, 256):
         assert_same(gpu_list(h, s, FORCED[mode]), oracle_list("width", h, s), f"{mode} s={s}")
+
+
+def test_slg_batch_call_matches_oracle():
+    # the one-call batch: per member |L_s|, W_s, digest and (when asked) the list
+    hs, s_list = _batch_members()
+    gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
+    try:
+        want = [k % 2 == 0 for k in range(len(hs))]
+        res = slg.slg_batch(gs, s_list, want_lists=want)
+        assert len(res) == len(hs)
+        for k, (h, s, r) in enumerate(zip(hs, s_list, res)):
+            wI, wJ, wO = oracle.slg(h.off, h.idx, s)
+            assert r["status"] == 0 and r["pairs"] == wI.size, k
+            assert r["digest"] == oracle.list_digest(wI, wJ, wO), k
+            sz = np.diff(h.off)
+            deg = np.bincount(h.idx[np.repeat(sz >= s, sz)], minlength=h.n).astype(np.int64)
+            assert r["wedges"] == int((deg * (deg - 1) // 2).sum()), k
+            if want[k]:
+                assert_same((r["I"], r["J"], r["O"]), (wI, wJ, wO), f"slg_batch member {k}")
+            else:
+                assert "I" not in r
+        # a bad threshold fails the whole call with every status set
+        with pytest.raises(slg.SlgError) as ei:
+            slg.slg_batch(gs, [0] * len(gs))
+        assert ei.value.code == slg.SLG_EINVAL
+    finally:
+        for g in gs:
+            g.free()
+
+
+def test_slg_batch_windows_smaller_than_the_list():
+    # a member list that spans several of the call's device windows (at most 2^27
+    # pairs each): two copies of a graph whose s = 1 list has 1.9e8 pairs
+    h = synth.medium(seed=3, m=20000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        pairs, _ = slg.slg_count(g, 1)
+        assert pairs > (1 << 27)
+        res = slg.slg_batch([g, g], [1, 6], want_lists=[True, False])
+        counts, digs, _ = oracle.rows(h.off, h.idx, None, [1, 6])
+        for k, col in ((0, 0), (1, 1)):
+            assert res[k]["pairs"] == int(counts[:, col].sum())
+            assert res[k]["digest"] == int(digs[:, col].astype(np.uint64).sum(dtype=np.uint64))
+        I, J, O = res[0]["I"], res[0]["J"], res[0]["O"]
+        rowoff = np.concatenate([[0], np.cumsum(counts[:, 0])])
+        rng = np.random.default_rng(8)
+        for i in rng.choice(h.m, size=60, replace=False).tolist() + [0, h.m - 1]:
+            wj, wo = oracle.row_list(h.off, h.idx, i, 1)
+            a, b = int(rowoff[i]), int(rowoff[i + 1])
+            assert np.all(I[a:b] == i) and np.array_equal(J[a:b], wj) and np.array_equal(O[a:b], wo)
+    finally:
+        g.free()

@@ -152,8 +152,10 @@ def test_batched_small_queries_match_oracle(graphs):
         rng = np.random.default_rng(17)
         queries = [(int(rng.integers(0, len(gs))), int(rng.integers(1, 9))) for _ in range(48)]
         tickets = [slg.slg_serve_submit(srv, ids[g], s) for g, s in queries]
+        sizes = []
         for t, (g, s) in zip(tickets, queries):
             r = slg.slg_serve_poll(srv, t, 120000)
+            sizes.append(r["batch_size"])
             h = hs[g]
             wI, wJ, wO = oracle.slg_par(h.off, h.idx, s)
             assert r["status"] == 0 and r["pairs"] == wI.size, (g, s)
@@ -165,6 +167,11 @@ def test_batched_small_queries_match_oracle(graphs):
                 I, J, O = slg.slg_serve_fetch(srv, t, r["pairs"])
                 assert np.array_equal(I, wI) and np.array_equal(J, wJ) and np.array_equal(O, wO)
             slg.slg_serve_release(srv, t)
-        assert slg.slg_serve_stats(srv)["completed"] == len(queries)
+        st = slg.slg_serve_stats(srv)
+        assert st["completed"] == len(queries)
+        # batches really formed, and none failed over to one-by-one runs
+        assert st["batch_failures"] == 0, st.get("batch_error")
+        assert st["batches"] > 0 and st["batched"] == sum(1 for x in sizes if x > 1)
+        assert max(sizes) > 1
     finally:
         srv.close()

@@ -67,6 +67,62 @@ def test_noalloc_scan_equals_regular_path(torch_cuda):
         assert np.array_equal(got, want), (h.name, s)
 
 
+def scan_with_noalloc(torch, counts, stream):
+    out = torch.full((counts.numel() + 1,), -7, dtype=torch.int64, device="cuda")
+    code = slg.lib().slg_scan_counts_noalloc(counts.data_ptr(), out.data_ptr(), counts.numel(),
+                                            stream.cuda_stream)
+    assert code == slg.SLG_OK, slg.lib().slg_last_error()
+    stream.synchronize()
+    return out
+
+
+def test_noalloc_scan_single_tile_and_capacity_edge(torch_cuda):
+    # one tile (n <= 2048: no tile sums at all) and exactly the capacity
+    # (67,108,864 counts: 32768 level-1 and 16 level-2 tile sums, the last one
+    # at the end of the fixed array), against numpy's cumulative sum
+    torch = torch_cuda
+    st = torch.cuda.Stream()
+    rng = np.random.default_rng(31)
+    for n in (1, 5, 2047, 2048, 2049, 67_108_864):
+        c = rng.integers(0, 4, size=n, dtype=np.int32)
+        if n == 67_108_864:
+            c[-1] = 1_000_000  # the last count reaches only the last offset
+        got = scan_with_noalloc(torch, torch.from_numpy(c).cuda(), st).cpu().numpy()
+        want = np.zeros(n + 1, np.int64)
+        np.cumsum(c, out=want[1:])
+        assert np.array_equal(got, want), n
+        del c, got, want
+
+
+def test_noalloc_scan_allocates_nothing(torch_cuda):
+    # after the first call (which may load the library's kernels), further calls
+    # change neither torch's allocations nor the device's free memory
+    torch = torch_cuda
+    st = torch.cuda.Stream()
+    counts = torch.randint(0, 9, (3_000_000,), dtype=torch.int32, device="cuda")
+    out = torch.empty(counts.numel() + 1, dtype=torch.int64, device="cuda")
+    lib = slg.lib()
+
+    def call():
+        assert lib.slg_scan_counts_noalloc(counts.data_ptr(), out.data_ptr(), counts.numel(),
+                                           st.cuda_stream) == slg.SLG_OK
+        st.synchronize()
+
+    call()
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0, (free0, free1)
+    want = torch.zeros_like(out)
+    want[1:] = torch.cumsum(counts.to(torch.int64), 0)
+    assert torch.equal(out, want)
+
+
 def test_noalloc_scan_limits(torch_cuda):
     torch = torch_cuda
     lib = slg.lib()
