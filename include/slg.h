@@ -251,14 +251,14 @@ slg_status slg_last_timing(slg_graph* g, float* ms5);
 /*
  * Number of handlers (SLG_NMODES): 0 = warp table, 1 = CTA table, 2 = CTA
  * dense tiles, 3 = warp dense tiles, 4 = CTA sparse accumulator, 5 = warp
- * sparse accumulator.
+ * sparse accumulator (hash rounds), 6 = hub pairs (see slg_set_hub_pairs).
  *
  * Per-handler kernel time accumulated while timing is enabled:
  * ms[pass*SLG_NMODES + mode] and launches[pass*SLG_NMODES + mode] (2 *
  * SLG_NMODES entries each), pass 0 = counting, 1 = fill. reset != 0 zeroes
  * the totals after reading. Either output may be NULL.
  */
-#define SLG_NMODES 6
+#define SLG_NMODES 7
 slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms, int64_t* launches);
 
 /*
@@ -504,6 +504,32 @@ slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_ite
                         int32_t dense_min_density, int32_t dense_item_tiles,
                         int32_t wdense_max_ranges, int32_t sparse_min_per_tile,
                         int32_t sparse_item_wedges, int32_t wsparse_max_size);
+
+/*
+ * slg_set_hub_pairs -- the hub-pair handler for sparse rows at s >= 2.
+ *
+ * Algorithm 2 (Section III-C) counts every wedge (i, v, j). A pair with
+ * overlap >= s >= 2 shares either a vertex outside the max_hubs highest-degree
+ * vertices ("hubs") or at least two hubs. So for s >= 2 a row's partners can be
+ * taken from its wedges through non-hub vertices and from the lists of rows
+ * holding a pair of its hubs (built once per graph: the transpose of every
+ * row's hub pairs); a partner sharing t hubs appears in t(t-1)/2 of those
+ * lists, which gives t, and one look at the partner's hubs settles t <= 1.
+ * Pairs that share a single hub and nothing else are never visited. The result
+ * is the same list; only the work changes. A row (|e_i| <= 255, not dense)
+ * uses the handler when its hub-pair work is at most half its wedges.
+ *
+ *   max_hubs          : hubs of the index, at most 4096 (fewer when the index
+ *                       would exceed about 1.9e9 entries or the free device
+ *                       memory); 0 disables the handler. Default 4096.
+ *   min_sparse_wedges : the index is built by the first plan for s >= 2 whose
+ *                       table and sparse-accumulator rows carry at least this
+ *                       many wedges (default 2^33); 0 builds it whenever such
+ *                       rows exist.
+ * Releases the plan and any index built before. Not available on batches or
+ * on a server's views.
+ */
+slg_status slg_set_hub_pairs(slg_graph* g, int32_t max_hubs, int64_t min_sparse_wedges);
 
 /*
  * slg_autotune -- choose the binning thresholds of slg_set_bins for s on this

@@ -24,7 +24,7 @@ __all__ = [
     "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
-    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -110,6 +110,7 @@ _SIGS = {
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "slg_set_hub_pairs": (_i32, [_vp, _i32, _i64]),
     "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
@@ -398,8 +399,8 @@ def slg_last_timing(g: Graph):
     return list(ms)
 
 
-NMODES = 6
-MODE_NAMES = ("warp", "block", "dense", "wdense", "sparse", "wsparse")
+NMODES = 7
+MODE_NAMES = ("warp", "block", "dense", "wdense", "sparse", "wsparse", "hubpair")
 
 
 def slg_kernel_stats(g: Graph, reset: bool = False):
@@ -592,6 +593,11 @@ def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 
     _check(lib().slg_set_bins(g.handle, warp_max_wedges, block_item_wedges, dense_min_density,
                               dense_item_tiles, wdense_max_ranges, sparse_min_per_tile,
                               sparse_item_wedges, wsparse_max_size))
+
+
+def slg_set_hub_pairs(g: Graph, max_hubs: int = 4096, min_sparse_wedges: int = 1 << 33):
+    """Hub-pair handler for sparse rows at s >= 2 (max_hubs = 0 disables it)."""
+    _check(lib().slg_set_hub_pairs(g.handle, max_hubs, min_sparse_wedges))
 
 
 def slg_autotune(g: Graph, s: int, max_trials: int = 24):

@@ -102,6 +102,25 @@ void mtimer_init(ModeTimer& t) {
         if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
 }
 
+void build_plan(slg_graph* h, int32_t s, const BinParams& bp) {
+    Plan& p = h->plan;
+    const bool allowed = s >= 2 && h->owns_data && !h->g.srow && h->hp_max_hubs >= 2;
+    if (!allowed) {
+        plan_build(h->g, s, bp, p, h->st, nullptr);
+        return;
+    }
+    if (!h->hp.built && !h->hp.tried) {
+        // decide on the plan without hub pairs: worth it only when the rows that
+        // would walk every wedge (table and sparse-accumulator rows) carry many
+        plan_build(h->g, s, bp, p, h->st, nullptr);
+        const int64_t sw = plan_sparse_wedges(h->g, p, h->st);
+        if (sw == 0 || sw < h->hp_min_wedges) return;
+        hubpair_build(h->g, std::min(h->hp_max_hubs, HP_MAXK), h->hp_max_pairs, h->hp, h->st);
+        if (!h->hp.built) return;
+    }
+    plan_build(h->g, s, bp, p, h->st, h->hp.built ? &h->hp : nullptr);
+}
+
 slg_graph* make_view(const slg_graph* base, cudaStream_t st) {
     slg_graph* h = new slg_graph();
     h->g = base->g;
@@ -170,7 +189,7 @@ void ensure_counted(slg_graph* h, int32_t s) {
     slg::Plan& p = h->plan;
     if (p.built && p.s == s && p.counted) return;
     h->timer.mark(0, h->st);
-    if (!(p.built && p.s == s)) slg::plan_build(h->g, s, h->bp, p, h->st);
+    if (!(p.built && p.s == s)) slg::build_plan(h, s, h->bp);
     h->timer.mark(1, h->st);
     slg::run_count(h->g, p, p.rs, p.icnt, &h->mtimer, h->st);
     h->timer.mark(2, h->st);
@@ -201,7 +220,7 @@ void ensure_ensemble(slg_graph* h, const int32_t* s_list, int32_t k) {
         std::equal(s_list, s_list + k, p.ens.s))
         return;
     h->timer.mark(0, h->st);
-    if (!(p.built && p.s == s_list[0])) slg::plan_build(h->g, s_list[0], h->bp, p, h->st);
+    if (!(p.built && p.s == s_list[0])) slg::build_plan(h, s_list[0], h->bp);
     h->timer.mark(1, h->st);
     slg::ensemble_count(h->g, p, s_list, k, &h->mtimer, h->st);  // synchronises
     h->timer.mark(2, h->st);
@@ -349,6 +368,7 @@ void slg_free(slg_graph* h) {
     } catch (...) {
     }
     if (h->owns_data) free_graph_dev(h->g, h->st);
+    h->hp.release(h->st);
     cudaStreamSynchronize(h->st);
     h->timer.destroy();
     for (auto& e : h->mtimer.ev)
@@ -386,7 +406,7 @@ slg_status slg_bound(slg_graph* h, int32_t s, int64_t* pairs_ub) {
     if (!h || !pairs_ub) return fail(SLG_EINVAL, "NULL argument");
     API_BEGIN
     check_s(h, s);
-    if (!h->plan.built || h->plan.s != s) slg::plan_build(h->g, s, h->bp, h->plan, h->st);
+    if (!h->plan.built || h->plan.s != s) slg::build_plan(h, s, h->bp);
     // every s-incident pair accounts for at least s wedges (at least 1 in a batch)
     *pairs_ub = h->plan.wedges / (s > 0 ? s : 1);
     API_END
@@ -716,6 +736,19 @@ slg_status slg_set_bins(slg_graph* h, int32_t warp_max_wedges, int32_t block_ite
     h->bp.sparse_item_wedges = sparse_item_wedges;
     h->bp.wsparse_max_size = wsparse_max_size;
     h->plan.release(h->st);
+    API_END
+}
+
+slg_status slg_set_hub_pairs(slg_graph* h, int32_t max_hubs, int64_t min_sparse_wedges) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (max_hubs < 0 || max_hubs > slg::HP_MAXK || min_sparse_wedges < 0)
+        return fail(SLG_EINVAL, "max_hubs must be in [0, 4096], min_sparse_wedges >= 0");
+    API_BEGIN
+    h->plan.release(h->st);
+    h->hp.release(h->st);
+    h->hp.tried = false;
+    h->hp_max_hubs = max_hubs;
+    h->hp_min_wedges = min_sparse_wedges;
     API_END
 }
 

@@ -52,7 +52,7 @@ float autotune_trial(slg_graph* h, int32_t s, const BinParams& bp,
     Plan& p = h->plan;
     p.release(h->st);
     SLG_CUDA_TRY(cudaEventRecord(e0, h->st));
-    plan_build(h->g, s, bp, p, h->st);
+    build_plan(h, s, bp);
     run_count(h->g, p, p.rs, p.icnt, nullptr, h->st);
     plan_offsets(h->g, p, h->st);
     for (const auto& w : sample) {
@@ -79,7 +79,7 @@ void autotune(slg_graph* h, int32_t s, int32_t max_trials, float* best_ms_out) {
     // per-row counts do not depend on the binning: take the sample from the
     // current one
     h->plan.release(h->st);
-    plan_build(h->g, s, h->bp, h->plan, h->st);
+    build_plan(h, s, h->bp);
     run_count(h->g, h->plan, h->plan.rs, h->plan.icnt, nullptr, h->st);
     plan_offsets(h->g, h->plan, h->st);
     std::vector<int64_t> rowoff((size_t)m + 1);

@@ -956,6 +956,7 @@ __global__ void k_digest(const int32_t* __restrict__ I, const int32_t* __restric
 struct Occupancy {
     int sms = 0;
     int warp_ctas = 0, block_ctas = 0, dense_ctas = 0, sparse_ctas[2] = {}, wsparse_ctas[2] = {};
+    int hubpair_ctas[2] = {};
     int wdense_ctas[2][2] = {};  // [fill][ensemble]
 };
 
@@ -989,6 +990,7 @@ void occupancy_init() {
                                       (int)DENSE_SMEM));
     sparse_setup(o.sms, o.sparse_ctas);
     wsparse_setup(o.sms, o.wsparse_ctas);
+    hubpair_setup(o.sms, o.hubpair_ctas);
     o.wdense_ctas[0][0] = wdense_setup<false, false>(o.sms);
     o.wdense_ctas[1][0] = wdense_setup<true, false>(o.sms);
     o.wdense_ctas[0][1] = wdense_setup<false, true>(o.sms);
@@ -1099,6 +1101,13 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         launch_wsparse(FILL, oc.wsparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J,
                        O, queue + MODE_WSPARSE, limit, err, st);
         tick(MODE_WSPARSE, 1);
+    }
+    if (want(MODE_HUBPAIR) && p.hp) {
+        ran[MODE_HUBPAIR] = true;
+        tick(MODE_HUBPAIR, 0);
+        launch_hubpair(FILL, oc.hubpair_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J,
+                       O, queue + MODE_HUBPAIR, limit, err, st);
+        tick(MODE_HUBPAIR, 1);
     }
     if (timed) {
         for (int k = 0; k < NMODES; ++k) {

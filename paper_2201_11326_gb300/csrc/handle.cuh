@@ -33,6 +33,12 @@ struct slg_graph {
     slg::ModeTimer mtimer;
     float ms[5] = {0, 0, 0, 0, 0};
     std::vector<int32_t> batch_row_base;  // members' first rows (k+1) when this is a batch
+    // hub pairs (MODE_HUBPAIR): built on the first plan for s >= 2 whose table
+    // and sparse-accumulator rows carry at least hp_min_wedges wedges
+    slg::HubPairs hp;
+    int32_t hp_max_hubs = slg::HP_MAXK;           // 0 disables the hub-pair handler
+    int64_t hp_min_wedges = (int64_t)1 << 33;
+    int64_t hp_max_pairs = (int64_t)1900000000;  // hub-pair incidences at most
 };
 
 namespace slg {
@@ -40,6 +46,10 @@ namespace slg {
 // A handle that shares base's device arrays (which must outlive it) with its
 // own plan and stream, so that several s of one graph can run concurrently.
 slg_graph* make_view(const slg_graph* base, cudaStream_t st);
+
+// Builds h->plan for s (s = 0: a batch's own thresholds), deciding on the way
+// whether the hub-pair handler applies and building the hub pairs when it does.
+void build_plan(slg_graph* h, int32_t s, const BinParams& bp);
 
 // Chooses h->bp for s by timing binnings on h (autotune.cu); the plan is left
 // released.

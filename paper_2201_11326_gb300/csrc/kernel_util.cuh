@@ -22,6 +22,12 @@ __device__ __forceinline__ int32_t lower_bound_dev(const int32_t* __restrict__ a
     return lo;
 }
 
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
 template <int NT>
 __device__ __forceinline__ int32_t block_excl_scan(int32_t x, int32_t* total, int32_t* tmp) {
     // tmp: NT/32 + 1 ints of shared memory

@@ -107,15 +107,83 @@ __global__ void k_row_work(const int32_t* __restrict__ off, const int32_t* __res
     if (lane == 0 && acc_total) atomicAdd(wtotal, acc_total);
 }
 
+// Hub-pair work of row i for s (MODE_HUBPAIR): the wedge range of each of its
+// hub-pair incidences in the pruned pair lists, and per row the entries to
+// walk (non-HP-hub wedges plus pair-list hits) and their first and last
+// partner. Rows outside E_s get empty ranges.
+__global__ void k_pair_ranges(const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                              const int32_t* __restrict__ size, const int32_t* __restrict__ wbeg,
+                              const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs,
+                              const int32_t* __restrict__ hp_id, const int32_t* __restrict__ off2,
+                              const int32_t* __restrict__ idx2, const int32_t* __restrict__ tpos2,
+                              const int32_t* __restrict__ offT2, const int32_t* __restrict__ ks2,
+                              const int32_t* __restrict__ idxT2s, int32_t m, RowS rs,
+                              int32_t* __restrict__ wbeg2, int32_t* __restrict__ wend2,
+                              int64_t* __restrict__ Wp, int32_t* __restrict__ lo2,
+                              int32_t* __restrict__ hi2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < m; i += nwarps) {
+        const bool kept = size[i] >= rs.s_of((int32_t)i);
+        int64_t w = 0;
+        int32_t lo = INT32_MAX, hi = -1;
+        for (int32_t e = off[i] + lane; e < off[i + 1]; e += 32) {
+            const int32_t b = wbeg[e], t = wend[e];
+            if (t > b && hp_id[idx[e]] < 0) {
+                w += t - b;
+                lo = min(lo, idxTs[b]);
+                hi = max(hi, idxTs[t - 1]);
+            }
+        }
+        for (int32_t f = off2[i] + lane; f < off2[i + 1]; f += 32) {
+            int32_t b = 0, t = 0;
+            if (kept) {
+                const int32_t key = idx2[f];
+                const int32_t q = tpos2[f];
+                b = (ks2 ? ks2[q] : q) + 1;
+                t = ks2 ? ks2[offT2[key + 1]] : offT2[key + 1];
+            }
+            wbeg2[f] = b;
+            wend2[f] = t;
+            if (t > b) {
+                w += t - b;
+                lo = min(lo, idxT2s[b]);
+                hi = max(hi, idxT2s[t - 1]);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, d);
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+        }
+        if (lane == 0) {
+            // rows with many hub pairs slice poorly: every work item searches
+            // every range; they keep the other handlers
+            Wp[i] = (off2[i + 1] - off2[i] <= HP_MAXR) ? w : -1;
+            lo2[i] = lo;
+            hi2[i] = hi;
+        }
+    }
+}
+
 struct RowItems {
     int32_t mode;
     int32_t count;
-    int64_t step;  // j width of each item (dense) or 0 (uniform split)
+    int64_t step;    // j width of each item (dense) or 0 (uniform split)
+    int32_t lo, hi;  // the partner range the items split
+};
+
+// hub-pair inputs of a row (wp < 0: not available)
+struct RowHP {
+    int64_t wp;
+    int32_t lo, hi;
 };
 
 __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, int32_t nnh,
-                             int32_t s, BinParams bp) {
-    RowItems r{MODE_WARP, 0, 0};
+                             int32_t s, BinParams bp, RowHP hp) {
+    RowItems r{MODE_WARP, 0, 0, lo, hi};
     if (w <= 0) return r;
     const int64_t span = (int64_t)hi - lo + 1;
     if (w <= bp.warp_max_wedges) {
@@ -136,6 +204,22 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
         r.mode = MODE_DENSE;
         r.step = (int64_t)DENSE_TILE * bp.dense_item_tiles;
         r.count = (int32_t)((span + r.step - 1) / r.step);
+        return r;
+    }
+    // hub pairs: at s >= 2 the row walks its non-hub wedges and the rows sharing
+    // a pair of its hubs, when that is at most half its wedges (no entry at all:
+    // no partner can reach an overlap of 2, and the row has no item)
+    if (hp.wp >= 0 && s >= 2 && size <= SP_MAX_SIZE && 2 * hp.wp <= w) {
+        r.mode = MODE_HUBPAIR;
+        if (hp.wp == 0) return r;
+        r.lo = hp.lo;
+        r.hi = hp.hi;
+        const int64_t span2 = (int64_t)hp.hi - hp.lo + 1;
+        int64_t k = (hp.wp + HP_ITEM - 1) / HP_ITEM;
+        const int64_t kmax = (span2 + 1023) / 1024;
+        if (k > kmax) k = kmax;
+        if (k < 1) k = 1;
+        r.count = (int32_t)k;
         return r;
     }
     const int64_t tiles = (span + SP_TILE - 1) / SP_TILE;
@@ -163,23 +247,33 @@ __device__ RowItems classify(int64_t w, int32_t lo, int32_t hi, int32_t size, in
     return r;
 }
 
+__device__ __forceinline__ RowHP row_hp(const int64_t* Wp, const int32_t* lo2,
+                                        const int32_t* hi2, int64_t i) {
+    return Wp ? RowHP{Wp[i], lo2[i], hi2[i]} : RowHP{-1, 0, 0};
+}
+
 __global__ void k_item_count(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                              const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
                              const int32_t* __restrict__ nnh, int32_t m, RowS rs, BinParams bp,
-                             int32_t* __restrict__ nitem) {
+                             const int64_t* __restrict__ Wp, const int32_t* __restrict__ lo2,
+                             const int32_t* __restrict__ hi2, int32_t* __restrict__ nitem) {
     GRID_STRIDE(i, m) {
-        nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp).count;
+        nitem[i] = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp,
+                            row_hp(Wp, lo2, hi2, i)).count;
     }
 }
 
 __global__ void k_item_emit(const int64_t* __restrict__ W, const int32_t* __restrict__ jmin,
                             const int32_t* __restrict__ jmax, const int32_t* __restrict__ size,
                             const int32_t* __restrict__ nnh, int32_t m, RowS rs, BinParams bp,
-                            const int32_t* __restrict__ row_item, Item* __restrict__ items) {
+                            const int64_t* __restrict__ Wp, const int32_t* __restrict__ lo2,
+                            const int32_t* __restrict__ hi2, const int32_t* __restrict__ row_item,
+                            Item* __restrict__ items) {
     GRID_STRIDE(i, m) {
-        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp);
+        const RowItems r = classify(W[i], jmin[i], jmax[i], size[i], nnh[i], rs.s_of((int32_t)i), bp,
+                                    row_hp(Wp, lo2, hi2, i));
         if (r.count == 0) continue;
-        const int64_t lo = jmin[i], end = (int64_t)jmax[i] + 1, span = end - lo;
+        const int64_t lo = r.lo, end = (int64_t)r.hi + 1, span = end - lo;
         Item* out = items + row_item[i];
         for (int32_t q = 0; q < r.count; ++q) {
             int64_t a, b;
@@ -253,15 +347,19 @@ __global__ void k_mode_stats(const int32_t* __restrict__ row_item, const Item* _
                              const int64_t* __restrict__ rowoff, const int64_t* __restrict__ ioff,
                              const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
                              const int32_t* __restrict__ hubidx, const int32_t* __restrict__ wbeg,
-                             const int32_t* __restrict__ wend, int32_t m,
-                             unsigned long long* __restrict__ out) {
+                             const int32_t* __restrict__ wend, const int64_t* __restrict__ Wp,
+                             int32_t m, unsigned long long* __restrict__ out) {
     GRID_STRIDE(i, m) {
         const int32_t q0 = row_item[i], q1 = row_item[i + 1];
         if (q1 == q0) continue;
         const int mode = items[q0].mode;
         unsigned long long nonhub = 0, scan_c = 0, scan_f = 0;
-        for (int32_t e = off[i]; e < off[i + 1]; ++e)
-            if (hubidx[idx[e]] < 0) nonhub += (unsigned long long)(wend[e] - wbeg[e]);
+        if (mode == MODE_HUBPAIR) {
+            nonhub = (unsigned long long)Wp[i];  // entries walked: non-hub wedges + pair hits
+        } else {
+            for (int32_t e = off[i]; e < off[i + 1]; ++e)
+                if (hubidx[idx[e]] < 0) nonhub += (unsigned long long)(wend[e] - wbeg[e]);
+        }
         if (mode == MODE_DENSE || mode == MODE_WDENSE) {
             for (int32_t q = q0; q < q1; ++q) {
                 const Item it = items[q];
@@ -281,6 +379,23 @@ __global__ void k_mode_stats(const int32_t* __restrict__ row_item, const Item* _
         atomicAdd(&o[5], scan_c);
         atomicAdd(&o[6], scan_f);
     }
+}
+
+// Wedges of the rows whose items go to the table or sparse-accumulator handlers.
+__global__ void k_sparse_wedges(const int32_t* __restrict__ row_item,
+                                const Item* __restrict__ items, const int64_t* __restrict__ W,
+                                int32_t m, unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    GRID_STRIDE(i, m) {
+        const int32_t q = row_item[i];
+        if (row_item[i + 1] == q) continue;
+        const int mode = items[q].mode;
+        if (mode == MODE_BLOCK || mode == MODE_SPARSE || mode == MODE_WSPARSE)
+            acc += (unsigned long long)W[i];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
 // rowtot[r] = sum over the k lists of rowoff[t][r] (cumulative, so the sum of
@@ -327,6 +442,14 @@ void Plan::release(cudaStream_t st) {
     dfree(icnt, st);
     dfree(ioff, st);
     dfree(rowoff, st);
+    if (idxT2s_owned) dfree(idxT2s, st);
+    idxT2s = nullptr;
+    idxT2s_owned = false;
+    dfree(ks2, st);
+    dfree(wbeg2, st);
+    dfree(wend2, st);
+    dfree(Wp, st);
+    hp = nullptr;
     s = 0;
     built = false;
     nitems = 0;
@@ -334,7 +457,8 @@ void Plan::release(cudaStream_t st) {
     pairs = wedges = 0;
 }
 
-void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st) {
+void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st,
+                const HubPairs* hp) {
     p.release(st);
     p.s = s;
     p.rs = RowS{g.srow, g.rbase, s};
@@ -386,12 +510,44 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
                                                                p.jmax, p.nnh, wtot);
         SLG_LAUNCH_CHECK();
     }
+    // hub pairs (single graphs at s >= 2): pruned pair lists and per-row work
+    int32_t *lo2 = nullptr, *hi2 = nullptr;
+    if (hp && hp->built && s >= 2 && !g.srow && m) {
+        p.hp = hp;
+        const int64_t E2 = hp->E2;
+        if (s <= g.min_size) {
+            p.idxT2s = hp->idxT2;
+            p.idxT2s_owned = false;
+            p.ks2 = nullptr;
+        } else {
+            int32_t* keep = dalloc<int32_t>(E2, st);
+            p.ks2 = dalloc<int32_t>(E2 + 1, st);
+            k_keep_flags<<<grid_for(E2, T), T, 0, st>>>(hp->idxT2, g.size, E2, p.rs, keep);
+            SLG_LAUNCH_CHECK();
+            scan_i32_to_i32(keep, p.ks2, E2, st);
+            dfree(keep, st);
+            p.idxT2s = dalloc<int32_t>(E2 + 4, st);
+            SLG_CUDA_TRY(cudaMemsetAsync(p.idxT2s, 0, sizeof(int32_t) * (E2 + 4), st));
+            p.idxT2s_owned = true;
+            k_compact<<<grid_for(E2, T), T, 0, st>>>(hp->idxT2, p.ks2, E2, p.idxT2s);
+            SLG_LAUNCH_CHECK();
+        }
+        p.wbeg2 = dalloc<int32_t>(E2, st);
+        p.wend2 = dalloc<int32_t>(E2, st);
+        p.Wp = dalloc<int64_t>(m, st);
+        lo2 = dalloc<int32_t>(m, st);
+        hi2 = dalloc<int32_t>(m, st);
+        k_pair_ranges<<<grid_for((int64_t)m * 32, T), T, 0, st>>>(
+            g.off, g.idx, g.size, p.wbeg, p.wend, p.idxTs, hp->hp_id, hp->off2, hp->idx2,
+            hp->tpos2, hp->offT2, p.ks2, p.idxT2s, m, p.rs, p.wbeg2, p.wend2, p.Wp, lo2, hi2);
+        SLG_LAUNCH_CHECK();
+    }
     // items
     int32_t* nitem = dalloc<int32_t>(m, st);
     p.row_item = dalloc<int32_t>((size_t)m + 1, st);
     if (m) {
         k_item_count<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, p.rs, bp,
-                                                   nitem);
+                                                   p.Wp, lo2, hi2, nitem);
         SLG_LAUNCH_CHECK();
     }
     {
@@ -404,6 +560,8 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
         dfree(c64, st);
         if (total > (int64_t)INT32_MAX - 1) {
             dfree(nitem, st);
+            dfree(lo2, st);
+            dfree(hi2, st);
             throw Error{SLG_ECAPACITY, "binning needs more than 2^31 work items: raise "
                                        "block_item_wedges or sparse_item_wedges"};
         }
@@ -422,9 +580,11 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
     p.items = dalloc<Item>(p.nitems, st);
     if (m) {
         k_item_emit<<<grid_for(m, T), T, 0, st>>>(p.W, p.jmin, p.jmax, g.size, p.nnh, m, p.rs, bp,
-                                                  p.row_item, p.items);
+                                                  p.Wp, lo2, hi2, p.row_item, p.items);
         SLG_LAUNCH_CHECK();
     }
+    dfree(lo2, st);
+    dfree(hi2, st);
     int32_t* flags = dalloc<int32_t>(p.nitems, st);
     for (int k = 0; k < NMODES; ++k) {
         p.mode_rank[k] = dalloc<int32_t>(p.nitems + 1, st);
@@ -503,7 +663,7 @@ void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_CO
     if (g.m) {
         k_mode_stats<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.size,
                                                          p.rowoff, p.ioff, g.off, g.idx,
-                                                         g.hubidx, p.wbeg, p.wend, g.m, d);
+                                                         g.hubidx, p.wbeg, p.wend, p.Wp, g.m, d);
         SLG_LAUNCH_CHECK();
     }
     unsigned long long h[NMODES * MS_COLS];
@@ -512,6 +672,20 @@ void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_CO
     dfree(d, st);
     for (int k = 0; k < NMODES; ++k)
         for (int c = 0; c < MS_COLS; ++c) out[k][c] = (int64_t)h[k * MS_COLS + c];
+}
+
+int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st) {
+    unsigned long long* d = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    if (g.m) {
+        k_sparse_wedges<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.m, d);
+        SLG_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    return (int64_t)h;
 }
 
 int64_t plan_max_row(const GraphDev& g, const int64_t* rowoff, cudaStream_t st) {

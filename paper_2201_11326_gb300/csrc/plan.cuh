@@ -25,6 +25,38 @@ struct GraphDev {
     uint32_t* hubmask = nullptr;   // [m]  bit b set when hub b is in e_i
 };
 
+// Hub pairs of a graph (built on demand for s >= 2, when its sparse rows carry
+// many wedges). The HP hubs are the (at most max_hubs) highest-degree vertices,
+// numbered in vertex order. For a row i with hubs H_i, its hub-pair incidences
+// are the keys a*K + b of the pairs a < b of H_i (ascending), and the
+// transpose lists, for each pair key, the rows holding both hubs in increasing
+// id. Two rows then share t >= 2 hubs exactly when each lies in t(t-1)/2 of
+// the other's pair lists.
+struct HubPairs {
+    bool built = false, tried = false;
+    int32_t K = 0;             // hubs
+    int64_t E1 = 0, E2 = 0;    // hub incidences, hub-pair incidences
+    int32_t* hp_id = nullptr;  // [n] hub number of v (vertex order), -1 if none
+    int32_t* hoff = nullptr;   // [m+1] row hub lists
+    int32_t* hlist = nullptr;  // [E1] hub numbers of each row, ascending
+    int32_t* off2 = nullptr;   // [m+1] row hub-pair incidences
+    int32_t* idx2 = nullptr;   // [E2] pair keys, ascending per row
+    int32_t* offT2 = nullptr;  // [K*K+1] pair lists
+    int32_t* idxT2 = nullptr;  // [E2] rows of each pair list, ascending
+    int32_t* tpos2 = nullptr;  // [E2] position of each hub-pair incidence in idxT2
+    // rows with more than bigk hubs also keep their hubs as a bitmap of K bits
+    int32_t bigk = 0;
+    int32_t* bigidx = nullptr;    // [m] bitmap number of the row, -1 if none
+    uint32_t* bigbits = nullptr;  // [rows with a bitmap][HP_MAXK / 32]
+    void release(cudaStream_t st);
+};
+
+// Builds hp for g with at most max_hubs hubs and at most max_pairs hub-pair
+// incidences (fewer hubs when needed); leaves hp unbuilt (tried) when no hub
+// pair exists.
+void hubpair_build(const GraphDev& g, int32_t max_hubs, int64_t max_pairs, HubPairs& hp,
+                   cudaStream_t st);
+
 // Device descriptor of one member of a batch.
 struct BatchPart {
     const int32_t* off;
@@ -99,12 +131,27 @@ struct Plan {
         bool counted = false;
     } ens;
 
+    // hub pairs for s (MODE_HUBPAIR rows; null when the plan uses none)
+    const HubPairs* hp = nullptr;
+    int32_t* ks2 = nullptr;      // [E2+1] kept-prefix over the pair lists (null: nothing pruned)
+    int32_t* idxT2s = nullptr;   // pruned pair lists (aliases hp->idxT2 when nothing is pruned)
+    bool idxT2s_owned = false;
+    int32_t* wbeg2 = nullptr;    // [E2] wedge range of each hub-pair incidence in idxT2s
+    int32_t* wend2 = nullptr;
+    int64_t* Wp = nullptr;       // [m] entries a MODE_HUBPAIR row walks (non-hub wedges +
+                                 // pair-list hits); null without hub pairs
+
     RowS rs_for(int32_t s_t) const { return RowS{rs.srow, rs.rbase, s_t}; }
     void release_ensemble(cudaStream_t st);
     void release(cudaStream_t st);
 };
 
-void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st);
+// hp: hub pairs to bin sparse rows into MODE_HUBPAIR (s >= 2), or null.
+void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cudaStream_t st,
+                const HubPairs* hp = nullptr);
+// Wedges of the rows binned as table or sparse-accumulator rows (MODE_BLOCK,
+// MODE_SPARSE, MODE_WSPARSE) in a built plan: what hub pairs could shorten.
+int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st);
 void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st);
 // Largest row total and window splits over cumulative row offsets rowoff[m+1]
 // (a single list's or the ensemble's sum).
@@ -144,6 +191,13 @@ void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS r
 constexpr int MS_COLS = 7;
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_COLS],
                      cudaStream_t st);
+// Hub-pair handler (hubpair.cu): kernel attributes, CTAs per launch, and one
+// launch over the MODE_HUBPAIR items.
+void hubpair_setup(int sms, int ctas[2]);
+void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
+                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
+                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
+                    int32_t* err, cudaStream_t st);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,

@@ -77,8 +77,10 @@ enum ItemMode : int32_t {
     MODE_WDENSE = 3, // dense slice, <= 32 non-hub ranges: one warp, j tiles of 4096
     MODE_SPARSE = 4, // sparse slice of a heavy row (|e_i| <= 255): one CTA, j tiles of
                      // 65536 8-bit counters and a list of the counters it touched
-    MODE_WSPARSE = 5,// the same for rows with |e_i| <= 32: one warp, j tiles of 4096
-    NMODES = 6
+    MODE_WSPARSE = 5,// the same for rows with |e_i| <= 32: one warp, counting in hash rounds
+    MODE_HUBPAIR = 6,// sparse row at s >= 2 whose candidates come from its non-hub wedges and
+                     // the rows sharing a pair of its hubs: one CTA, shared-memory hash table
+    NMODES = 7
 };
 
 struct Item {
@@ -147,6 +149,9 @@ constexpr int SP_TILE = 65536;            // j per tile (8-bit counters, 64 KB)
 constexpr int SP_TOUCH = 8192;            // touched counters listed per tile
 constexpr int SP_MAX_SIZE = 255;          // |e_i| bound for 8-bit counters
 constexpr int WS_MAXE = 32;               // |e_i| bound of MODE_WSPARSE (one range per lane)
+constexpr int HP_MAXK = 4096;             // hubs of the hub-pair index (MODE_HUBPAIR)
+constexpr int HP_ITEM = 2304;             // entries (non-hub wedges + pair-list hits) per item
+constexpr int HP_MAXR = 256;              // hub-pair incidences of a MODE_HUBPAIR row, at most
 
 // --------------------------------------------------------- device helpers
 

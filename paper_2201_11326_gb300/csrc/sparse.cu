@@ -317,39 +317,95 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
 
 // ========================================================= MODE_WSPARSE
 //
-// The sparse accumulator at warp granularity, for sparse rows with at most 32
-// vertices (one wedge range per lane): a warp owns an item and a private tile
-// of 4096 8-bit counters, so many tiles are in flight per SM and no CTA barrier
-// is ever taken. Per tile (which starts at the smallest next partner of any
-// range, so empty stretches of the id range cost nothing):
-//   1. ranges with a partner inside the tile load 32 entries each, four
-//      ranges per round, and count them; a counter's first increment appends
-//      it to the warp's touched list;
-//   2. survivors are read off the touched list (or the whole tile when it
-//      overflows); the counting pass adds them up, the fill marks them in a
-//      bitmap of the tile;
-//   3. fill: the bitmap is walked in id order, four partners per lane, and
-//      survivors go through a ring to 128-byte-aligned chunk stores, as in the
-//      warp dense handler;
-//   4. the touched counters are cleared.
+// Sparse rows with at most 32 vertices (one wedge range per lane) whose
+// partners are spread thinly over a wide id range: one warp per item, counting
+// in rounds into a private open-addressing hash table, so the on-chip state
+// grows with the wedges counted, not with the id span they cover (a
+// direct-addressed tile of 8-bit counters holds one id per byte; the table holds
+// one partner per 8 bytes at half load, which wins below one wedge per 8 ids).
+// A round takes every wedge with partner j in [t0, t1):
+//   1. t0 is the smallest next partner over the ranges; from each range's
+//      density (entries left per id of its remaining span) a round end t1e is
+//      chosen for about HS_TARGET wedges, and each range whose next partner
+//      lies below t1e gets a load window of its next L entries (the expected
+//      count plus a margin, at least 2; the windows together at most HS_CAP
+//      entries in HS_STEPS loads of 32, else t1e shrinks);
+//   2. the windows are loaded, eight independent 32-entry loads in flight, into
+//      a staging buffer. t1 = the smallest last entry of a window that does not
+//      reach its range's end (every entry below it is inside its window), the
+//      next partner of a range without a window, or the item's end;
+//   3. every staged entry below t1 adds 1 to its partner's count in the table
+//      (a 32-bit slot: (j - t0 + 1) << 8 | count, placed by compare-and-swap).
+//      Each range advances past its entries below t1; its next partner is the
+//      first staged entry it did not take, so a range becomes active again only
+//      when a later round's end passes that partner;
+//   4. the table is scanned: partners with count >= s are survivors; the
+//      counting pass adds them up, the fill sorts them by j (a warp bitonic
+//      sort) and writes them in order. The table is cleared as it is read.
+// Every round makes progress: a window holds at least two entries unless it
+// reaches its range's end, so its last entry exceeds t0, and a range without a
+// window has its next partner at or beyond t1e > t0; hence t1 > t0, and the
+// next round starts at or beyond t1 (every entry below t1 has been taken).
 
-constexpr int WS_WARPS = 16;
-constexpr int WS_TILE = 4096;
-constexpr int WS_WORDS = WS_TILE / 4;   // four 8-bit counters per word
-constexpr int WS_BITS = WS_TILE / 32;   // survivor bitmap words (fill)
-constexpr int WS_TOUCH = 256;           // touched counters listed per tile
-constexpr int WS_RING = 256;            // fill: survivors waiting for an aligned store
-constexpr int WS_GROUP = 4;             // ranges loaded together per round
-static_assert(WS_BITS == 4 * 32, "the bitmap walk takes four partners per lane and round");
+constexpr int HS_WARPS = 8;              // warps per CTA
+constexpr int HS_SLOTS = 1024;           // table slots per warp
+constexpr int HS_LOG = 10;
+constexpr int HS_CAP = 512;              // entries loaded per round at most (table half full)
+constexpr int HS_STEPS = 32;             // 32-entry loads per round at most
+constexpr int HS_TARGET = 384;           // wedges aimed at per round
+constexpr int32_t HS_SPAN = 1 << 23;     // ids per round at most: keys + 1 fit 24 bits
+constexpr int HS_GROUP = 8;              // loads issued together
+static_assert((1 << HS_LOG) == HS_SLOTS && 2 * HS_CAP <= HS_SLOTS, "table at most half full");
+static_assert(HS_STEPS == 32, "one step per lane in the step table");
+static_assert(HS_CAP <= HS_STEPS * 32, "survivors are sorted in the staging buffer");
 static_assert(WS_MAXE <= 32 && WS_MAXE < 256, "one range per lane; 8-bit counts");
-// fill: the ring keeps ids (32 bits) and counts (8 bits) in separate arrays
-constexpr size_t ws_warp_words(bool fill) {
-    return WS_WORDS + WS_TOUCH / 2 + (fill ? WS_BITS + WS_RING + WS_RING / 4 : 0);
+// per warp: table, staging buffer (also the fill's survivor list), step table
+constexpr size_t HS_WARP_WORDS = HS_SLOTS + HS_STEPS * 32 + 2 * HS_STEPS;
+constexpr size_t HS_SMEM = sizeof(uint32_t) * HS_WARP_WORDS * HS_WARPS;
+
+// Ascending bitonic sort of n <= HS_CAP packed survivors (key << 8 | count) in
+// shared memory by one warp; n <= 32 in registers.
+__device__ __forceinline__ void warp_sort_u32(uint32_t* a, int32_t n, int lane) {
+    if (n <= 1) return;
+    if (n <= 32) {
+        uint32_t x = lane < n ? a[lane] : 0xffffffffu;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                const bool up = (lane & k) == 0, low = (lane & j) == 0;
+                x = (low == up) ? min(x, y) : max(x, y);
+            }
+        }
+        __syncwarp();
+        if (lane < n) a[lane] = x;
+        __syncwarp();
+        return;
+    }
+    int32_t P = 64;
+    while (P < n) P <<= 1;
+    for (int32_t t = n + lane; t < P; t += 32) a[t] = 0xffffffffu;
+    __syncwarp();
+    for (int32_t k = 2; k <= P; k <<= 1) {
+        for (int32_t j = k >> 1; j > 0; j >>= 1) {
+            for (int32_t t = lane; t < P; t += 32) {
+                const int32_t u = t ^ j;
+                if (u > t) {
+                    const uint32_t x = a[t], y = a[u];
+                    if ((x > y) == ((t & k) == 0)) {
+                        a[t] = y;
+                        a[u] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
 }
-constexpr size_t ws_smem(bool fill) { return sizeof(uint32_t) * ws_warp_words(fill) * WS_WARPS; }
 
 template <bool FILL>
-__global__ void __launch_bounds__(WS_WARPS * 32, FILL ? 2 : 3)
+__global__ void __launch_bounds__(HS_WARPS * 32)
 k_wsparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
                 const int32_t* __restrict__ off, const int32_t* __restrict__ wbeg,
@@ -359,22 +415,19 @@ k_wsparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
     extern __shared__ __align__(16) uint32_t dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* ctr = dyn + (size_t)warp * ws_warp_words(FILL);           // WS_WORDS
-    uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + WS_WORDS);    // WS_TOUCH
-    uint32_t* bm = reinterpret_cast<uint32_t*>(touched + WS_TOUCH);     // fill: WS_BITS
-    int32_t* ring_j = reinterpret_cast<int32_t*>(bm + WS_BITS);          // fill: WS_RING
-    uint8_t* ring_o = reinterpret_cast<uint8_t*>(ring_j + WS_RING);      // fill: WS_RING
-    const unsigned lt = (1u << lane) - 1u;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    uint32_t* tab = dyn + (size_t)warp * HS_WARP_WORDS;                    // HS_SLOTS
+    int32_t* stage = reinterpret_cast<int32_t*>(tab + HS_SLOTS);           // HS_STEPS * 32
+    int32_t* st_p0 = stage + HS_STEPS * 32;                                // HS_STEPS
+    int32_t* st_meta = st_p0 + HS_STEPS;                                   // HS_STEPS
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
-    for (int32_t w = lane; w < WS_WORDS; w += 32) ctr[w] = 0;
-    if (FILL)
-        for (int32_t w = lane; w < WS_BITS; w += 32) bm[w] = 0;
+    for (int32_t w = lane; w < HS_SLOTS; w += 32) tab[w] = 0u;
     __syncwarp();
 
     for (;;) {
         int32_t pos = 0;
         if (lane == 0) pos = lo + atomicAdd(queue, 1);
-        pos = __shfl_sync(0xffffffffu, pos, 0);
+        pos = __shfl_sync(FULL, pos, 0);
         if (pos >= hi) break;
         const int32_t q = list[pos];
         if (FILL && ioff[q + 1] == ioff[q]) continue;  // nothing to write
@@ -385,189 +438,176 @@ k_wsparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list
         const int32_t e0 = off[i];
         const int32_t ne = off[i + 1] - e0;
         if (ne > 32 && lane == 0) atomicOr(err, ERR_TABLE);  // binning admits |e_i| <= 32
-        // lane k holds the wedge range of the row's k-th vertex, cursor at jlo
-        int32_t cur = 0, end = 0, nxt = INT32_MAX;
+        // lane k: the wedge range of the row's k-th vertex, cursor at jlo
+        int32_t cur = 0, end = 0, nxt = INT32_MAX, last = 0;
         if (lane < ne) {
             const int32_t e = e0 + lane;
             const int32_t b0 = wbeg[e], t = wend[e];
             if (t > b0) {
-                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo)
-                                      ? b0 : lower_bound_dev(idxTs, b0, t, it.jlo);
+                const int32_t c = (__ldg(&idxTs[b0]) >= it.jlo) ? b0
+                                                                : lower_bound_dev(idxTs, b0, t, it.jlo);
                 if (c < t) {
                     cur = c;
                     end = t;
                     nxt = __ldg(&idxTs[c]);
+                    last = __ldg(&idxTs[t - 1]);
                 }
             }
         }
         int64_t wpos = FILL ? ioff[q] - ioff[item_lo] : 0;  // next output position
-        int32_t rhead = 0, rcount = 0;
-        int32_t need = FILL ? 32 - (int32_t)((reinterpret_cast<uintptr_t>(I + wpos) >> 2) & 31) : 32;
         int32_t my_count = 0;
         for (;;) {
-            const int32_t t0 = __reduce_min_sync(0xffffffffu, nxt);  // next partner of any range
+            const int32_t t0 = __reduce_min_sync(FULL, nxt);
             if (t0 >= it.jhi) break;
-            const int32_t t1 = min(t0 + WS_TILE, it.jhi);
-            const int32_t span = t1 - t0;
-            // 1. wedges of the tile
-            unsigned act = __ballot_sync(0xffffffffu, nxt < t1);
-            int32_t nt = 0;  // counters touched (same in every lane)
-            while (act) {
-                int32_t kk[WS_GROUP], vv[WS_GROUP];
-                unsigned aa = act;
+            // 1. the round's end and each range's load window. A range with n
+            // entries left spread over the ids [nxt, last] is expected to hold
+            // min(n, (t0 + span - nxt) * n / (last - nxt + 1)) entries below t0 +
+            // span; the span is set so that the ranges together expect about
+            // HS_TARGET (a few multiplicative corrections of a first estimate)
+            const bool live = nxt < it.jhi;
+            const float left = (float)(end - cur);
+            const float dens = live ? left / ((float)last - (float)nxt + 1.f) : 0.f;
+            const float a = live ? (float)nxt - (float)t0 : 0.f;
+            float span = warp_sum_f(dens);
+            span = span > 0.f ? (float)HS_TARGET / span : (float)HS_SPAN;
 #pragma unroll
-                for (int g = 0; g < WS_GROUP; ++g) {
-                    int32_t k = -1;
-                    if (aa) {
-                        k = __ffs(aa) - 1;
-                        aa &= aa - 1u;
-                    }
-                    kk[g] = k;
-                    const int32_t c = __shfl_sync(0xffffffffu, cur, k & 31);
-                    const int32_t e = __shfl_sync(0xffffffffu, end, k & 31);
-                    const int32_t p = c + lane;
-                    vv[g] = (k >= 0 && p < e) ? __ldg(&idxTs[p]) : INT32_MAX;
+            for (int k = 0; k < 4; ++k) {
+                span = fminf(fmaxf(span, 2.f), (float)HS_SPAN);
+                const float f = warp_sum_f(live ? fminf(fmaxf((span - a) * dens, 0.f), left) : 0.f);
+                span *= f > 0.f ? fminf(fmaxf((float)HS_TARGET / f, 0.0625f), 64.f) : 64.f;
+            }
+            int64_t ispan = (int64_t)fminf(fmaxf(span, 2.f), (float)HS_SPAN);
+            int32_t L = 0, nst = 0, t1e = t0;
+            for (int guard = 0; guard < 32; ++guard) {
+                t1e = (int32_t)min((int64_t)t0 + ispan, (int64_t)it.jhi);
+                L = 0;
+                if (nxt < t1e) {
+                    const float want = ((float)t1e - (float)nxt) * dens * 1.25f + 2.f;
+                    L = want >= left ? end - cur : (int32_t)ceilf(want);
                 }
+                nst = (L + 31) >> 5;
+                const int32_t tl = (int32_t)__reduce_add_sync(FULL, (unsigned)L);
+                const int32_t ts = (int32_t)__reduce_add_sync(FULL, (unsigned)nst);
+                // at span 1 a window holds at most 4 entries: always within bounds
+                if ((tl <= HS_CAP && ts <= HS_STEPS) || ispan <= 1) break;
+                ispan >>= 1;
+            }
+            // step table: lane x of the warp then holds load step x
+            int32_t sb = nst;
 #pragma unroll
-                for (int g = 0; g < WS_GROUP; ++g) {
-                    const int32_t k = kk[g];
-                    if (k < 0) break;
-                    const bool valid = vv[g] < t1;
-                    bool first = false;
-                    int32_t slot = 0;
-                    if (valid) {
-                        slot = vv[g] - t0;
-                        const int sh = (slot & 3) << 3;
-                        const uint32_t old = atomicAdd(&ctr[slot >> 2], 1u << sh);
-                        first = ((old >> sh) & 0xffu) == 0;
-                    }
-                    const unsigned fb = __ballot_sync(0xffffffffu, first);
-                    if (fb) {
-                        const int32_t at = nt + __popc(fb & lt);
-                        if (first && at < WS_TOUCH) touched[at] = (uint16_t)slot;
-                        nt += __popc(fb);
-                    }
-                    const int n = __popc(__ballot_sync(0xffffffffu, valid));
-                    // the first entry not taken is the range's next partner
-                    const int32_t nx = __shfl_sync(0xffffffffu, vv[g], n & 31);
-                    if (lane == k) {
-                        cur += n;
-                        if (n < 32) nxt = nx;
-                    }
-                    if (n < 32) act &= ~(1u << k);
-                }
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(FULL, sb, d);
+                if (lane >= d) sb += y;
+            }
+            const int32_t nsteps = __shfl_sync(FULL, sb, 31);
+            sb -= nst;
+            for (int32_t x = 0; x < nst; ++x) {
+                const int32_t cnt = min(32, L - 32 * x);
+                // the last load of a window that stops short of its range's end
+                // bounds the round
+                const int32_t bound = (x == nst - 1 && cur + L < end) ? (1 << 16) : 0;
+                st_p0[sb + x] = cur + 32 * x;
+                st_meta[sb + x] = cnt | (lane << 8) | bound;
             }
             __syncwarp();
-            const bool listed = nt <= WS_TOUCH;
-            const int32_t nwords = (span + 3) >> 2;
-            // 2. survivors
-            if (listed) {
-                for (int32_t x = lane; x < nt; x += 32) {
-                    const int32_t slot = touched[x];
-                    const int32_t c = (int32_t)((ctr[slot >> 2] >> ((slot & 3) << 3)) & 0xffu);
-                    if (c >= s) {
-                        if (FILL)
-                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                        else
-                            ++my_count;
-                    }
-                }
-            } else {
-                for (int32_t w = lane; w < nwords; w += 32) {
-                    const uint32_t v = ctr[w];
-                    if (!v) continue;
+            const int32_t my_p0 = lane < nsteps ? st_p0[lane] : 0;
+            const int32_t my_meta = lane < nsteps ? st_meta[lane] : 0;
+            // 2. loads, HS_GROUP in flight, into the staging buffer
+            int32_t cand = (L == 0) ? nxt : INT32_MAX;  // a range without a window
+            for (int32_t g0 = 0; g0 < nsteps; g0 += HS_GROUP) {
+                int32_t v[HS_GROUP];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int32_t slot = 4 * w + r;
-                        if (slot < span && (int32_t)((v >> (8 * r)) & 0xffu) >= s) {
-                            if (FILL)
-                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                            else
-                                ++my_count;
-                        }
-                    }
+                for (int b = 0; b < HS_GROUP; ++b) {
+                    const int32_t p0 = __shfl_sync(FULL, my_p0, (g0 + b) & 31);
+                    const int32_t meta = __shfl_sync(FULL, my_meta, (g0 + b) & 31);
+                    const int32_t cnt = (g0 + b < nsteps) ? (meta & 0xff) : 0;
+                    v[b] = lane < cnt ? __ldg(&idxTs[p0 + lane]) : INT32_MAX;
                 }
+#pragma unroll
+                for (int b = 0; b < HS_GROUP; ++b) {
+                    if (g0 + b >= nsteps) break;
+                    const int32_t meta = __shfl_sync(FULL, my_meta, (g0 + b) & 31);
+                    stage[(g0 + b) * 32 + lane] = v[b];
+                    if ((meta >> 16) && lane == (meta & 0xff) - 1) cand = min(cand, v[b]);
+                }
+            }
+            int32_t t1 = __reduce_min_sync(FULL, cand);
+            t1 = (int32_t)min((int64_t)t1, min((int64_t)it.jhi, (int64_t)t0 + HS_SPAN));
+            __syncwarp();
+            // 3. count the staged entries below t1
+            int32_t adv = 0;
+            for (int32_t st = 0; st < nsteps; ++st) {
+                const int32_t v = stage[st * 32 + lane];
+                const int32_t meta = __shfl_sync(FULL, my_meta, st & 31);
+                const bool valid = v < t1;
+                if (valid) {
+                    const uint32_t key = (uint32_t)(v - t0) + 1u;
+                    uint32_t h = (key * 2654435761u) >> (32 - HS_LOG);
+                    const uint32_t want = (key << 8) | 1u;
+                    int probe = 0;
+                    for (; probe < HS_SLOTS; ++probe) {
+                        const uint32_t old = atomicCAS(&tab[h], 0u, want);
+                        if (old == 0u) break;
+                        if ((old >> 8) == key) {
+                            atomicAdd(&tab[h], 1u);
+                            break;
+                        }
+                        h = (h + 1) & (HS_SLOTS - 1);
+                    }
+                    if (probe == HS_SLOTS) atomicOr(err, ERR_TABLE);
+                }
+                const int n = __popc(__ballot_sync(FULL, valid));
+                if (lane == ((meta >> 8) & 31)) adv += n;
+            }
+            if (L > 0) {
+                // the first entry not taken is the range's next partner: it sits in
+                // the staging buffer at window offset adv (a window that reaches
+                // its range's end is taken whole)
+                cur += adv;
+                nxt = cur >= end ? INT32_MAX : stage[sb * 32 + adv];
             }
             __syncwarp();
-            if (FILL) {
-                // 3. survivors in id order: round r covers partners 128r .. 128r+127,
-                // lane l the four partners 128r + 4l .. 128r + 4l + 3 (one counter word);
-                // only rounds whose four bitmap words hold a survivor are visited
-                const uint32_t b4 = bm[4 * lane] | bm[4 * lane + 1] | bm[4 * lane + 2] | bm[4 * lane + 3];
-                for (unsigned rounds = __ballot_sync(0xffffffffu, b4 != 0); rounds;
-                     rounds &= rounds - 1u) {
-                    const int32_t r = __ffs(rounds) - 1;
-                    const uint32_t nib = (bm[4 * r + (lane >> 3)] >> ((lane & 7) * 4)) & 0xfu;
-                    const uint32_t cw = nib ? ctr[32 * r + lane] : 0u;
-                    const int32_t mine = __popc(nib);
-                    int32_t inc = mine;
+            // 4. survivors; the table is cleared as it is read
+            int32_t ns = 0;  // fill: survivors staged so far (same in every lane)
 #pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-                        if (lane >= d) inc += y;
-                    }
-                    const int32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-                    int32_t slot = rhead + rcount + inc - mine;
+            for (int r = 0; r < HS_SLOTS / 128; ++r) {
+                uint4* t4 = reinterpret_cast<uint4*>(tab) + r * 32 + lane;
+                const uint4 w4 = *t4;
+                const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+                if (w4.x | w4.y | w4.z | w4.w) *t4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        if ((nib >> b) & 1u) {
-                            ring_j[slot & (WS_RING - 1)] = t0 + 128 * r + 4 * lane + b;
-                            ring_o[slot & (WS_RING - 1)] = (uint8_t)((cw >> (8 * b)) & 0xffu);
-                            ++slot;
-                        }
+                for (int c = 0; c < 4; ++c) {
+                    const bool sv = w[c] != 0u && (int32_t)(w[c] & 0xffu) >= s;
+                    if (!FILL) {
+                        my_count += sv ? 1 : 0;
+                    } else {
+                        const unsigned bal = __ballot_sync(FULL, sv);
+                        if (sv) stage[ns + __popc(bal & lt)] = (int32_t)(w[c] - 0x100u);
+                        ns += __popc(bal);
                     }
-                    rcount += tot;
-                    __syncwarp();
-                    while (rcount >= need) {
-                        if (lane < need) {
-                            const int32_t x = (rhead + lane) & (WS_RING - 1);
-                            const int64_t p2 = wpos + lane;
-                            if (p2 < limit) {
-                                I[p2] = i - ib;
-                                J[p2] = ring_j[x] - ib;
-                                O[p2] = ring_o[x];
-                            } else {
-                                atomicOr(err, ERR_BOUNDS);
-                            }
-                        }
-                        rhead = (rhead + need) & (WS_RING - 1);
-                        rcount -= need;
-                        wpos += need;
-                        need = 32;
-                    }
-                    __syncwarp();
-                }
-                if (b4) {  // clear this lane's four words
-                    bm[4 * lane] = 0;
-                    bm[4 * lane + 1] = 0;
-                    bm[4 * lane + 2] = 0;
-                    bm[4 * lane + 3] = 0;
                 }
             }
-            // 4. clear what the tile used (every read above is done)
-            if (listed) {
-                for (int32_t x = lane; x < nt; x += 32) ctr[touched[x] >> 2] = 0;
-            } else {
-                for (int32_t w = lane; w < nwords; w += 32) ctr[w] = 0;
-            }
-            __syncwarp();
-        }
-        if (FILL && rcount > 0) {  // the item's last, partial chunk
-            if (lane < rcount) {
-                const int32_t x = (rhead + lane) & (WS_RING - 1);
-                const int64_t p2 = wpos + lane;
-                if (p2 < limit) {
-                    I[p2] = i - ib;
-                    J[p2] = ring_j[x] - ib;
-                    O[p2] = ring_o[x];
-                } else {
-                    atomicOr(err, ERR_BOUNDS);
+            if (FILL && ns > 0) {
+                __syncwarp();
+                uint32_t* sv = reinterpret_cast<uint32_t*>(stage);
+                warp_sort_u32(sv, ns, lane);
+                for (int32_t x = lane; x < ns; x += 32) {
+                    const uint32_t w = sv[x];
+                    const int64_t p2 = wpos + x;
+                    if (p2 < limit) {
+                        I[p2] = i - ib;
+                        J[p2] = t0 + (int32_t)(w >> 8) - ib;
+                        O[p2] = (int32_t)(w & 0xffu);
+                    } else {
+                        atomicOr(err, ERR_BOUNDS);
+                    }
                 }
+                wpos += ns;
             }
             __syncwarp();
         }
         if (!FILL) {
-            const int32_t total = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)my_count);
+            const int32_t total = (int32_t)__reduce_add_sync(FULL, (unsigned)my_count);
             if (lane == 0) icnt[q] = total;
         }
     }
@@ -589,12 +629,11 @@ void sparse_setup(int sms, int ctas[2]) {
 
 void wsparse_setup(int sms, int ctas[2]) {
     for (int f = 0; f < 2; ++f) {
-        const size_t smem = ws_smem(f == 1);
         auto kern = f ? k_wsparse_items<true> : k_wsparse_items<false>;
         SLG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+                                          (int)HS_SMEM));
         int d = 0;
-        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, WS_WARPS * 32, smem));
+        SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, HS_WARPS * 32, HS_SMEM));
         ctas[f] = sms * (d > 0 ? d : 1);
     }
 }
@@ -604,11 +643,11 @@ void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
                     int32_t* err, cudaStream_t st) {
     if (fill)
-        k_wsparse_items<true><<<ctas, WS_WARPS * 32, ws_smem(true), st>>>(
+        k_wsparse_items<true><<<ctas, HS_WARPS * 32, HS_SMEM, st>>>(
             p.items, p.mode_list[MODE_WSPARSE], p.mode_rank[MODE_WSPARSE], item_lo, item_hi,
             g.off, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
     else
-        k_wsparse_items<false><<<ctas, WS_WARPS * 32, ws_smem(false), st>>>(
+        k_wsparse_items<false><<<ctas, HS_WARPS * 32, HS_SMEM, st>>>(
             p.items, p.mode_list[MODE_WSPARSE], p.mode_rank[MODE_WSPARSE], item_lo, item_hi,
             g.off, p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
     SLG_LAUNCH_CHECK();

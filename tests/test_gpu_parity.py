@@ -494,3 +494,83 @@ def test_slg_batch_windows_smaller_than_the_list():
             assert np.all(I[a:b] == i) and np.array_equal(J[a:b], wj) and np.array_equal(O[a:b], wo)
     finally:
         g.free()
+
+
+# ---------------------------------------------------------------- hub pairs
+
+HUBPAIR_GRAPHS = {
+    "large20000": lambda: synth.large(m=20000),
+    "med6000": lambda: synth.medium(seed=2, m=6000),
+    "tiny": lambda: synth.tiny(),
+    "striped": lambda: synth.striped_hub(3, 70001, 3000, 40),
+    "overflow": _overflow_graph,
+}
+
+
+def hubpair_rows(g, s):
+    return slg.slg_mode_stats(g, s)[slg.MODE_NAMES.index("hubpair")][0]
+
+
+@pytest.mark.parametrize("max_hubs", [2, 16, 256, 4096])
+@pytest.mark.parametrize("key", sorted(HUBPAIR_GRAPHS))
+def test_hub_pairs_match_oracle(key, max_hubs):
+    # partners from non-hub wedges and hub-pair lists (overlap = non-hub count +
+    # the hubs recovered from the pair count, or the one-hub check), with and
+    # without the table and dense handlers beside them
+    h = HUBPAIR_GRAPHS[key]()
+    used = 0
+    for bins in (None, FORCED["block_only"]):
+        g = slg.slg_load(h.off, h.idx, h.m, h.n)
+        try:
+            if bins is not None:
+                slg.slg_set_bins(g, *bins)
+            slg.slg_set_hub_pairs(g, max_hubs, 0)
+            for s in (2, 3, 5):
+                got = slg.slg_build(g, s)
+                used += hubpair_rows(g, s)
+                assert_same(got, oracle_list(key, h, s), f"{key} hubs<={max_hubs} s={s}")
+            # s = 1 never uses hub pairs (a single shared hub is an overlap)
+            assert hubpair_rows(g, 1) == 0
+        finally:
+            g.free()
+    if key in ("large20000", "med6000") and max_hubs >= 16:
+        assert used > 0
+
+
+def test_hub_pairs_in_an_ensemble_and_windows():
+    h = synth.large(m=20000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        slg.slg_set_bins(g, *FORCED["block_only"])
+        slg.slg_set_hub_pairs(g, 512, 0)
+        s_list = [2, 4, 8, 16]
+        lists = slg.slg_ensemble_build(g, s_list)
+        for s, got in zip(s_list, lists):
+            assert_same(got, oracle_list("large20000", h, s), f"ensemble s={s}")
+        # windows with per-row digests through the hub-pair handler
+        counts, digs, _ = oracle.rows(h.off, h.idx, None, [3])
+        cap = max(int(counts.max()), int(counts.sum()) // 5 + 1)
+        I, J, O = (np.zeros(cap, np.int32) for _ in range(3))
+        splits = slg.slg_plan_windows(g, 3, cap)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            rd = np.zeros(r1 - r0, np.uint64)
+            slg.slg_build_window(g, 3, int(r0), int(r1), I, J, O, digest=True, row_digests=rd)
+            assert np.array_equal(rd, digs[r0:r1, 0])
+        assert hubpair_rows(g, 3) > 0
+    finally:
+        g.free()
+
+
+def test_hub_pairs_disabled_and_default_threshold():
+    h = synth.large(m=20000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        # the default threshold (2^33 sparse wedges) is far above this graph's
+        assert hubpair_rows(g, 2) == 0
+        slg.slg_set_hub_pairs(g, 0, 0)  # disabled
+        assert hubpair_rows(g, 2) == 0
+        assert_same(slg.slg_build(g, 2), oracle_list("large20000", h, 2), "disabled")
+        with pytest.raises(slg.SlgError):
+            slg.slg_set_hub_pairs(g, 5000, 0)
+    finally:
+        g.free()
