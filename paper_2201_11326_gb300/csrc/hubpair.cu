@@ -321,7 +321,9 @@ constexpr int HP_TABLE = 6144;           // slots (key + packed counts): 48 KB, 
 constexpr int HP_CAP = HP_TABLE / 2;     // distinct partners before a slice splits
 constexpr int HP_WORDS = HP_MAXK / 32;   // hub bitmap of the row
 constexpr int HP_SLOTS_PER_THREAD = HP_TABLE / HP_THREADS;
-constexpr int HP_RANGES = SP_MAX_SIZE + HP_MAXR;  // non-hub and hub-pair ranges of a row
+constexpr int HP_RANGES = (SP_MAX_SIZE + HP_MAXR + 31) & ~31;  // ranges of a row, at most
+// per-CTA scratch in device memory: range cursors, and the fill's survivors
+constexpr int HP_SCRATCH_WORDS = 2 * HP_RANGES + 2 * HP_CAP;
 constexpr uint32_t HP_LIGHT = 0x10000u;  // a non-hub wedge (high half); a pair-list hit adds 1
 constexpr int32_t HP_EMPTY = -1;
 constexpr int HP_BUCKETS = 1024;         // fill: survivors are bucketed by j before sorting
@@ -404,16 +406,18 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 const int32_t* __restrict__ wend2, const int32_t* __restrict__ idxT2s, RowS rs,
                 int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
                 int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
-                int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+                int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err,
+                int32_t* __restrict__ scratch) {
     constexpr int NT = HP_THREADS;
+    int32_t* cur = scratch + (int64_t)blockIdx.x * HP_SCRATCH_WORDS;  // first entry of the next slice
+    int32_t* nxt = cur + HP_RANGES;                                   // first entry after this slice
+    unsigned long long* surv = reinterpret_cast<unsigned long long*>(nxt + HP_RANGES);  // fill
     extern __shared__ __align__(16) int32_t hp_dyn[];
     int32_t* keys = hp_dyn;                                              // HP_TABLE
     uint32_t* cnts = reinterpret_cast<uint32_t*>(hp_dyn + HP_TABLE);     // HP_TABLE
     unsigned long long* sortbuf = reinterpret_cast<unsigned long long*>(hp_dyn);  // fill
     __shared__ uint32_t hbits[HP_WORDS];
     __shared__ int32_t hmine[SP_MAX_SIZE + 1];  // the row's hubs (|e_i| <= 255)
-    __shared__ int32_t cur[HP_RANGES];          // per range: first entry of the next slice
-    __shared__ int32_t nxt[HP_RANGES];          // per range: first entry after this slice
     __shared__ int32_t pre[NT + 1];
     __shared__ int32_t sub[NT];
     __shared__ int32_t stk_a[64], stk_b[64];
@@ -658,41 +662,47 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                     cnts[slot] = ov >= s ? (uint32_t)ov : 0u;
                 }
                 __syncthreads();
-                int32_t kk[HP_SLOTS_PER_THREAD], oo[HP_SLOTS_PER_THREAD];
                 int32_t mine = 0;
 #pragma unroll
                 for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r) {
                     const int slot = r * NT + tid;
-                    kk[r] = keys[slot];
-                    oo[r] = (int32_t)cnts[slot];
-                    mine += oo[r] > 0 ? 1 : 0;
+                    mine += cnts[slot] > 0u ? 1 : 0;
+                    if (!FILL && keys[slot] != HP_EMPTY) {  // the counting pass clears as it reads
+                        keys[slot] = HP_EMPTY;
+                        cnts[slot] = 0u;
+                    }
                 }
                 int32_t c;
                 const int32_t ex = block_excl_scan<NT>(mine, &c, tmp);
                 if (!FILL) {
-                    // the table is read: clear the slots this thread read
-#pragma unroll
-                    for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r)
-                        if (kk[r] != HP_EMPTY) {
-                            const int slot = r * NT + tid;
-                            keys[slot] = HP_EMPTY;
-                            cnts[slot] = 0u;
-                        }
                     clean = true;
                 } else if (c > 0) {
-                    // the table has been read into registers: reuse it as the sort
-                    // buffer. Survivors go to HP_BUCKETS buckets by j (counted,
-                    // scanned, placed), each thread sorts its buckets by insertion;
-                    // a crowded bucket sends the whole list to a bitonic sort
+                    // survivors to the CTA's scratch list, then back into the table's
+                    // memory in order of j: counted into HP_BUCKETS buckets by j,
+                    // placed, and each thread sorts its buckets by insertion (a
+                    // crowded bucket sends the whole list to a bitonic sort)
+                    int32_t p = ex;
+#pragma unroll
+                    for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r) {
+                        const int slot = r * NT + tid;
+                        const uint32_t ov = cnts[slot];
+                        if (ov > 0u)
+                            surv[p++] = ((unsigned long long)(uint32_t)keys[slot] << 32) | ov;
+                    }
                     int32_t* hist = reinterpret_cast<int32_t*>(chk);  // HP_BUCKETS + 1
                     const int64_t a = sh_a, span = (int64_t)b - a;
                     for (int32_t t = tid; t <= HP_BUCKETS; t += NT) hist[t] = 0;
                     __syncthreads();
-                    int32_t bp[HP_SLOTS_PER_THREAD];
+                    constexpr int SPT = HP_CAP / NT;  // survivors per thread, at most
+                    int32_t bp[SPT];
 #pragma unroll
-                    for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r)
-                        if (oo[r] > 0)
-                            bp[r] = atomicAdd(&hist[(int32_t)(((int64_t)kk[r] - a) * HP_BUCKETS / span)], 1);
+                    for (int u = 0; u < SPT; ++u) {
+                        const int32_t t = u * NT + tid;
+                        if (t < c) {
+                            const int32_t j = (int32_t)(surv[t] >> 32);
+                            bp[u] = atomicAdd(&hist[(int32_t)(((int64_t)j - a) * HP_BUCKETS / span)], 1);
+                        }
+                    }
                     __syncthreads();
                     constexpr int BPT = HP_BUCKETS / NT;  // buckets per thread
                     int32_t hs[BPT], tot = 0;
@@ -703,7 +713,7 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                     }
                     int32_t all;
                     int32_t run = block_excl_scan<NT>(tot, &all, tmp);
-                    int32_t my0 = run;
+                    const int32_t my0 = run;
 #pragma unroll
                     for (int u = 0; u < BPT; ++u) {
                         hist[tid * BPT + u] = run;
@@ -711,12 +721,14 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                     }
                     __syncthreads();
 #pragma unroll
-                    for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r)
-                        if (oo[r] > 0) {
-                            const int32_t bk = (int32_t)(((int64_t)kk[r] - a) * HP_BUCKETS / span);
-                            sortbuf[hist[bk] + bp[r]] =
-                                ((unsigned long long)(uint32_t)kk[r] << 32) | (uint32_t)oo[r];
+                    for (int u = 0; u < SPT; ++u) {
+                        const int32_t t = u * NT + tid;
+                        if (t < c) {
+                            const unsigned long long v = surv[t];
+                            const int32_t j = (int32_t)(v >> 32);
+                            sortbuf[hist[(int32_t)(((int64_t)j - a) * HP_BUCKETS / span)] + bp[u]] = v;
                         }
+                    }
                     __syncthreads();
                     bool crowded = false;
                     {
@@ -772,15 +784,6 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                         }
                     }
                     clean = false;
-                } else {
-                    // no survivor: clear what this thread read
-#pragma unroll
-                    for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r)
-                        if (kk[r] != HP_EMPTY) {
-                            const int slot = r * NT + tid;
-                            keys[slot] = HP_EMPTY;
-                            cnts[slot] = 0u;
-                        }
                 }
                 out_pos += c;
             }
@@ -808,19 +811,21 @@ void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
                     int32_t* err, cudaStream_t st) {
     const HubPairs& hp = *p.hp;
+    int32_t* scratch = dalloc<int32_t>((size_t)ctas * HP_SCRATCH_WORDS, st);
     if (fill)
         k_hubpair_items<true><<<ctas, HP_THREADS, HP_SMEM, st>>>(
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
             hp.bigbits, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err);
+            limit, err, scratch);
     else
         k_hubpair_items<false><<<ctas, HP_THREADS, HP_SMEM, st>>>(
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
             hp.bigbits, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err);
+            limit, err, scratch);
     SLG_LAUNCH_CHECK();
+    dfree(scratch, st);
 }
 
 }  // namespace slg
