@@ -6,9 +6,11 @@ n = 500,000 vertices, log-normal(1.8, 1.0) sizes clipped to [2, 5000],
 Zipf(1.7) vertex popularity, seed 0) with the sweep s = 1..8.
 
 One step = the whole hot path on that input, resident in HBM:
-  slg_load from device memory (validate, transpose), then for every s:
-  counting pass (prune, per-row work, binning, count, scan), window plan and
-  the fill of every window of at most 2^33 pairs into a reused device window.
+  slg_load from device memory (validate, transpose), then the sweep as one
+  ensemble (Algorithm 3: one plan and one counting pass for every s), then for
+  every s its window plan and the fill of every window of at most 2^33 pairs
+  into a reused device window. `--sweep per_s` runs each s on its own instead
+  (plan, counting pass, windows).
 Metric: wedges per second, W = sum_s W_s with W_s = sum_v C(d_s(v), 2);
 s-edges per second (sum_s |L_s| / time) is reported beside it.
 
@@ -57,6 +59,10 @@ def parse_args():
     ap.add_argument("--workload", choices=["medium", "large", "batch", "serve", "ensemble"],
                     default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
+    ap.add_argument("--sweep", choices=["ensemble", "per_s"], default=None,
+                    help="medium: the s sweep as one ensemble (default) or one s at a time; "
+                         "large: one s at a time (default)")
+    ap.add_argument("--queries", type=int, default=1000, help="serve workload: queries per rate")
     return ap.parse_args()
 
 
@@ -188,6 +194,37 @@ def run_sweep(slg, g, s_list, bufs, stream, per_s, mode_work=None):
         d["ms"].append(e0.elapsed_time(e1))
 
 
+def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None):
+    """The s sweep as one ensemble (Algorithm 3): one plan for min(s) and one
+    counting pass for every list, then each list's windows. Per s: its fill time,
+    with the shared counting pass recorded once."""
+    import torch
+    I, J, O = bufs
+    cap = I.numel()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(s_list) + 2)]
+    ev[0].record(stream)
+    pairs, _ = slg.slg_ensemble_count(g, s_list)
+    ev[1].record(stream)
+    if mode_work is not None:
+        for t, s in enumerate(s_list):
+            mode_work[s] = slg.slg_ensemble_mode_stats(g, s_list, t)
+    for t, s in enumerate(s_list):
+        splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap, which=t)
+        ev[t + 2].record(stream)
+    ev[-1].synchronize()
+    count_ms = ev[0].elapsed_time(ev[1])
+    for t, s in enumerate(s_list):
+        d = per_s.setdefault(s, {"s": s, "wedges": wedges[s], "pairs": pairs[t], "ms": [],
+                                 "fill_ms": [], "count_ms_shared": []})
+        fill = ev[t + 1].elapsed_time(ev[t + 2])
+        d["fill_ms"].append(fill)
+        d["count_ms_shared"].append(count_ms)
+        # the shared counting pass is charged to the lists in equal parts
+        d["ms"].append(fill + count_ms / len(s_list))
+
+
 def bench_ours(args):
     import torch
     import paper_2201_11326_gb300 as slg
@@ -202,10 +239,19 @@ def bench_ours(args):
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
     h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
+    sweep = args.sweep or ("per_s" if args.workload == "large" else "ensemble")
     # inputs resident in HBM before the timed region
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)
     stream = torch.cuda.Stream(dev)
+    wedges = {}
+    if sweep == "ensemble":
+        # W_s of every s (the metric's work), outside the timed region
+        with torch.cuda.stream(stream):
+            g0 = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
+            for s in s_list:
+                wedges[s] = slg.slg_count(g0, s)[1]
+            g0.free()
     I = torch.empty(args.window, dtype=torch.int32, device=dev)
     J = torch.empty_like(I)
     O = torch.empty_like(I)
@@ -217,7 +263,10 @@ def bench_ours(args):
             g = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
             if timing:
                 slg.slg_set_timing(g, True)
-            run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
+            if sweep == "ensemble":
+                run_sweep_ensemble(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work)
+            else:
+                run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
             g.free()
         return ks
@@ -287,14 +336,19 @@ def bench_ours(args):
     # candidates: (pass, mode, kernel bytes per step, ms per step, launches per step,
     # section 8(d) model bytes per step)
     cands = []
+    shared = 1.0 / len(s_list) if sweep == "ensemble" else 1.0
     for k in range(NM):
         model_c = 4 * w_mode[k] + 8 * inc_mode[k]
         if names[k] in ("dense", "wdense"):
             # what these kernels move: adj_s entries of non-hub wedges only, one
             # 4-byte hub mask per candidate partner scanned, the row's wedge-range
-            # bounds; hub wedges are popcounts and read nothing
-            kern_c = 4 * nonhub_mode[k] + 4 * scan_c_mode[k] + 8 * inc_mode[k]
+            # bounds; hub wedges are popcounts and read nothing. In an ensemble
+            # their counting pass is one launch for every list.
+            kern_c = shared * (4 * nonhub_mode[k] + 4 * scan_c_mode[k] + 8 * inc_mode[k])
             kern_f = 4 * nonhub_mode[k] + 4 * scan_f_mode[k] + 8 * inc_mode[k]
+        elif names[k] == "hubpair":
+            # entries walked (non-hub wedges + hub-pair list hits) and their bounds
+            kern_c = kern_f = 4 * nonhub_mode[k] + 8 * inc_mode[k]
         else:
             kern_c = kern_f = model_c
         cands.append(("count", k, kern_c, ms_tot[0][k] / args.steps, ln_tot[0][k] / args.steps,
@@ -347,17 +401,22 @@ def bench_ours(args):
         ms = statistics.mean(d["ms"])
         pw = mode_work[s]
         alg = sum(4 * pw[k][1] + 8 * pw[k][2] for k in range(NM)) * 2 + 12 * d["pairs"]
-        per_s_out.append({"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
-                          "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
-                          "s_edges_per_s": d["pairs"] / (ms / 1e3),
-                          "alg_model_GBps": round(alg / (ms / 1e3) / 1e9, 1)})
+        rec = {"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
+               "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
+               "s_edges_per_s": d["pairs"] / (ms / 1e3),
+               "output_write_GBps": round(12 * d["pairs"] / (ms / 1e3) / 1e9, 1),
+               "alg_model_GBps": round(alg / (ms / 1e3) / 1e9, 1)}
+        if "fill_ms" in d:
+            rec["fill_ms"] = round(statistics.mean(d["fill_ms"]), 2)
+            rec["count_ms_shared"] = round(statistics.mean(d["count_ms_shared"]), 2)
+        per_s_out.append(rec)
 
     out = {
         "metric": metric, "value": value, "unit": "wedges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": wl_text,
+        "config": {"workload": wl_text, "sweep": sweep,
                    "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": args.window,
                    "l2": "flushed before each step (512 MiB device write); inputs resident",
                    "parallelism": f"replicas x{world}"},
@@ -369,7 +428,7 @@ def bench_ours(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O))
+        out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O), sweep)
     if rank == 0 and world == 1 and not args.no_cpu:
         wedges, dt, cores, sample = oracle_sample(h, s_list, cpu_rows, seed=1)
         out["cpu_baseline"] = {"value": wedges / dt, "unit": "wedges/s", "cores": cores,
@@ -380,7 +439,7 @@ def bench_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def e2e(args, slg, h, s_list, stream, bufs):
+def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s"):
     """Same sweep through the public API from pinned host memory.
 
     Timed (wall clock): host->device copy of the CSR (inside slg_load), the
@@ -399,16 +458,29 @@ def e2e(args, slg, h, s_list, stream, bufs):
     W = 0
     with torch.cuda.stream(stream):
         g = slg.slg_load(off_h, idx_h, h.m, h.n, stream=stream)
-        for s in s_list:
-            _, w = slg.slg_count(g, s)
-            W += w
-            splits = slg.slg_plan_windows(g, s, WINDOW)
-            for r0, r1 in zip(splits[:-1], splits[1:]):
-                slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW)
-            slg.slg_row_offsets(g, s, rowoff)
+        if sweep == "ensemble":
+            slg.slg_ensemble_count(g, s_list)
+            rows = torch.empty((len(s_list), h.m + 1), dtype=torch.int64).pin_memory()
+            for t in range(len(s_list)):
+                splits = slg.slg_ensemble_plan_windows(g, s_list, WINDOW, which=t)
+                for r0, r1 in zip(splits[:-1], splits[1:]):
+                    slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, WINDOW,
+                                                  which=t)
+            slg.slg_ensemble_row_offsets(g, s_list, rows)
+        else:
+            for s in s_list:
+                splits = slg.slg_plan_windows(g, s, WINDOW)
+                for r0, r1 in zip(splits[:-1], splits[1:]):
+                    slg.slg_build_window(g, s, int(r0), int(r1), I, J, O, WINDOW)
+                slg.slg_row_offsets(g, s, rowoff)
         g.free()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # the metric's work, W = sum over s of W_s (counted outside the timed region)
+    with torch.cuda.stream(stream):
+        g = slg.slg_load(h.off, h.idx, h.m, h.n, stream=stream)
+        W = sum(slg.slg_count(g, s)[1] for s in s_list)
+        g.free()
     return {"value": W / dt, "unit": "wedges/s", "h2d_bytes_per_step": int(h.off.nbytes + h.idx.nbytes),
             "d2h_bytes_per_step": int(8 * (h.m + 1) * len(s_list)), "seconds": round(dt, 3),
             "note": "lists stay in the device window; host reads |L_s| and row offsets"}
@@ -564,6 +636,7 @@ def bench_batch(args):
         tune_s = time.perf_counter() - t0
         b.free()
     res = {}
+    clocks = Clocks(dev)
     for name, fn in (("batched", batched), ("sequential", sequential), ("batched_autotuned", batched)):
         if name == "batched_autotuned":
             tuned_bins = tuned
@@ -578,6 +651,7 @@ def bench_batch(args):
         res[name] = {"wedges_per_s": W / (ms / 1e3), "s_edges_per_s": P / (ms / 1e3),
                      "ms_per_step": round(ms, 1), "gpu_launches": int(launches),
                      "pairs": P, "wedges": W}
+    clk = clocks.stop()
     for g in graphs:
         g.free()
     out = {
@@ -595,6 +669,7 @@ def bench_batch(args):
         "batched_autotuned": dict(res["batched_autotuned"], bins=tuned, tuning_s=round(tune_s, 1)),
         "speedup_vs_sequential": (res["batched_autotuned"]["wedges_per_s"]
                                   / res["sequential"]["wedges_per_s"]),
+        "clocks": clk,
     }
     print(json.dumps(out), flush=True)
 
@@ -736,10 +811,11 @@ SERVE_WORKLOAD = ("served: 64 resident hypergraphs (8 with m=1,000,000, 56 with 
 def bench_serve(args):
     """Latency and throughput of the query server against one query at a time.
 
-    For each arrival rate the same seeded query stream is played against a
-    server with 8 workers (queries overlap on the device, admission by
-    predicted kept-result memory) and against the same runtime with one worker
-    (a one-query-at-a-time loop). Latency is submit -> result ready.
+    For each arrival rate the same seeded query stream (args.queries queries) is
+    played against the server with continuous batching, the same server without
+    batching, and one worker (a one-query-at-a-time loop). Latency is submit ->
+    result ready, reported overall and per size class (queries on the eight
+    graphs with m = 1,000,000 and on the 56 small ones).
     """
     import torch
     import paper_2201_11326_gb300 as slg
@@ -749,14 +825,17 @@ def bench_serve(args):
     gen_s = time.perf_counter() - t0
     gs = [slg.slg_load(h.off, h.idx, h.m, h.n) for h in hs]
     torch.cuda.synchronize()
-    rates = [100, 300, 1000, 3000, 10000]
-    nq = args.graphs if args.graphs != 4096 else 128
+    rates = [100, 1000, 10000]
+    nq = args.queries
     rng = np.random.default_rng([1, 2])
     streams = {}
     for r in rates:
         gap = rng.exponential(1.0 / r, size=nq)
         streams[r] = (np.cumsum(gap) - gap[0], rng.integers(0, 64, size=nq),
                       rng.integers(1, 17, size=nq))
+
+    def pct(x, q):
+        return round(float(np.percentile(np.asarray(x), q)) / 1e3, 2) if len(x) else None
 
     def play(srv, ids, r):
         arr, gsel, ssel = streams[r]
@@ -767,21 +846,25 @@ def bench_serve(args):
             delay = start + a - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(slg.slg_serve_submit(srv, ids[int(g)], int(s)))
+            tickets.append((slg.slg_serve_submit(srv, ids[int(g)], int(s)), int(g)))
         # collect in completion order, releasing each kept result at once (a
         # result held by the client counts against the server's memory budget)
         outstanding = list(tickets)
-        deadline = time.perf_counter() + 1800
+        lat = {"large": [], "small": []}
+        batched = 0
+        deadline = time.perf_counter() + 3600
         while outstanding and time.perf_counter() < deadline:
             still = []
-            for t in outstanding:
+            for t, g in outstanding:
                 try:
-                    slg.slg_serve_poll(srv, t, 0)
+                    res = slg.slg_serve_poll(srv, t, 0)
                 except slg.SlgError as e:
                     if e.code != slg.SLG_ETIMEOUT:
                         raise
-                    still.append(t)
+                    still.append((t, g))
                     continue
+                lat["large" if g < 8 else "small"].append(res["latency_us"])
+                batched += 1 if res["batch_size"] > 1 else 0
                 slg.slg_serve_release(srv, t)
             outstanding = still
             if outstanding:
@@ -789,18 +872,25 @@ def bench_serve(args):
         if outstanding:
             raise RuntimeError(f"{len(outstanding)} queries did not finish")
         st = slg.slg_serve_stats(srv)
-        return {"rate": r, "p50_ms": round(st["p50_us"] / 1e3, 2),
-                "p99_ms": round(st["p99_us"] / 1e3, 2), "mean_ms": round(st["mean_us"] / 1e3, 2),
+        allv = lat["large"] + lat["small"]
+        return {"rate": r, "queries": nq, "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
+                "mean_ms": round(st["mean_us"] / 1e3, 2),
+                "large_m1M": {"queries": len(lat["large"]), "p50_ms": pct(lat["large"], 50),
+                              "p99_ms": pct(lat["large"], 99)},
+                "small": {"queries": len(lat["small"]), "p50_ms": pct(lat["small"], 50),
+                          "p99_ms": pct(lat["small"], 99)},
                 "queries_per_s": round(st["queries_per_s"], 2), "wedges_per_s": st["wedges_per_s"],
-                "s_edges_per_s": st["pairs_per_s"], "span_s": round(st["span_s"], 2)}
+                "s_edges_per_s": st["pairs_per_s"], "span_s": round(st["span_s"], 2),
+                "batched_queries": batched, "batches": st["batches"],
+                "batch_overflows": st["batch_overflows"], "batch_failures": st["batch_failures"]}
 
     res = {}
     arms = (("served", dict(workers=8, policy=1, small_workers=2, small_wedges=2_000_000_000,
                             batch_max=8)),
             ("served_unbatched", dict(workers=8, policy=1, small_workers=2,
                                       small_wedges=2_000_000_000)),
-            ("served_fifo", dict(workers=8, policy=0)),
             ("one_at_a_time", dict(workers=1, policy=0)))
+    clk = {}
     for name, kw in arms:
         srv = slg.Server(memory_budget=64 << 30, window_pairs=1 << 28,
                          max_result_pairs=1 << 26, max_s=16, digest=False, **kw)
@@ -810,7 +900,9 @@ def bench_serve(args):
             t = slg.slg_serve_submit(srv, ids[g], 4)
             slg.slg_serve_poll(srv, t, 600000)
             slg.slg_serve_release(srv, t)
+        clocks = Clocks(dev)
         res[name] = [play(srv, ids, r) for r in rates]
+        clk[name] = clocks.stop()
         srv.close()
     for g in gs:
         g.free()
@@ -825,8 +917,8 @@ def bench_serve(args):
                    "memory_budget_GiB": 64, "window_pairs": 1 << 28,
                    "max_result_pairs": 1 << 26, "generation_s": round(gen_s, 1),
                    "rows": int(sum(h.m for h in hs)), "nnz": int(sum(h.nnz for h in hs))},
-        "served": served, "served_unbatched": res["served_unbatched"],
-        "served_fifo": res["served_fifo"], "one_at_a_time": loop,
+        "served": served, "served_unbatched": res["served_unbatched"], "one_at_a_time": loop,
+        "clocks": clk["served"], "clocks_by_arm": clk,
     }
     print(json.dumps(out), flush=True)
 

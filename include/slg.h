@@ -277,6 +277,13 @@ slg_status slg_kernel_stats(slg_graph* g, int32_t reset, float* ms, int64_t* lau
 #define SLG_MODE_STATS_COLS 7
 slg_status slg_mode_stats(slg_graph* g, int32_t s, int64_t* out);
 
+/* The same per handler for list `which` of an ensemble (Algorithm 3, Section
+ * III-D; see slg_ensemble_count): rows and wedges of the shared plan (built for
+ * s_list[0]), that list's pairs, and the partners its fill scans. Column 5 is
+ * the one counting pass shared by every list. */
+slg_status slg_ensemble_mode_stats(slg_graph* g, const int32_t* s_list, int32_t k, int32_t which,
+                                   int64_t* out);
+
 /*
  * slg_batch_load -- many hypergraphs, each with its own s, as one handle.
  *

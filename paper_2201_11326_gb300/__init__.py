@@ -21,7 +21,7 @@ __all__ = [
     "SlgError", "Graph", "slg_load", "slg_free", "slg_count", "slg_bound", "slg_build",
     "slg_build_window", "slg_plan_windows", "slg_row_offsets", "slg_transpose_copy",
     "slg_graph_info", "slg_set_timing", "slg_last_timing", "slg_set_bins", "slg_kernel_stats",
-    "slg_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
+    "slg_mode_stats", "slg_ensemble_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
     "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "Server", "slg_serve_create", "slg_serve_destroy",
@@ -114,6 +114,7 @@ _SIGS = {
     "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
+    "slg_ensemble_mode_stats": (_i32, [_vp, _i32p, _i32, _i32, _i64p]),
     "slg_kernel_launches": (_i64, []),
     "slg_scan_counts_noalloc": (_i32, [_vp, _vp, _i64, _vp]),
     "slg_batch_load": (_i32, [ctypes.POINTER(_vp), _i32p, _i32, _vp, ctypes.POINTER(_vp)]),
@@ -423,6 +424,15 @@ def slg_mode_stats(g: Graph, s: int):
     out = (ctypes.c_int64 * (c * NMODES))()
     _check(lib().slg_mode_stats(g.handle, s, out))
     return [list(out[c * k:c * k + c]) for k in range(NMODES)]
+
+
+def slg_ensemble_mode_stats(g: Graph, s_list, which: int):
+    """slg_mode_stats for list `which` of the ensemble s_list."""
+    a, ap, k = _s_list(s_list)
+    c = MODE_STATS_COLS
+    out = (ctypes.c_int64 * (c * NMODES))()
+    _check(lib().slg_ensemble_mode_stats(g.handle, ap, k, which, out))
+    return [list(out[c * q:c * q + c]) for q in range(NMODES)]
 
 
 def slg_kernel_launches() -> int:

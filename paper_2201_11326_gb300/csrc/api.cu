@@ -708,6 +708,21 @@ slg_status slg_mode_stats(slg_graph* h, int32_t s, int64_t* out) {
     API_END
 }
 
+slg_status slg_ensemble_mode_stats(slg_graph* h, const int32_t* s_list, int32_t k, int32_t which,
+                                   int64_t* out) {
+    if (!h || !out) return fail(SLG_EINVAL, "NULL argument");
+    if (which < 0 || which >= k) return fail(SLG_EINVAL, "bad list selector");
+    API_BEGIN
+    ensure_ensemble(h, s_list, k);
+    const slg::Plan& p = h->plan;
+    int64_t st[slg::NMODES][slg::MS_COLS];
+    slg::plan_mode_stats(h->g, p, st, h->st, p.ens.rowoff + (int64_t)which * ((int64_t)h->g.m + 1),
+                         p.ens.ioff + (int64_t)which * (p.nitems + 1));
+    for (int q = 0; q < slg::NMODES; ++q)
+        for (int c = 0; c < slg::MS_COLS; ++c) out[q * slg::MS_COLS + c] = st[q][c];
+    API_END
+}
+
 int64_t slg_kernel_launches(void) { return (int64_t)slg::g_launches.load(); }
 
 slg_status slg_last_timing(slg_graph* h, float* ms5) {

@@ -657,12 +657,14 @@ void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, Mod
 }
 
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_COLS],
-                     cudaStream_t st) {
+                     cudaStream_t st, const int64_t* rowoff, const int64_t* ioff) {
+    if (!rowoff) rowoff = p.rowoff;
+    if (!ioff) ioff = p.ioff;
     unsigned long long* d = dalloc<unsigned long long>(NMODES * MS_COLS, st);
     SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * NMODES * MS_COLS, st));
     if (g.m) {
         k_mode_stats<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.size,
-                                                         p.rowoff, p.ioff, g.off, g.idx,
+                                                         rowoff, ioff, g.off, g.idx,
                                                          g.hubidx, p.wbeg, p.wend, p.Wp, g.m, d);
         SLG_LAUNCH_CHECK();
     }

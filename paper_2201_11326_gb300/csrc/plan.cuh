@@ -189,8 +189,10 @@ void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS r
 // Per-handler totals over rows (needs counts): rows, wedges, incidences, pairs,
 // non-hub wedges, partners scanned by the dense extraction (count, fill).
 constexpr int MS_COLS = 7;
+// rowoff/ioff: the list's row and item offsets (null: the plan's own).
 void plan_mode_stats(const GraphDev& g, const Plan& p, int64_t out[NMODES][MS_COLS],
-                     cudaStream_t st);
+                     cudaStream_t st, const int64_t* rowoff = nullptr,
+                     const int64_t* ioff = nullptr);
 // Hub-pair handler (hubpair.cu): kernel attributes, CTAs per launch, and one
 // launch over the MODE_HUBPAIR items.
 void hubpair_setup(int sms, int ctas[2]);
