@@ -539,6 +539,39 @@ slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_ite
 slg_status slg_set_hub_pairs(slg_graph* g, int32_t max_hubs, int64_t min_sparse_wedges);
 
 /*
+ * slg_set_staging -- one walk instead of two for the sparse-accumulator and
+ * hub-pair rows.
+ *
+ * Algorithm 2 (Section III-C) counts each row's pairs, the offsets are a scan
+ * of the counts, and each row is then walked again to write its pairs. For the
+ * sparse-accumulator and hub-pair rows the counting pass may instead run their
+ * writing kernels: each item's pairs go, in canonical order, into a staging
+ * pool on the device (in chunks of 2^20 pairs per CTA) along with its count;
+ * once the pool is spent the remaining items are counted as usual. A window
+ * (slg_build_window, slg_build) then copies its staged items into place and
+ * walks only the others. Results are identical with or without staging.
+ *
+ *   max_bytes : -1 (default) automatic: three quarters of the free device
+ *               memory beyond 6 GiB (5 bytes per pair plus 8 bytes per work
+ *               item), at most 2^34 pairs, and no more than the rows can fill
+ *               (the entries they walk, plus a chunk per CTA); 0 disables
+ *               staging; > 0 caps the pool at this many bytes.
+ * CTAs take chunks of 2^12 to 2^20 pairs (a quarter CTA's share of what the
+ * rows can fill); no pool is made below 16 chunks (automatic) or one chunk
+ * (capped). The pool is allocated by each counting pass of a plan that has
+ * such rows and released with the plan (a new s, slg_set_bins, slg_free). A
+ * server's queries never stage. Releases the current plan.
+ */
+slg_status slg_set_staging(slg_graph* g, int64_t max_bytes);
+
+/*
+ * slg_staging_stats -- the last counting pass's staging: out4 = {pool size
+ * in pairs, chunk size in pairs, items staged, work items of the plan}; zeros
+ * (but the items) when it staged nothing or the plan is not counted.
+ */
+slg_status slg_staging_stats(slg_graph* g, int64_t* out4);
+
+/*
  * slg_autotune -- choose the binning thresholds of slg_set_bins for s on this
  * graph by measurement (the paper tunes its ranges, chunking and relabelling by
  * hand, Sections III-F and IV). Coordinate descent from the current thresholds:

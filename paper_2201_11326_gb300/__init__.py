@@ -24,7 +24,7 @@ __all__ = [
     "slg_mode_stats", "slg_ensemble_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
-    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "Server", "slg_serve_create", "slg_serve_destroy",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "slg_set_staging", "slg_staging_stats", "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
     "lib",
@@ -111,6 +111,8 @@ _SIGS = {
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
     "slg_set_hub_pairs": (_i32, [_vp, _i32, _i64]),
+    "slg_set_staging": (_i32, [_vp, _i64]),
+    "slg_staging_stats": (_i32, [_vp, _i64p]),
     "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
@@ -405,7 +407,7 @@ MODE_NAMES = ("warp", "block", "dense", "wdense", "sparse", "wsparse", "hubpair"
 
 
 def slg_kernel_stats(g: Graph, reset: bool = False):
-    """(ms[2][4], launches[2][4]) per pass (count, fill) and handler (MODE_NAMES)."""
+    """(ms[2][NMODES], launches[2][NMODES]) per pass (count, fill) and handler (MODE_NAMES)."""
     ms = (ctypes.c_float * (2 * NMODES))()
     ln = (ctypes.c_int64 * (2 * NMODES))()
     _check(lib().slg_kernel_stats(g.handle, 1 if reset else 0, ms, ln))
@@ -608,6 +610,19 @@ def slg_set_bins(g: Graph, warp_max_wedges: int = 128, block_item_wedges: int = 
 def slg_set_hub_pairs(g: Graph, max_hubs: int = 4096, min_sparse_wedges: int = 1 << 33):
     """Hub-pair handler for sparse rows at s >= 2 (max_hubs = 0 disables it)."""
     _check(lib().slg_set_hub_pairs(g.handle, max_hubs, min_sparse_wedges))
+
+
+def slg_set_staging(g: Graph, max_bytes: int = -1):
+    """The counting pass's staging pool: -1 automatic, 0 off, > 0 at most this many bytes."""
+    _check(lib().slg_set_staging(g.handle, max_bytes))
+
+
+def slg_staging_stats(g: Graph) -> dict:
+    """The last counting pass's staging: pool and chunk sizes (pairs), items staged, plan items."""
+    out = np.zeros(4, np.int64)
+    _check(lib().slg_staging_stats(g.handle, out.ctypes.data_as(_i64p)))
+    return {"pool_pairs": int(out[0]), "chunk_pairs": int(out[1]), "items_staged": int(out[2]),
+            "items": int(out[3])}
 
 
 def slg_autotune(g: Graph, s: int, max_trials: int = 24):

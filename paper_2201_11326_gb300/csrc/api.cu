@@ -121,6 +121,36 @@ void build_plan(slg_graph* h, int32_t s, const BinParams& bp) {
     plan_build(h->g, s, bp, p, h->st, h->hp.built ? &h->hp : nullptr);
 }
 
+// The counting pass's staging pool (StageArgs) for a plan with
+// sparse-accumulator or hub-pair items: three quarters of the free device
+// memory beyond 6 GiB, at most stage_max_bytes when set, at most 2^34 pairs,
+// and no more than those rows can fill (their walk, plus a chunk per CTA).
+// Views (which share their device with other queries) stage nothing.
+void plan_staging(slg_graph* h) {
+    Plan& p = h->plan;
+    p.release_stage(h->st);
+    if (h->stage_max_bytes == 0 || !h->owns_data) return;
+    if (p.mode_count[MODE_SPARSE] == 0 && (p.mode_count[MODE_HUBPAIR] == 0 || !p.hp)) return;
+    SLG_CUDA_TRY(cudaStreamSynchronize(h->st));  // released buffers are back with the device
+    size_t fr = 0, tot = 0;
+    SLG_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    int64_t budget = ((int64_t)fr - ((int64_t)6 << 30)) / 4 * 3;
+    if (h->stage_max_bytes > 0) budget = std::min(budget, h->stage_max_bytes);
+    // chunks: a CTA's share of what the rows can fill, between 2^12 and 2^20 pairs
+    const int64_t bound = plan_stage_bound(h->g, p, h->st);
+    const int64_t ctas = 1024;  // CTAs of the two handlers' fill launches, about
+    const int64_t chunk = std::max<int64_t>(4096, std::min<int64_t>(SG_CHUNK, bound / (4 * ctas)));
+    int64_t cap = std::min<int64_t>((budget - 8 * p.nitems) / 5, (int64_t)1 << 34);
+    cap = std::min(cap, bound + (ctas + 16) * chunk);
+    if (cap < (h->stage_max_bytes > 0 ? chunk : 16 * chunk)) return;
+    p.stage_chunk = chunk;
+    p.stage_at = dalloc<int64_t>((size_t)p.nitems, h->st);
+    p.stage_J = dalloc<int32_t>((size_t)cap, h->st);
+    p.stage_O = dalloc<uint8_t>((size_t)cap, h->st);
+    p.stage_cursor = dalloc<unsigned long long>(1, h->st);
+    p.stage_cap = cap;
+}
+
 slg_graph* make_view(const slg_graph* base, cudaStream_t st) {
     slg_graph* h = new slg_graph();
     h->g = base->g;
@@ -190,6 +220,7 @@ void ensure_counted(slg_graph* h, int32_t s) {
     if (p.built && p.s == s && p.counted) return;
     h->timer.mark(0, h->st);
     if (!(p.built && p.s == s)) slg::build_plan(h, s, h->bp);
+    slg::plan_staging(h);
     h->timer.mark(1, h->st);
     slg::run_count(h->g, p, p.rs, p.icnt, &h->mtimer, h->st);
     h->timer.mark(2, h->st);
@@ -261,7 +292,7 @@ int64_t fill_window_dev(slg_graph* h, int32_t r0, int32_t r1, int32_t* I, int32_
     const int64_t P = w.end - w.base;
     h->timer.mark(3, h->st);
     slg::run_fill(h->g, h->plan, h->plan.rs, h->plan.ioff, w.q0, w.q1, I, J, O, P, &h->mtimer,
-                  h->st);
+                  h->st, /*staged=*/true);
     h->timer.mark(4, h->st);
     if (dtot || drows)
         slg::run_digest(h->plan.rs, h->plan.rowoff, r0, r1, I, J, O, P, dtot, drows, h->st);
@@ -764,6 +795,27 @@ slg_status slg_set_hub_pairs(slg_graph* h, int32_t max_hubs, int64_t min_sparse_
     h->hp.tried = false;
     h->hp_max_hubs = max_hubs;
     h->hp_min_wedges = min_sparse_wedges;
+    API_END
+}
+
+slg_status slg_set_staging(slg_graph* h, int64_t max_bytes) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (max_bytes < -1) return fail(SLG_EINVAL, "max_bytes must be -1 (automatic), 0 (off) or > 0");
+    API_BEGIN
+    h->plan.release(h->st);
+    h->stage_max_bytes = max_bytes;
+    API_END
+}
+
+slg_status slg_staging_stats(slg_graph* h, int64_t* out4) {
+    if (!h || !out4) return fail(SLG_EINVAL, "graph and out4 must not be NULL");
+    API_BEGIN
+    const slg::Plan& p = h->plan;
+    const bool on = p.counted && p.stage_at;
+    out4[0] = on ? p.stage_cap : 0;
+    out4[1] = on ? p.stage_chunk : 0;
+    out4[2] = on ? slg::plan_staged_items(p, h->st) : 0;
+    out4[3] = p.built ? p.nitems : 0;
     API_END
 }
 

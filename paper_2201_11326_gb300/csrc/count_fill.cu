@@ -1021,13 +1021,45 @@ constexpr unsigned ENS_PER_LIST = ALL_MODES & ~ENS_FUSED;
 // heads (zeroed, used once); err: the shared error flag. With `ea` (counting
 // pass only), the dense handlers run their ensemble form (every list in one
 // launch).
+// Staged items of [item_lo, item_hi) into place, one warp per item: pairs
+// at[q] .. at[q] + n - 1 of the pool go to ioff[q] - ioff[item_lo] onwards.
+__global__ void k_place_staged(const Item* __restrict__ items, const int64_t* __restrict__ at,
+                               const int64_t* __restrict__ ioff, int32_t item_lo, int32_t item_hi,
+                               const int32_t* __restrict__ sJ, const uint8_t* __restrict__ sO,
+                               RowS rs, int32_t* __restrict__ I, int32_t* __restrict__ J,
+                               int32_t* __restrict__ O, int64_t limit, int32_t* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t o0 = ioff[item_lo];
+    for (int64_t q = item_lo + warp; q < item_hi; q += nwarps) {
+        const int64_t a = at[q];
+        if (a < 0) continue;
+        const int64_t base = ioff[q] - o0, n = ioff[q + 1] - ioff[q];
+        const int32_t i = items[q].row;
+        const int32_t row = i - rs.base_of(i);
+        for (int64_t k = lane; k < n; k += 32) {
+            const int64_t p = base + k;
+            if (p < limit) {
+                I[p] = row;
+                J[p] = sJ[a + k];
+                O[p] = (int32_t)sO[a + k];
+            } else {
+                atomicOr(err, ERR_BOUNDS);
+            }
+        }
+    }
+}
+
 template <bool FILL>
 void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
                   int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
                   int64_t limit, int32_t* queue, int32_t* err, ModeTimer* mt, cudaStream_t st,
-                  unsigned modes = ALL_MODES, const EnsArgs* ea = nullptr) {
+                  unsigned modes = ALL_MODES, const EnsArgs* ea = nullptr,
+                  const StageArgs& sa = StageArgs{}) {
     Occupancy& oc = occupancy();
     const bool timed = mt && mt->on;
+    const int pass = FILL && sa.J == nullptr ? 1 : 0;  // staging fills count as counting
     auto tick = [&](int mode, int edge) {
         if (timed) SLG_CUDA_TRY(cudaEventRecord(mt->ev[2 * mode + edge], st));
     };
@@ -1092,7 +1124,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         ran[MODE_SPARSE] = true;
         tick(MODE_SPARSE, 0);
         launch_sparse(FILL, oc.sparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J, O,
-                      queue + MODE_SPARSE, limit, err, st);
+                      queue + MODE_SPARSE, limit, err, st, sa);
         tick(MODE_SPARSE, 1);
     }
     if (want(MODE_WSPARSE)) {
@@ -1106,7 +1138,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         ran[MODE_HUBPAIR] = true;
         tick(MODE_HUBPAIR, 0);
         launch_hubpair(FILL, oc.hubpair_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J,
-                       O, queue + MODE_HUBPAIR, limit, err, st);
+                       O, queue + MODE_HUBPAIR, limit, err, st, sa);
         tick(MODE_HUBPAIR, 1);
     }
     if (timed) {
@@ -1115,8 +1147,8 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
             float ms = 0;
             SLG_CUDA_TRY(cudaEventSynchronize(mt->ev[2 * k + 1]));
             SLG_CUDA_TRY(cudaEventElapsedTime(&ms, mt->ev[2 * k], mt->ev[2 * k + 1]));
-            mt->ms[FILL ? 1 : 0][k] += ms;
-            mt->launches[FILL ? 1 : 0][k] += 1;
+            mt->ms[pass][k] += ms;
+            mt->launches[pass][k] += 1;
         }
     }
 }
@@ -1158,6 +1190,16 @@ EnsArgs ens_args(const Plan& p) {
 void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
                cudaStream_t st) {
     int32_t* sc = new_scratch(st);
+    if (p.stage_at && p.stage_cap > 0) {
+        // sparse-accumulator and hub-pair items: their fill kernels count and
+        // stage while the pool lasts; the counting kernels below go on from
+        // where each of their queues stopped
+        SLG_CUDA_TRY(cudaMemsetAsync(p.stage_at, 0xff, sizeof(int64_t) * p.nitems, st));
+        SLG_CUDA_TRY(cudaMemsetAsync(p.stage_cursor, 0, sizeof(unsigned long long), st));
+        launch_items<true>(g, p, rs, 0, (int32_t)p.nitems, icnt, nullptr, nullptr, nullptr,
+                           nullptr, 0, sc, sc + NMODES, mt, st,
+                           (1u << MODE_SPARSE) | (1u << MODE_HUBPAIR), nullptr, p.stage_args());
+    }
     launch_items<false>(g, p, rs, 0, (int32_t)p.nitems, icnt, nullptr, nullptr, nullptr, nullptr,
                         0, sc, sc + NMODES, mt, st);
     check_scratch(sc, st, "counting pass");
@@ -1165,11 +1207,20 @@ void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTim
 
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
-              cudaStream_t st) {
+              cudaStream_t st, bool staged) {
     if (item_hi <= item_lo) return;
     int32_t* sc = new_scratch(st);
+    StageArgs skip{};
+    if (staged && p.stage_at && p.stage_cap > 0) {
+        // staged items are copied into place; the fill kernels skip them
+        k_place_staged<<<152 * 16, 256, 0, st>>>(p.items, p.stage_at, ioff, item_lo, item_hi,
+                                                 p.stage_J, p.stage_O, rs, I, J, O, limit,
+                                                 sc + NMODES);
+        SLG_LAUNCH_CHECK();
+        skip.at = p.stage_at;
+    }
     launch_items<true>(g, p, rs, item_lo, item_hi, nullptr, ioff, I, J, O, limit, sc, sc + NMODES,
-                       mt, st);
+                       mt, st, ALL_MODES, nullptr, skip);
     check_scratch(sc, st, "fill pass");
 }
 

@@ -39,6 +39,9 @@ struct slg_graph {
     int32_t hp_max_hubs = slg::HP_MAXK;           // 0 disables the hub-pair handler
     int64_t hp_min_wedges = (int64_t)1 << 33;
     int64_t hp_max_pairs = (int64_t)1900000000;  // hub-pair incidences at most
+    // staging pool of the counting pass (slg::StageArgs): -1 automatic, 0 off,
+    // > 0 at most this many bytes
+    int64_t stage_max_bytes = -1;
 };
 
 namespace slg {

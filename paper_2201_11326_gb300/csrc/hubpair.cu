@@ -132,6 +132,34 @@ __global__ void k_big_bits(const int32_t* __restrict__ hoff, const int32_t* __re
     }
 }
 
+// Row i's look record (a thread per row).
+__global__ void k_row_records(const int32_t* __restrict__ hoff, const int32_t* __restrict__ hlist,
+                              int32_t m, uint4* __restrict__ hrec) {
+    GRID_STRIDE(i, m) {
+        const int32_t h0 = hoff[i], nh = hoff[i + 1] - h0;
+        uint32_t w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = 0u;
+        if (nh > 31) {
+            w[0] = 0xffffu;
+        } else {
+            w[0] = (uint32_t)nh;
+            for (int32_t k = 0; k < nh; ++k) {
+                const int32_t pos = k + 1;
+                const uint32_t id = (uint32_t)hlist[h0 + k];
+#pragma unroll
+                for (int x = 0; x < 16; ++x)
+                    if (x == (pos >> 1)) w[x] |= id << ((pos & 1) * 16);
+            }
+        }
+        uint4* r = hrec + (int64_t)i * 4;
+        r[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        r[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        r[2] = make_uint4(w[8], w[9], w[10], w[11]);
+        r[3] = make_uint4(w[12], w[13], w[14], w[15]);
+    }
+}
+
 __global__ void k_pair_counts(const int32_t* __restrict__ hoff, int32_t m,
                               int32_t* __restrict__ np) {
     GRID_STRIDE(i, m) {
@@ -176,6 +204,7 @@ void HubPairs::release(cudaStream_t st) {
     dfree(tpos2, st);
     dfree(bigidx, st);
     dfree(bigbits, st);
+    dfree(hrec, st);
     bigk = 0;
     built = false;
     K = 0;
@@ -288,6 +317,9 @@ void hubpair_build(const GraphDev& g, int32_t max_hubs, int64_t max_pairs, HubPa
         dfree(flags, st);
         dfree(rank, st);
     }
+    hp.hrec = dalloc<uint4>((size_t)m * 4, st);
+    k_row_records<<<grid_for(m, 256), 256, 0, st>>>(hp.hoff, hp.hlist, m, hp.hrec);
+    SLG_LAUNCH_CHECK();
     // hub-pair incidences and their transpose
     k_pair_counts<<<grid_for(m, 256), 256, 0, st>>>(hp.hoff, m, kr);
     SLG_LAUNCH_CHECK();
@@ -394,7 +426,7 @@ __device__ __forceinline__ int32_t gallop_to(const int32_t* __restrict__ src, in
 // row's items in this launch in order, so each range keeps a cursor at the
 // first entry of the next slice and only the slice's end is searched).
 template <bool FILL>
-__global__ void __launch_bounds__(HP_THREADS)
+__global__ void __launch_bounds__(HP_THREADS, 3)
 k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
                 const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
@@ -402,13 +434,14 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 const int32_t* __restrict__ idxTs, const int32_t* __restrict__ hp_id,
                 const int32_t* __restrict__ hoff, const int32_t* __restrict__ hlist,
                 const int32_t* __restrict__ bigidx, const uint32_t* __restrict__ bigbits,
-                int32_t bigk, const int32_t* __restrict__ off2, const int32_t* __restrict__ wbeg2,
+                const uint4* __restrict__ hrec, int32_t bigk, const int32_t* __restrict__ off2, const int32_t* __restrict__ wbeg2,
                 const int32_t* __restrict__ wend2, const int32_t* __restrict__ idxT2s, RowS rs,
                 int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
                 int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
                 int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err,
-                int32_t* __restrict__ scratch) {
+                int32_t* __restrict__ scratch, StageArgs sa) {
     constexpr int NT = HP_THREADS;
+    const bool stg = FILL && sa.J != nullptr;  // the counting pass, staging pairs
     int32_t* cur = scratch + (int64_t)blockIdx.x * HP_SCRATCH_WORDS;  // first entry of the next slice
     int32_t* nxt = cur + HP_RANGES;                                   // first entry after this slice
     unsigned long long* surv = reinterpret_cast<unsigned long long*>(nxt + HP_RANGES);  // fill
@@ -425,6 +458,8 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
     __shared__ int32_t sh_pos, sh_n, sh_a, sh_b, sh_nchk;
     __shared__ volatile int32_t nkeys, ovf;
     __shared__ __align__(16) uint16_t chk[HP_CAP + 32];  // slots needing a look; fill: buckets
+    __shared__ long long sh_cpos, sh_cend;  // staging: the CTA's chunk of the pool
+    __shared__ int32_t sh_sovf, sh_dry;     // staging: the item did not fit; the pool is spent
     const int tid = threadIdx.x;
     const int32_t lo_r = rank[item_lo], hi_r = rank[item_hi];
     for (int t = tid; t < HP_TABLE; t += NT) {
@@ -432,9 +467,19 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
         cnts[t] = 0u;
     }
     bool clean = true;  // the table is empty (same in every thread)
+    if (tid == 0) {
+        sh_cpos = sh_cend = 0;
+        sh_dry = 0;
+    }
+    // a fill item needs its pass: it has pairs and was not staged
+    auto needs_fill = [&](int32_t qn) {
+        return ioff[qn + 1] != ioff[qn] && !(sa.at && sa.at[qn] >= 0);
+    };
 
     for (;;) {
-        if (tid == 0) sh_pos = lo_r + atomicAdd(queue, 1);
+        // a spent pool ends the staging launch; the counting kernel takes the
+        // rows from this queue position on
+        if (tid == 0) sh_pos = sh_dry ? hi_r : lo_r + atomicAdd(queue, 1);
         __syncthreads();
         const int32_t pos = sh_pos;
         if (pos >= hi_r) break;
@@ -444,6 +489,19 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
         if (pos > lo_r && items[list[pos - 1]].row == i) {
             __syncthreads();  // everyone has read sh_pos before thread 0 rewrites it
             continue;
+        }
+        if (FILL && !stg) {
+            // a row with nothing left to write (no pairs, or staged) is passed over
+            bool want = false;
+            for (int32_t k = pos + tid; k < hi_r; k += NT) {
+                const int32_t qk = list[k];
+                if (items[qk].row != i) break;
+                if (needs_fill(qk)) {
+                    want = true;
+                    break;
+                }
+            }
+            if (!__syncthreads_or(want)) continue;
         }
         const int32_t s = rs.s_of(i);
         const int32_t ib = rs.base_of(i);
@@ -466,8 +524,8 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
             int32_t qq = pp == pos ? q : list[pp];
             Item it = items[qq];
             if (it.row != i) break;
-            bool skip = false;  // cursors only: move them to the next item with pairs
-            if (FILL && ioff[qq + 1] == ioff[qq]) {
+            bool skip = false;  // cursors only: move them to the next item to fill
+            if (FILL && !stg && !needs_fill(qq)) {
                 int32_t pn = pp + 1;
                 while (pn < hi_r) {
                     const int32_t qn = list[pn];
@@ -475,7 +533,7 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                         pn = hi_r;
                         break;
                     }
-                    if (ioff[qn + 1] != ioff[qn]) break;
+                    if (needs_fill(qn)) break;
                     ++pn;
                 }
                 if (pn >= hi_r) break;  // no item of the row left with pairs
@@ -483,7 +541,25 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 pp = pn - 1;
                 skip = true;
             }
-            const int64_t obase = FILL ? ioff[qq] - ioff[item_lo] : 0;
+            if (stg) {
+                if (tid == 0) {
+                    sh_sovf = 0;
+                    if (sh_cend - sh_cpos < sa.min_room && !sh_dry) {  // a fresh chunk, if any
+                        const unsigned long long c =
+                            atomicAdd(sa.cursor, (unsigned long long)sa.chunk);
+                        if ((int64_t)c + sa.chunk <= sa.cap) {
+                            sh_cpos = (long long)c;
+                            sh_cend = (long long)c + sa.chunk;
+                        } else {
+                            sh_dry = 1;  // the row's items left are counted, not staged
+                        }
+                    }
+                    if (sh_dry) sh_cend = sh_cpos;
+                }
+                __syncthreads();
+            }
+            const int64_t obase = !FILL ? 0 : stg ? (int64_t)sh_cpos : ioff[qq] - ioff[item_lo];
+            const int64_t olimit = stg ? (int64_t)sh_cend : limit;
             int64_t out_pos = 0;  // same value in every thread
             if (tid == 0) {
                 sh_n = 1;
@@ -629,37 +705,84 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 }
                 __syncthreads();
                 const int32_t nchk = sh_nchk;
-                for (int32_t x = tid; x < nchk; x += NT) {
-                    const int slot = chk[x];
-                    const int32_t j = keys[slot];
-                    const int32_t l = (int32_t)cnts[slot];
-                    const int32_t x0 = __ldg(&hoff[j]), x1 = __ldg(&hoff[j + 1]);
-                    int32_t t = 0;
-                    if (x1 - x0 <= bigk) {
-                        // the partner's hubs against the row's bitmap, four at a time
-                        for (int32_t y = x0; y < x1 && !t; y += 4) {
-                            int32_t hv[4];
+                // two looks in flight per thread: the partner's record (its hub
+                // count and first 15 hubs in one 32-byte sector, 16 more in the
+                // next) against the row's bitmap
+                for (int32_t xb = tid; xb < nchk; xb += 2 * NT) {
+                    int slotv[2];
+                    int32_t jv[2], nh[2], tv[2];
+                    uint4 ra[2], rb[2];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) hv[u] = y + u < x1 ? __ldg(&hlist[y + u]) : -1;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                if (hv[u] >= 0 && ((hbits[hv[u] >> 5] >> (hv[u] & 31)) & 1u)) t = 1;
-                        }
-                    } else {
-                        // the row's hubs against the partner's bitmap
-                        const uint32_t* bb = bigbits + (int64_t)__ldg(&bigidx[j]) * HP_WORDS;
-                        for (int32_t y = 0; y < ki && !t; y += 4) {
-                            uint32_t bw[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                bw[u] = y + u < ki ? __ldg(&bb[hmine[y + u] >> 5]) : 0u;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                if (y + u < ki && ((bw[u] >> (hmine[y + u] & 31)) & 1u)) t = 1;
+                    for (int u = 0; u < 2; ++u) {
+                        const int32_t x = xb + u * NT;
+                        slotv[u] = x < nchk ? (int)chk[x] : -1;
+                        jv[u] = slotv[u] >= 0 ? keys[slotv[u]] : 0;
+                        ra[u] = rb[u] = make_uint4(0u, 0u, 0u, 0u);
+                        if (slotv[u] >= 0) {
+                            ra[u] = __ldg(&hrec[(int64_t)jv[u] * 4]);
+                            rb[u] = __ldg(&hrec[(int64_t)jv[u] * 4 + 1]);
                         }
                     }
-                    const int32_t ov = l + t;
-                    cnts[slot] = ov >= s ? (uint32_t)ov : 0u;
+                    // hub k of a record (1 <= k <= 31) is 16-bit field k
+                    auto hit = [&](uint32_t word, int half) {
+                        const uint32_t id = (word >> (half * 16)) & 0xffffu;
+                        return ((hbits[id >> 5] >> (id & 31)) & 1u) != 0u;
+                    };
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        nh[u] = (int32_t)(ra[u].x & 0xffffu);
+                        tv[u] = 0;
+                        if (slotv[u] < 0 || nh[u] > 31) continue;
+                        const uint32_t f[8] = {ra[u].x, ra[u].y, ra[u].z, ra[u].w,
+                                               rb[u].x, rb[u].y, rb[u].z, rb[u].w};
+#pragma unroll
+                        for (int k = 1; k < 16; ++k)
+                            if (k <= nh[u] && hit(f[k >> 1], k & 1)) tv[u] = 1;
+                        if (nh[u] > 15 && !tv[u]) {
+                            const uint4 c = __ldg(&hrec[(int64_t)jv[u] * 4 + 2]);
+                            const uint4 d = __ldg(&hrec[(int64_t)jv[u] * 4 + 3]);
+                            const uint32_t g2[8] = {c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+#pragma unroll
+                            for (int k = 16; k < 32; ++k)
+                                if (k <= nh[u] && hit(g2[(k >> 1) - 8], k & 1)) tv[u] = 1;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (slotv[u] < 0) continue;
+                        const int slot = slotv[u];
+                        const int32_t l = (int32_t)cnts[slot];
+                        int32_t t = tv[u];
+                        if (nh[u] > 31) {
+                            const int32_t j = jv[u];
+                            const int32_t x0 = __ldg(&hoff[j]), x1 = __ldg(&hoff[j + 1]);
+                            if (x1 - x0 <= bigk) {
+                                // the partner's hubs against the row's bitmap, four at a time
+                                for (int32_t y = x0; y < x1 && !t; y += 4) {
+                                    int32_t hv[4];
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v) hv[v] = y + v < x1 ? __ldg(&hlist[y + v]) : -1;
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v)
+                                        if (hv[v] >= 0 && ((hbits[hv[v] >> 5] >> (hv[v] & 31)) & 1u)) t = 1;
+                                }
+                            } else {
+                                // the row's hubs against the partner's bitmap
+                                const uint32_t* bb = bigbits + (int64_t)__ldg(&bigidx[j]) * HP_WORDS;
+                                for (int32_t y = 0; y < ki && !t; y += 4) {
+                                    uint32_t bw[4];
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v)
+                                        bw[v] = y + v < ki ? __ldg(&bb[hmine[y + v] >> 5]) : 0u;
+#pragma unroll
+                                    for (int v = 0; v < 4; ++v)
+                                        if (y + v < ki && ((bw[v] >> (hmine[y + v] & 31)) & 1u)) t = 1;
+                                }
+                            }
+                        }
+                        const int32_t ov = l + t;
+                        cnts[slot] = ov >= s ? (uint32_t)ov : 0u;
+                    }
                 }
                 __syncthreads();
                 int32_t mine = 0;
@@ -775,10 +898,17 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                     for (int32_t t = tid; t < c; t += NT) {
                         const unsigned long long v = sortbuf[t];
                         const int64_t p2 = obase + out_pos + t;
-                        if (p2 < limit) {
-                            I[p2] = i - ib;
-                            J[p2] = (int32_t)(v >> 32) - ib;
-                            O[p2] = (int32_t)(v & 0xffffffffu);
+                        if (p2 < olimit) {
+                            if (stg) {
+                                sa.J[p2] = (int32_t)(v >> 32) - ib;
+                                sa.O[p2] = (uint8_t)(v & 0xffu);
+                            } else {
+                                I[p2] = i - ib;
+                                J[p2] = (int32_t)(v >> 32) - ib;
+                                O[p2] = (int32_t)(v & 0xffffffffu);
+                            }
+                        } else if (stg) {
+                            sh_sovf = 1;  // the item is filled again later
                         } else {
                             atomicOr(err, ERR_BOUNDS);
                         }
@@ -788,6 +918,13 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 out_pos += c;
             }
             if (!FILL && tid == 0) icnt[qq] = (int32_t)out_pos;
+            if (stg && tid == 0) {
+                icnt[qq] = (int32_t)out_pos;
+                if (!sh_sovf) {
+                    sa.at[qq] = obase;
+                    sh_cpos = obase + out_pos;
+                }
+            }
             __syncthreads();
         }
     }
@@ -809,21 +946,21 @@ void hubpair_setup(int sms, int ctas[2]) {
 void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                     int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                    int32_t* err, cudaStream_t st) {
+                    int32_t* err, cudaStream_t st, const StageArgs& sa) {
     const HubPairs& hp = *p.hp;
     int32_t* scratch = dalloc<int32_t>((size_t)ctas * HP_SCRATCH_WORDS, st);
     if (fill)
         k_hubpair_items<true><<<ctas, HP_THREADS, HP_SMEM, st>>>(
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
-            hp.bigbits, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err, scratch);
+            hp.bigbits, hp.hrec, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
+            limit, err, scratch, sa);
     else
         k_hubpair_items<false><<<ctas, HP_THREADS, HP_SMEM, st>>>(
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
-            hp.bigbits, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err, scratch);
+            hp.bigbits, hp.hrec, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
+            limit, err, scratch, StageArgs{});
     SLG_LAUNCH_CHECK();
     dfree(scratch, st);
 }

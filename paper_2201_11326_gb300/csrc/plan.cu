@@ -398,6 +398,24 @@ __global__ void k_sparse_wedges(const int32_t* __restrict__ row_item,
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+// Entries the sparse-accumulator and hub-pair rows walk (wedges W[i], or the
+// hub-pair walk Wp[i]): no row of theirs has more pairs than that.
+__global__ void k_stage_bound(const int32_t* __restrict__ row_item, const Item* __restrict__ items,
+                              const int64_t* __restrict__ W, const int64_t* __restrict__ Wp,
+                              int32_t m, unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    GRID_STRIDE(i, m) {
+        const int32_t q = row_item[i];
+        if (row_item[i + 1] == q) continue;
+        const int mode = items[q].mode;
+        if (mode == MODE_SPARSE) acc += (unsigned long long)W[i];
+        if (mode == MODE_HUBPAIR && Wp) acc += (unsigned long long)max(Wp[i], (int64_t)0);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 // rowtot[r] = sum over the k lists of rowoff[t][r] (cumulative, so the sum of
 // the lists' row counts before row r)
 __global__ void k_sum_rows(const int64_t* __restrict__ rowoff, int32_t k, int32_t m,
@@ -421,8 +439,17 @@ void Plan::release_ensemble(cudaStream_t st) {
     ens.counted = false;
 }
 
+void Plan::release_stage(cudaStream_t st) {
+    dfree(stage_at, st);
+    dfree(stage_J, st);
+    dfree(stage_O, st);
+    dfree(stage_cursor, st);
+    stage_cap = 0;
+}
+
 void Plan::release(cudaStream_t st) {
     release_ensemble(st);
+    release_stage(st);
     if (idxTs_owned) dfree(idxTs, st);
     idxTs = nullptr;
     dfree(ks, st);
@@ -683,6 +710,44 @@ int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st) {
         k_sparse_wedges<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, g.m, d);
         SLG_LAUNCH_CHECK();
     }
+    unsigned long long h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    return (int64_t)h;
+}
+
+int64_t plan_stage_bound(const GraphDev& g, const Plan& p, cudaStream_t st) {
+    unsigned long long* d = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    if (g.m) {
+        k_stage_bound<<<grid_for(g.m, 256), 256, 0, st>>>(p.row_item, p.items, p.W, p.Wp, g.m, d);
+        SLG_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    return (int64_t)h;
+}
+
+namespace {
+__global__ void k_count_staged(const int64_t* __restrict__ at, int64_t n,
+                               unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    GRID_STRIDE(q, n) acc += at[q] >= 0 ? 1ull : 0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+}  // namespace
+
+int64_t plan_staged_items(const Plan& p, cudaStream_t st) {
+    if (!p.stage_at || p.nitems == 0) return 0;
+    unsigned long long* d = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    k_count_staged<<<grid_for(p.nitems, 256), 256, 0, st>>>(p.stage_at, p.nitems, d);
+    SLG_LAUNCH_CHECK();
     unsigned long long h = 0;
     SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
     SLG_CUDA_TRY(cudaStreamSynchronize(st));

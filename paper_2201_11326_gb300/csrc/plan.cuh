@@ -48,6 +48,9 @@ struct HubPairs {
     int32_t bigk = 0;
     int32_t* bigidx = nullptr;    // [m] bitmap number of the row, -1 if none
     uint32_t* bigbits = nullptr;  // [rows with a bitmap][HP_MAXK / 32]
+    // per row, 64 bytes read in one go by a one-hub look: 32 16-bit fields,
+    // the row's hub count then its hub numbers (count 0xffff: more than 31)
+    uint4* hrec = nullptr;        // [m][4]
     void release(cudaStream_t st);
 };
 
@@ -91,6 +94,24 @@ void launch_gather_offsets(const int64_t* rowoff, const int32_t* row_base_dev, i
 
 // Everything derived for one s. Items and offsets are valid once built;
 // icnt/ioff/rowoff once `counted`.
+// A staging pool for the counting pass: the sparse-accumulator and hub-pair
+// fill kernels, run as the counting pass, write each item's pairs (in order)
+// into per-CTA chunks of the pool as well as its count; an item whose pairs
+// all fit is staged at at[q], and a window later copies it into place instead
+// of walking it again. J == nullptr: no staging writes (a window's fill, which
+// skips the items with at[q] >= 0 when at is given).
+constexpr int64_t SG_CHUNK = 1 << 20;  // pairs a CTA takes from the pool at a time, at most
+struct StageArgs {
+    int32_t* J = nullptr;                  // staged partners (member-local ids)
+    uint8_t* O = nullptr;                  // staged overlaps (<= 255: both handlers take
+                                           // rows of at most 255 vertices)
+    int64_t cap = 0;                       // pool size in pairs
+    unsigned long long* cursor = nullptr;  // next free pair of the pool
+    int64_t* at = nullptr;                 // [nitems] first staged pair of item q, -1: not staged
+    int64_t chunk = SG_CHUNK;              // pairs a CTA takes from the pool at a time
+    int64_t min_room = SG_CHUNK / 32;      // an item starts in a fresh chunk below this room
+};
+
 struct Plan {
     int32_t s = 0;              // 0 for a batch (per-row s)
     bool built = false;
@@ -141,6 +162,19 @@ struct Plan {
     int64_t* Wp = nullptr;       // [m] entries a MODE_HUBPAIR row walks (non-hub wedges +
                                  // pair-list hits); null without hub pairs
 
+    // staged counting (see StageArgs); null when the counting pass stages nothing
+    int64_t* stage_at = nullptr;   // [nitems]
+    int32_t* stage_J = nullptr;    // [stage_cap]
+    uint8_t* stage_O = nullptr;    // [stage_cap]
+    unsigned long long* stage_cursor = nullptr;
+    int64_t stage_cap = 0;
+    int64_t stage_chunk = SG_CHUNK;
+    StageArgs stage_args() const {
+        return StageArgs{stage_J, stage_O, stage_cap, stage_cursor, stage_at, stage_chunk,
+                         stage_chunk / 32};
+    }
+    void release_stage(cudaStream_t st);
+
     RowS rs_for(int32_t s_t) const { return RowS{rs.srow, rs.rbase, s_t}; }
     void release_ensemble(cudaStream_t st);
     void release(cudaStream_t st);
@@ -153,6 +187,11 @@ void plan_build(const GraphDev& g, int32_t s, const BinParams& bp, Plan& p, cuda
 // MODE_SPARSE, MODE_WSPARSE) in a built plan: what hub pairs could shorten.
 int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st);
 void plan_offsets(const GraphDev& g, Plan& p, cudaStream_t st);
+// Pairs the sparse-accumulator and hub-pair rows can have at most (the
+// entries they walk): what a staging pool may need to hold.
+int64_t plan_stage_bound(const GraphDev& g, const Plan& p, cudaStream_t st);
+// Items the last counting pass staged.
+int64_t plan_staged_items(const Plan& p, cudaStream_t st);
 // Largest row total and window splits over cumulative row offsets rowoff[m+1]
 // (a single list's or the ensemble's sum).
 int64_t plan_max_row(const GraphDev& g, const int64_t* rowoff, cudaStream_t st);
@@ -168,9 +207,11 @@ void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, Mod
 // and ioff the matching per-item counts and offsets.
 void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
                cudaStream_t st);
+// staged: the plan's staging (run_count staged items of this list) is used:
+// staged items are copied into place and the fill kernels skip them.
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
-              cudaStream_t st);
+              cudaStream_t st, bool staged = false);
 // Ensemble counting pass over the plan's items (p.ens.k lists, thresholds
 // p.ens.s): counts into p.ens.icnt. Lists are filled one at a time by run_fill.
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st);
@@ -185,7 +226,7 @@ void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                   int32_t* err, cudaStream_t st);
+                   int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{});
 // Per-handler totals over rows (needs counts): rows, wedges, incidences, pairs,
 // non-hub wedges, partners scanned by the dense extraction (count, fill).
 constexpr int MS_COLS = 7;
@@ -199,7 +240,7 @@ void hubpair_setup(int sms, int ctas[2]);
 void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                     int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                    int32_t* err, cudaStream_t st);
+                    int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{});
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,

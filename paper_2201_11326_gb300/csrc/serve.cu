@@ -163,6 +163,7 @@ bool run_batch(slg_server* S, Worker& W, std::vector<ServeQuery>& Qs) {
         slg_graph* v;
         ~Free() { slg_free(v); }
     } guard{bh};
+    bh->stage_max_bytes = 0;  // workers share the device: no staging pool
     int64_t total = 0;
     rc = slg_count(bh, 0, &total, nullptr);
     if (rc != SLG_OK) throw slg::Error{rc, slg_last_error()};

@@ -56,7 +56,8 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ wend, const int32_t* __restrict__ idxTs, RowS rs,
                int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
                int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
-               int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err) {
+               int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err,
+               StageArgs sa) {
     extern __shared__ __align__(16) uint32_t dyn[];
     uint32_t* ctr = dyn;                                                   // SP_WORDS
     uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + SP_WORDS);      // SP_TOUCH
@@ -70,7 +71,10 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     __shared__ int32_t tmp[SP_WARPS + 1];
     __shared__ int32_t sh_pos, sh_n;
     __shared__ int32_t sh_nt[2];  // touched counters of the tile, by tile parity
+    __shared__ long long sh_cpos, sh_cend;  // staging: the CTA's chunk of the pool
+    __shared__ int32_t sh_sovf;             // staging: the item's pairs did not fit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool stg = FILL && sa.J != nullptr;  // the counting pass, staging pairs
     const unsigned lt = (1u << lane) - 1u;
     const int32_t lo = rank[item_lo], hi = rank[item_hi];
     // the counters (and the fill's bitmap) start at zero; every tile leaves them so
@@ -78,18 +82,31 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
     if (FILL)
         for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
 
+    if (tid == 0) sh_cpos = sh_cend = 0;
     for (;;) {
         if (tid == 0) {
-            sh_pos = lo + atomicAdd(queue, 1);
             sh_n = 0;
             sh_nt[0] = sh_nt[1] = 0;
+            sh_sovf = 0;
+            bool room = true;
+            if (stg && sh_cend - sh_cpos < sa.min_room) {  // a fresh chunk, if the pool has one
+                const unsigned long long c = atomicAdd(sa.cursor, (unsigned long long)sa.chunk);
+                room = (int64_t)c + sa.chunk <= sa.cap;
+                if (room) {
+                    sh_cpos = (long long)c;
+                    sh_cend = (long long)c + sa.chunk;
+                }
+            }
+            // a spent pool ends the staging launch; the counting kernel takes the
+            // items from this queue position on
+            sh_pos = room ? lo + atomicAdd(queue, 1) : hi;
         }
         __syncthreads();
         const int32_t pos = sh_pos;
         if (pos >= hi) break;
         const int32_t q = list[pos];
-        if (FILL && ioff[q + 1] == ioff[q]) {  // nothing to write (same in every thread)
-            __syncthreads();
+        if (FILL && !stg && (ioff[q + 1] == ioff[q] || (sa.at && sa.at[q] >= 0))) {
+            __syncthreads();  // nothing to write, or staged (same in every thread)
             continue;
         }
         const Item it = items[q];
@@ -116,7 +133,8 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 }
             }
         }
-        const int64_t obase = FILL ? ioff[q] - ioff[item_lo] : 0;
+        const int64_t obase = !FILL ? 0 : stg ? (int64_t)sh_cpos : ioff[q] - ioff[item_lo];
+        const int64_t olimit = stg ? (int64_t)sh_cend : limit;
         int64_t out_pos = 0;   // fill: the item's pairs before the tile (same in every thread)
         int32_t my_count = 0;  // counting pass: this thread's survivors so far
         __syncthreads();
@@ -247,12 +265,24 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                     }
                 }
             }
+            if (!__syncthreads_or(mine > 0)) {
+                // no survivor: clear the tile's counters, as the counting pass does
+                if (listed) {
+                    for (int32_t x = tid; x < nt; x += SP_THREADS) {
+                        const int32_t slot = touched[x];
+                        ctr[slot >> 2] = 0u;
+                    }
+                } else {
+                    for (int32_t w = tid; w < nwords; w += SP_THREADS) ctr[w] = 0u;
+                }
+                __syncthreads();  // the touched list is refilled by the next tile
+                continue;
+            }
             // 3. rank of a survivor: survivors in earlier bitmap words plus
             // earlier bits of its own word (the scan's barriers order the
             // bitmap writes above before these reads)
             uint32_t wv[4];
             int32_t sum = 0;
-            __syncthreads();
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 wv[r] = bm[4 * tid + r];
@@ -270,10 +300,17 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             auto emit = [&](int32_t slot, int32_t c) {
                 const uint32_t wb = bm[slot >> 5];
                 const int64_t p2 = base + wpre[slot >> 5] + __popc(wb & ((1u << (slot & 31)) - 1u));
-                if (p2 < limit) {
-                    I[p2] = i - ib;
-                    J[p2] = t0 + slot - ib;
-                    O[p2] = c;
+                if (p2 < olimit) {
+                    if (stg) {
+                        sa.J[p2] = t0 + slot - ib;
+                        sa.O[p2] = (uint8_t)c;
+                    } else {
+                        I[p2] = i - ib;
+                        J[p2] = t0 + slot - ib;
+                        O[p2] = c;
+                    }
+                } else if (stg) {
+                    sh_sovf = 1;  // the item is filled again later
                 } else {
                     atomicOr(err, ERR_BOUNDS);
                 }
@@ -310,6 +347,15 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
             int32_t total = 0;
             block_excl_scan<SP_THREADS>(my_count, &total, tmp);
             if (tid == 0) icnt[q] = total;
+        } else if (stg) {
+            __syncthreads();  // every write (and overflow flag) of the item is done
+            if (tid == 0) {
+                icnt[q] = (int32_t)out_pos;
+                if (!sh_sovf) {
+                    sa.at[q] = obase;
+                    sh_cpos = obase + out_pos;
+                }
+            }
         }
         __syncthreads();
     }
@@ -656,15 +702,15 @@ void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                   int32_t* err, cudaStream_t st) {
+                   int32_t* err, cudaStream_t st, const StageArgs& sa) {
     if (fill)
         k_sparse_items<true><<<ctas, SP_THREADS, sp_smem(true), st>>>(
             p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, sa);
     else
         k_sparse_items<false><<<ctas, SP_THREADS, sp_smem(false), st>>>(
             p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err);
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, StageArgs{});
     SLG_LAUNCH_CHECK();
 }
 

@@ -574,3 +574,59 @@ def test_hub_pairs_disabled_and_default_threshold():
             slg.slg_set_hub_pairs(g, 5000, 0)
     finally:
         g.free()
+
+
+# staging pools: automatic, none, and one of three chunks (spent after three
+# CTAs' worth of items: the counting kernels take the others)
+@pytest.mark.parametrize("handler", ["hubpair", "sparse"])
+@pytest.mark.parametrize("pool", ["auto", "off", "three_chunks"])
+def test_staged_counting_pass(handler, pool):
+    # the sparse-accumulator and hub-pair fill kernels run as the counting pass,
+    # staging each item's pairs; windows copy staged items and fill the rest
+    h = synth.large(m=20000)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    mode = slg.MODE_NAMES.index(handler)
+    try:
+        if handler == "hubpair":
+            slg.slg_set_bins(g, *FORCED["block_only"])
+            slg.slg_set_hub_pairs(g, 512, 0)
+        else:
+            slg.slg_set_bins(g, *FORCED["sparse_cta_only"])
+            slg.slg_set_hub_pairs(g, 0, 0)
+        if pool != "auto":
+            slg.slg_count(g, 2)
+            st = slg.slg_staging_stats(g)
+            assert st["pool_pairs"] > 0 and st["items_staged"] > 0, st
+            # 8 bytes per item, 5 per pooled pair
+            slg.slg_set_staging(g, 0 if pool == "off" else 8 * st["items"] + 5 * 3 * st["chunk_pairs"])
+        slg.slg_set_timing(g, True)
+        for s in (2, 4, 8):
+            slg.slg_kernel_stats(g, reset=True)
+            got = slg.slg_build(g, s)
+            assert_same(got, oracle_list("large20000", h, s), f"{handler} {pool} s={s}")
+            launches = slg.slg_kernel_stats(g)[1][0][mode]
+            rows = slg.slg_mode_stats(g, s)[mode][0]
+            st = slg.slg_staging_stats(g)
+            assert rows > 0
+            # staging launches the fill kernel before the counting kernel
+            assert launches == (1 if pool == "off" else 2), (pool, s, launches)
+            if pool == "off":
+                assert st["items_staged"] == 0
+            elif pool == "three_chunks":
+                assert 0 < st["items_staged"] and st["pool_pairs"] <= 3 << 20, st
+                if s == 2:  # the pool ran out: fewer items staged than the handler's rows
+                    assert st["items_staged"] < rows, (st, rows)
+        # several windows, each mixing copied and walked items, with row digests
+        counts, digs, _ = oracle.rows(h.off, h.idx, None, [3])
+        cap = max(int(counts.max()), int(counts.sum()) // 7 + 1)
+        I, J, O = (np.zeros(cap, np.int32) for _ in range(3))
+        splits = slg.slg_plan_windows(g, 3, cap)
+        assert len(splits) > 3
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            rd = np.zeros(r1 - r0, np.uint64)
+            slg.slg_build_window(g, 3, int(r0), int(r1), I, J, O, digest=True, row_digests=rd)
+            assert np.array_equal(rd, digs[r0:r1, 0])
+        with pytest.raises(slg.SlgError):
+            slg.slg_set_staging(g, -2)
+    finally:
+        g.free()
