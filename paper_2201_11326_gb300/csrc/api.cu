@@ -221,6 +221,7 @@ void ensure_counted(slg_graph* h, int32_t s) {
     h->timer.mark(0, h->st);
     if (!(p.built && p.s == s)) slg::build_plan(h, s, h->bp);
     slg::plan_staging(h);
+    p.stage_s = s;
     h->timer.mark(1, h->st);
     slg::run_count(h->g, p, p.rs, p.icnt, &h->mtimer, h->st);
     h->timer.mark(2, h->st);
@@ -291,8 +292,10 @@ int64_t fill_window_dev(slg_graph* h, int32_t r0, int32_t r1, int32_t* I, int32_
                         const WindowInfo& w) {
     const int64_t P = w.end - w.base;
     h->timer.mark(3, h->st);
-    slg::run_fill(h->g, h->plan, h->plan.rs, h->plan.ioff, w.q0, w.q1, I, J, O, P, &h->mtimer,
-                  h->st, /*staged=*/true);
+    const slg::Plan& p = h->plan;
+    slg::StageUse su;
+    if (p.stage_s == p.s) su.st_ioff = p.ioff;  // this list was staged
+    slg::run_fill(h->g, p, p.rs, p.ioff, w.q0, w.q1, I, J, O, P, &h->mtimer, h->st, su);
     h->timer.mark(4, h->st);
     if (dtot || drows)
         slg::run_digest(h->plan.rs, h->plan.rowoff, r0, r1, I, J, O, P, dtot, drows, h->st);
@@ -811,7 +814,7 @@ slg_status slg_staging_stats(slg_graph* h, int64_t* out4) {
     if (!h || !out4) return fail(SLG_EINVAL, "graph and out4 must not be NULL");
     API_BEGIN
     const slg::Plan& p = h->plan;
-    const bool on = p.counted && p.stage_at;
+    const bool on = (p.counted || p.ens.counted) && p.stage_at;
     out4[0] = on ? p.stage_cap : 0;
     out4[1] = on ? p.stage_chunk : 0;
     out4[2] = on ? slg::plan_staged_items(p, h->st) : 0;

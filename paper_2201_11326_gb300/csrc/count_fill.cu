@@ -75,13 +75,6 @@ __device__ __forceinline__ int table_add(int32_t* keys, int32_t* cnts, uint32_t 
 // Several thresholds in one counting launch (an ensemble, Algorithm 3): the
 // counting pass counts every list's partners. (Each list is then filled by
 // the single-threshold kernels.)
-struct EnsArgs {
-    int32_t k = 0;                   // number of lists (0: one threshold, from RowS)
-    int32_t s[ENS_MAX] = {};         // thresholds, strictly ascending
-    uint32_t bias[ENS_MAX] = {};     // 0x01010101 * (128 - min(s[t], 128)), see below
-    int32_t* icnt = nullptr;         // per-item counts of list t at [t * stride]
-    int64_t stride = 0;
-};
 
 // ============================================================ MODE_WARP
 
@@ -1021,33 +1014,50 @@ constexpr unsigned ENS_PER_LIST = ALL_MODES & ~ENS_FUSED;
 // heads (zeroed, used once); err: the shared error flag. With `ea` (counting
 // pass only), the dense handlers run their ensemble form (every list in one
 // launch).
-// Staged items of [item_lo, item_hi) into place, one warp per item: pairs
-// at[q] .. at[q] + n - 1 of the pool go to ioff[q] - ioff[item_lo] onwards.
+// Staged items of [item_lo, item_hi) into place, one warp per item: the item's
+// staged pairs at[q] .. at[q] + n - 1 of the pool (n from the staged list's
+// offsets st_ioff) go, in order, to ioff[q] - ioff[item_lo] onwards.
 __global__ void k_place_staged(const Item* __restrict__ items, const int64_t* __restrict__ at,
+                               const int64_t* __restrict__ st_ioff,
                                const int64_t* __restrict__ ioff, int32_t item_lo, int32_t item_hi,
                                const int32_t* __restrict__ sJ, const uint8_t* __restrict__ sO,
                                RowS rs, int32_t* __restrict__ I, int32_t* __restrict__ J,
                                int32_t* __restrict__ O, int64_t limit, int32_t* __restrict__ err) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t o0 = ioff[item_lo];
     for (int64_t q = item_lo + warp; q < item_hi; q += nwarps) {
         const int64_t a = at[q];
         if (a < 0) continue;
-        const int64_t base = ioff[q] - o0, n = ioff[q + 1] - ioff[q];
+        const int64_t base = ioff[q] - o0, n = st_ioff[q + 1] - st_ioff[q];
         const int32_t i = items[q].row;
         const int32_t row = i - rs.base_of(i);
-        for (int64_t k = lane; k < n; k += 32) {
-            const int64_t p = base + k;
-            if (p < limit) {
-                I[p] = row;
-                J[p] = sJ[a + k];
-                O[p] = (int32_t)sO[a + k];
-            } else {
-                atomicOr(err, ERR_BOUNDS);
+        int64_t w = base;  // next output position (same in every lane)
+        for (int64_t k0 = 0; k0 < n; k0 += 32) {
+            const int64_t k = k0 + lane;
+            int32_t jv = 0, ov = 0;
+            if (k < n) {
+                jv = sJ[a + k];
+                ov = (int32_t)sO[a + k];
             }
+            const bool keep = k < n;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int64_t p = w + __popc(bal & lt);
+                if (p < limit) {
+                    I[p] = row;
+                    J[p] = jv;
+                    O[p] = ov;
+                } else {
+                    atomicOr(err, ERR_BOUNDS);
+                }
+            }
+            w += __popc(bal);
         }
+        // the kept pairs are exactly the item's count in the list
+        if (lane == 0 && w - base != ioff[q + 1] - ioff[q]) atomicOr(err, ERR_BOUNDS);
     }
 }
 
@@ -1207,15 +1217,15 @@ void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTim
 
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
-              cudaStream_t st, bool staged) {
+              cudaStream_t st, StageUse su) {
     if (item_hi <= item_lo) return;
     int32_t* sc = new_scratch(st);
     StageArgs skip{};
-    if (staged && p.stage_at && p.stage_cap > 0) {
+    if (su.st_ioff && p.stage_at && p.stage_cap > 0) {
         // staged items are copied into place; the fill kernels skip them
-        k_place_staged<<<152 * 16, 256, 0, st>>>(p.items, p.stage_at, ioff, item_lo, item_hi,
-                                                 p.stage_J, p.stage_O, rs, I, J, O, limit,
-                                                 sc + NMODES);
+        k_place_staged<<<152 * 16, 256, 0, st>>>(p.items, p.stage_at, su.st_ioff, ioff,
+                                                 item_lo, item_hi, p.stage_J, p.stage_O, rs, I, J,
+                                                 O, limit, sc + NMODES);
         SLG_LAUNCH_CHECK();
         skip.at = p.stage_at;
     }
@@ -1229,7 +1239,7 @@ void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStr
     const int64_t ni = p.nitems;
     int32_t* sc = new_scratch(st, NMODES * k);
     int32_t* err = sc + NMODES * k;
-    // warp-table and CTA-table handlers (sparse rows): one launch per threshold
+    // table and sparse handlers: one launch per threshold
     for (int32_t t = 0; t < k; ++t)
         launch_items<false>(g, p, p.rs_for(p.ens.s[t]), 0, (int32_t)ni, p.ens.icnt + t * ni,
                             nullptr, nullptr, nullptr, nullptr, 0, sc + NMODES * t, err, mt, st,

@@ -629,7 +629,9 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                         // counted once per warp and step)
                         const int32_t tend = (total + 31) & ~31;
                         for (int32_t t = tid; t < tend; t += NT) {
-                            if (ovf) break;
+                            // another warp may set the flag at any time: the warp
+                            // decides together, so the ballots below see every lane
+                            if (__any_sync(0xffffffffu, ovf != 0)) break;
                             int rr = 0;
                             if (t < total) {
                                 int32_t x = 0, z = NT - 1;  // largest x with pre[x] <= t

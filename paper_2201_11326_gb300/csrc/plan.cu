@@ -445,6 +445,7 @@ void Plan::release_stage(cudaStream_t st) {
     dfree(stage_O, st);
     dfree(stage_cursor, st);
     stage_cap = 0;
+    stage_s = -1;
 }
 
 void Plan::release(cudaStream_t st) {

@@ -94,6 +94,16 @@ void launch_gather_offsets(const int64_t* rowoff, const int32_t* row_base_dev, i
 
 // Everything derived for one s. Items and offsets are valid once built;
 // icnt/ioff/rowoff once `counted`.
+// The thresholds of an ensemble counted in one pass (Algorithm 3): list t
+// holds the pairs with overlap >= s[t]; k = 0 for a single threshold.
+struct EnsArgs {
+    int32_t k = 0;                   // number of lists (0: one threshold, from RowS)
+    int32_t s[ENS_MAX] = {};         // thresholds, strictly ascending
+    uint32_t bias[ENS_MAX] = {};     // 0x01010101 * (128 - min(s[t], 128)) (byte-wise compares)
+    int32_t* icnt = nullptr;         // per-item counts of list t at [t * stride]
+    int64_t stride = 0;
+};
+
 // A staging pool for the counting pass: the sparse-accumulator and hub-pair
 // fill kernels, run as the counting pass, write each item's pairs (in order)
 // into per-CTA chunks of the pool as well as its count; an item whose pairs
@@ -169,6 +179,7 @@ struct Plan {
     unsigned long long* stage_cursor = nullptr;
     int64_t stage_cap = 0;
     int64_t stage_chunk = SG_CHUNK;
+    int32_t stage_s = -1;  // the threshold whose list the last counting pass staged
     StageArgs stage_args() const {
         return StageArgs{stage_J, stage_O, stage_cap, stage_cursor, stage_at, stage_chunk,
                          stage_chunk / 32};
@@ -207,11 +218,16 @@ void ensemble_count(const GraphDev& g, Plan& p, const int32_t* s, int32_t k, Mod
 // and ioff the matching per-item counts and offsets.
 void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTimer* mt,
                cudaStream_t st);
-// staged: the plan's staging (run_count staged items of this list) is used:
-// staged items are copied into place and the fill kernels skip them.
+// Staged items of a list: the pool's per-item counts come from st_ioff (the
+// list's item offsets; null: nothing of this list is staged).
+struct StageUse {
+    const int64_t* st_ioff = nullptr;
+};
+// Staged items (see StageUse) are copied into place and the fill kernels skip
+// them.
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
-              cudaStream_t st, bool staged = false);
+              cudaStream_t st, StageUse su = StageUse{});
 // Ensemble counting pass over the plan's items (p.ens.k lists, thresholds
 // p.ens.s): counts into p.ens.icnt. Lists are filled one at a time by run_fill.
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st);

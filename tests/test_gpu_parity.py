@@ -630,3 +630,4 @@ def test_staged_counting_pass(handler, pool):
             slg.slg_set_staging(g, -2)
     finally:
         g.free()
+
