@@ -1066,7 +1066,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
                   int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
                   int64_t limit, int32_t* queue, int32_t* err, ModeTimer* mt, cudaStream_t st,
                   unsigned modes = ALL_MODES, const EnsArgs* ea = nullptr,
-                  const StageArgs& sa = StageArgs{}) {
+                  const StageArgs& sa = StageArgs{}, const EnsArgs* ens4 = nullptr) {
     Occupancy& oc = occupancy();
     const bool timed = mt && mt->on;
     const int pass = FILL && sa.J == nullptr ? 1 : 0;  // staging fills count as counting
@@ -1134,7 +1134,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         ran[MODE_SPARSE] = true;
         tick(MODE_SPARSE, 0);
         launch_sparse(FILL, oc.sparse_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J, O,
-                      queue + MODE_SPARSE, limit, err, st, sa);
+                      queue + MODE_SPARSE, limit, err, st, sa, ens4);
         tick(MODE_SPARSE, 1);
     }
     if (want(MODE_WSPARSE)) {
@@ -1148,7 +1148,7 @@ void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, in
         ran[MODE_HUBPAIR] = true;
         tick(MODE_HUBPAIR, 0);
         launch_hubpair(FILL, oc.hubpair_ctas[FILL], g, p, rs, item_lo, item_hi, icnt, ioff, I, J,
-                       O, queue + MODE_HUBPAIR, limit, err, st, sa);
+                       O, queue + MODE_HUBPAIR, limit, err, st, sa, ens4);
         tick(MODE_HUBPAIR, 1);
     }
     if (timed) {
@@ -1239,18 +1239,32 @@ void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStr
     const int64_t ni = p.nitems;
     int32_t* sc = new_scratch(st, NMODES * k);
     int32_t* err = sc + NMODES * k;
-    // table and sparse handlers: one launch per threshold
-    for (int32_t t = 0; t < k; ++t)
-        launch_items<false>(g, p, p.rs_for(p.ens.s[t]), 0, (int32_t)ni, p.ens.icnt + t * ni,
-                            nullptr, nullptr, nullptr, nullptr, 0, sc + NMODES * t, err, mt, st,
-                            ENS_PER_LIST);
-    // dense handlers: every threshold in one launch
     EnsArgs ea = ens_args(p);
     ea.icnt = p.ens.icnt;
     ea.stride = ni;
+    // sparse-accumulator and hub-pair rows, up to four lists: every list in one
+    // walk (their counting kernels take the thresholds from device memory)
+    constexpr unsigned ONE_WALK = (1u << MODE_SPARSE) | (1u << MODE_HUBPAIR);
+    unsigned per_list = ENS_PER_LIST;
+    EnsArgs* ea_dev = nullptr;
+    if (k <= 4) {
+        ea_dev = dalloc<EnsArgs>(1, st);
+        SLG_CUDA_TRY(cudaMemcpyAsync(ea_dev, &ea, sizeof(EnsArgs), cudaMemcpyHostToDevice, st));
+        launch_items<false>(g, p, p.rs_for(p.ens.s[0]), 0, (int32_t)ni, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, 0, sc, err, mt, st, ONE_WALK, nullptr, StageArgs{},
+                            ea_dev);
+        per_list &= ~ONE_WALK;
+    }
+    // table (and otherwise sparse) handlers: one launch per threshold
+    for (int32_t t = 0; t < k; ++t)
+        launch_items<false>(g, p, p.rs_for(p.ens.s[t]), 0, (int32_t)ni, p.ens.icnt + t * ni,
+                            nullptr, nullptr, nullptr, nullptr, 0, sc + NMODES * t, err, mt, st,
+                            per_list);
+    // dense handlers: every threshold in one launch
     launch_items<false>(g, p, p.rs_for(p.ens.s[0]), 0, (int32_t)ni, nullptr, nullptr, nullptr,
                         nullptr, nullptr, 0, sc, err, mt, st, ENS_FUSED, &ea);
     check_scratch(sc, st, "ensemble counting pass", NMODES * k);
+    dfree(ea_dev, st);
 }
 
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,

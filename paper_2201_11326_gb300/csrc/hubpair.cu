@@ -425,7 +425,9 @@ __device__ __forceinline__ int32_t gallop_to(const int32_t* __restrict__ src, in
 // One CTA takes a row (it claims the row's first item and walks all of the
 // row's items in this launch in order, so each range keeps a cursor at the
 // first entry of the next slice and only the slice's end is searched).
-template <bool FILL>
+// ENS4: the counting pass of an ensemble of at most four lists (*eap, in device
+// memory): every list counted in the one walk.
+template <bool FILL, bool ENS4 = false>
 __global__ void __launch_bounds__(HP_THREADS, 3)
 k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
@@ -439,7 +441,8 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
                 int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
                 int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err,
-                int32_t* __restrict__ scratch, StageArgs sa) {
+                int32_t* __restrict__ scratch, StageArgs sa, const EnsArgs* __restrict__ eap) {
+    static_assert(!(FILL && ENS4), "an ensemble's lists are counted here, filled one at a time");
     constexpr int NT = HP_THREADS;
     const bool stg = FILL && sa.J != nullptr;  // the counting pass, staging pairs
     int32_t* cur = scratch + (int64_t)blockIdx.x * HP_SCRATCH_WORDS;  // first entry of the next slice
@@ -561,6 +564,13 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
             const int64_t obase = !FILL ? 0 : stg ? (int64_t)sh_cpos : ioff[qq] - ioff[item_lo];
             const int64_t olimit = stg ? (int64_t)sh_cend : limit;
             int64_t out_pos = 0;  // same value in every thread
+            // ENS4: this thread's survivors of each list in the item so far, and
+            // the thresholds (a list beyond the ensemble never counts)
+            int32_t en0 = 0, en1 = 0, en2 = 0, en3 = 0;
+            const uint32_t es0 = ENS4 ? (uint32_t)eap->s[0] : 0u;
+            const uint32_t es1 = ENS4 && eap->k > 1 ? (uint32_t)eap->s[1] : 0xffffffffu;
+            const uint32_t es2 = ENS4 && eap->k > 2 ? (uint32_t)eap->s[2] : 0xffffffffu;
+            const uint32_t es3 = ENS4 && eap->k > 3 ? (uint32_t)eap->s[3] : 0xffffffffu;
             if (tid == 0) {
                 sh_n = 1;
                 stk_a[0] = it.jlo;
@@ -792,6 +802,13 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 for (int r = 0; r < HP_SLOTS_PER_THREAD; ++r) {
                     const int slot = r * NT + tid;
                     mine += cnts[slot] > 0u ? 1 : 0;
+                    if (ENS4) {  // a survivor's count is its overlap (>= the first threshold)
+                        const uint32_t ov = cnts[slot];
+                        en0 += ov > 0u && ov >= es0 ? 1 : 0;
+                        en1 += ov >= es1 ? 1 : 0;
+                        en2 += ov >= es2 ? 1 : 0;
+                        en3 += ov >= es3 ? 1 : 0;
+                    }
                     if (!FILL && keys[slot] != HP_EMPTY) {  // the counting pass clears as it reads
                         keys[slot] = HP_EMPTY;
                         cnts[slot] = 0u;
@@ -919,7 +936,19 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
                 }
                 out_pos += c;
             }
-            if (!FILL && tid == 0) icnt[qq] = (int32_t)out_pos;
+            if (ENS4) {
+                int32_t t0c = 0, t1c = 0, t2c = 0, t3c = 0;
+                block_excl_scan<NT>(en0, &t0c, tmp);
+                block_excl_scan<NT>(en1, &t1c, tmp);
+                block_excl_scan<NT>(en2, &t2c, tmp);
+                block_excl_scan<NT>(en3, &t3c, tmp);
+                if (tid == 0) {
+                    const int32_t tc[4] = {t0c, t1c, t2c, t3c};
+                    for (int32_t t = 0; t < eap->k; ++t) eap->icnt[t * eap->stride + qq] = tc[t];
+                }
+            } else if (!FILL && tid == 0) {
+                icnt[qq] = (int32_t)out_pos;
+            }
             if (stg && tid == 0) {
                 icnt[qq] = (int32_t)out_pos;
                 if (!sh_sovf) {
@@ -935,6 +964,8 @@ k_hubpair_items(const Item* __restrict__ items, const int32_t* __restrict__ list
 }  // namespace
 
 void hubpair_setup(int sms, int ctas[2]) {
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_hubpair_items<false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HP_SMEM));
     for (int f = 0; f < 2; ++f) {
         auto kern = f ? k_hubpair_items<true> : k_hubpair_items<false>;
         SLG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -948,7 +979,7 @@ void hubpair_setup(int sms, int ctas[2]) {
 void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                     int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                    int32_t* err, cudaStream_t st, const StageArgs& sa) {
+                    int32_t* err, cudaStream_t st, const StageArgs& sa, const EnsArgs* ens4) {
     const HubPairs& hp = *p.hp;
     int32_t* scratch = dalloc<int32_t>((size_t)ctas * HP_SCRATCH_WORDS, st);
     if (fill)
@@ -956,13 +987,19 @@ void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
             hp.bigbits, hp.hrec, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err, scratch, sa);
+            limit, err, scratch, sa, nullptr);
+    else if (ens4)
+        k_hubpair_items<false, true><<<ctas, HP_THREADS, HP_SMEM, st>>>(
+            p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
+            g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
+            hp.bigbits, hp.hrec, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
+            limit, err, scratch, StageArgs{}, ens4);
     else
         k_hubpair_items<false><<<ctas, HP_THREADS, HP_SMEM, st>>>(
             p.items, p.mode_list[MODE_HUBPAIR], p.mode_rank[MODE_HUBPAIR], item_lo, item_hi,
             g.off, g.idx, p.wbeg, p.wend, p.idxTs, hp.hp_id, hp.hoff, hp.hlist, hp.bigidx,
             hp.bigbits, hp.hrec, hp.bigk, hp.off2, p.wbeg2, p.wend2, p.idxT2s, rs, icnt, ioff, I, J, O, queue,
-            limit, err, scratch, StageArgs{});
+            limit, err, scratch, StageArgs{}, nullptr);
     SLG_LAUNCH_CHECK();
     dfree(scratch, st);
 }

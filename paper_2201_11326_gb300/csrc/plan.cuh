@@ -242,7 +242,8 @@ void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                   int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{});
+                   int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{},
+                   const EnsArgs* ens4 = nullptr);
 // Per-handler totals over rows (needs counts): rows, wedges, incidences, pairs,
 // non-hub wedges, partners scanned by the dense extraction (count, fill).
 constexpr int MS_COLS = 7;
@@ -256,7 +257,8 @@ void hubpair_setup(int sms, int ctas[2]);
 void launch_hubpair(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                     int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                     int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                    int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{});
+                    int32_t* err, cudaStream_t st, const StageArgs& sa = StageArgs{},
+                    const EnsArgs* ens4 = nullptr);
 // Digest of a filled window (rows [r0, r1), pairs at I/J/O[0..P)).
 void run_digest(RowS rs, const int64_t* rowoff, int32_t r0, int32_t r1, const int32_t* I,
                 const int32_t* J, const int32_t* O, int64_t P, unsigned long long* total_dev,

@@ -48,7 +48,9 @@ constexpr size_t sp_smem(bool fill) {
            (fill ? sizeof(uint32_t) * 2 * SP_BITS : 0);
 }
 
-template <bool FILL>
+// ENS4: the counting pass of an ensemble of at most four lists (*eap, in device
+// memory): every list counted in the one walk.
+template <bool FILL, bool ENS4 = false>
 __global__ void __launch_bounds__(SP_THREADS, 2)
 k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                const int32_t* __restrict__ rank, int32_t item_lo, int32_t item_hi,
@@ -57,7 +59,8 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                int32_t* __restrict__ icnt, const int64_t* __restrict__ ioff,
                int32_t* __restrict__ I, int32_t* __restrict__ J, int32_t* __restrict__ O,
                int32_t* __restrict__ queue, int64_t limit, int32_t* __restrict__ err,
-               StageArgs sa) {
+               StageArgs sa, const EnsArgs* __restrict__ eap) {
+    static_assert(!(FILL && ENS4), "an ensemble's lists are counted here, filled one at a time");
     extern __shared__ __align__(16) uint32_t dyn[];
     uint32_t* ctr = dyn;                                                   // SP_WORDS
     uint16_t* touched = reinterpret_cast<uint16_t*>(ctr + SP_WORDS);      // SP_TOUCH
@@ -137,6 +140,13 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
         const int64_t olimit = stg ? (int64_t)sh_cend : limit;
         int64_t out_pos = 0;   // fill: the item's pairs before the tile (same in every thread)
         int32_t my_count = 0;  // counting pass: this thread's survivors so far
+        // ENS4: this thread's survivors of each list so far, and the thresholds
+        // (a list beyond the ensemble never counts)
+        int32_t en0 = 0, en1 = 0, en2 = 0, en3 = 0;
+        const int32_t es0 = ENS4 ? eap->s[0] : 0;
+        const int32_t es1 = ENS4 && eap->k > 1 ? eap->s[1] : INT32_MAX;
+        const int32_t es2 = ENS4 && eap->k > 2 ? eap->s[2] : INT32_MAX;
+        const int32_t es3 = ENS4 && eap->k > 3 ? eap->s[3] : INT32_MAX;
         __syncthreads();
         const int32_t nr = min(sh_n, SP_MAXR);
         // pieces per range, from its density: entries per id times the tile width
@@ -225,7 +235,15 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         const int32_t slot = touched[x];
                         const int sh = (slot & 3) << 3;
                         const uint32_t old = atomicAnd(&ctr[slot >> 2], ~(0xffu << sh));
-                        my_count += ((int32_t)((old >> sh) & 0xffu) >= s) ? 1 : 0;
+                        const int32_t c = (int32_t)((old >> sh) & 0xffu);
+                        if (ENS4) {
+                            en0 += c >= es0 ? 1 : 0;
+                            en1 += c >= es1 ? 1 : 0;
+                            en2 += c >= es2 ? 1 : 0;
+                            en3 += c >= es3 ? 1 : 0;
+                        } else {
+                            my_count += c >= s ? 1 : 0;
+                        }
                     }
                 } else {
                     for (int32_t w = tid; w < nwords; w += SP_THREADS) {
@@ -233,8 +251,17 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                         if (!v) continue;
                         ctr[w] = 0;
 #pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            my_count += ((int32_t)((v >> (8 * r)) & 0xffu) >= s) ? 1 : 0;
+                        for (int r = 0; r < 4; ++r) {
+                            const int32_t c = (int32_t)((v >> (8 * r)) & 0xffu);
+                            if (ENS4) {
+                                en0 += c >= es0 ? 1 : 0;
+                                en1 += c >= es1 ? 1 : 0;
+                                en2 += c >= es2 ? 1 : 0;
+                                en3 += c >= es3 ? 1 : 0;
+                            } else {
+                                my_count += c >= s ? 1 : 0;
+                            }
+                        }
                     }
                 }
                 __syncthreads();  // the touched list is refilled by the next tile
@@ -343,7 +370,17 @@ k_sparse_items(const Item* __restrict__ items, const int32_t* __restrict__ list,
                 for (int32_t w = tid; w < SP_BITS; w += SP_THREADS) bm[w] = 0;
             // (the next tile's bitmap writes follow its first barrier)
         }
-        if (!FILL) {
+        if (!FILL && ENS4) {
+            int32_t t0c = 0, t1c = 0, t2c = 0, t3c = 0;
+            block_excl_scan<SP_THREADS>(en0, &t0c, tmp);
+            block_excl_scan<SP_THREADS>(en1, &t1c, tmp);
+            block_excl_scan<SP_THREADS>(en2, &t2c, tmp);
+            block_excl_scan<SP_THREADS>(en3, &t3c, tmp);
+            if (tid == 0) {
+                const int32_t tc[4] = {t0c, t1c, t2c, t3c};
+                for (int32_t t = 0; t < eap->k; ++t) eap->icnt[t * eap->stride + q] = tc[t];
+            }
+        } else if (!FILL) {
             int32_t total = 0;
             block_excl_scan<SP_THREADS>(my_count, &total, tmp);
             if (tid == 0) icnt[q] = total;
@@ -671,6 +708,9 @@ void sparse_setup(int sms, int ctas[2]) {
         SLG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, kern, SP_THREADS, smem));
         ctas[f] = sms * (d > 0 ? d : 1);
     }
+    SLG_CUDA_TRY(cudaFuncSetAttribute(k_sparse_items<false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sp_smem(false)));
 }
 
 void wsparse_setup(int sms, int ctas[2]) {
@@ -702,15 +742,20 @@ void launch_wsparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS 
 void launch_sparse(bool fill, int ctas, const GraphDev& g, const Plan& p, RowS rs,
                    int32_t item_lo, int32_t item_hi, int32_t* icnt, const int64_t* ioff,
                    int32_t* I, int32_t* J, int32_t* O, int32_t* queue, int64_t limit,
-                   int32_t* err, cudaStream_t st, const StageArgs& sa) {
+                   int32_t* err, cudaStream_t st, const StageArgs& sa, const EnsArgs* ens4) {
     if (fill)
         k_sparse_items<true><<<ctas, SP_THREADS, sp_smem(true), st>>>(
             p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, sa);
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, sa, nullptr);
+    else if (ens4)
+        k_sparse_items<false, true><<<ctas, SP_THREADS, sp_smem(false), st>>>(
+            p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, StageArgs{}, ens4);
     else
         k_sparse_items<false><<<ctas, SP_THREADS, sp_smem(false), st>>>(
             p.items, p.mode_list[MODE_SPARSE], p.mode_rank[MODE_SPARSE], item_lo, item_hi, g.off,
-            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, StageArgs{});
+            p.wbeg, p.wend, p.idxTs, rs, icnt, ioff, I, J, O, queue, limit, err, StageArgs{},
+            nullptr);
     SLG_LAUNCH_CHECK();
 }
 

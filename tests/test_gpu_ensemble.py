@@ -266,3 +266,44 @@ def test_ensemble_rejects_bad_lists():
     finally:
         b.free()
         g1.free()
+
+
+@pytest.mark.parametrize("handler", ["hubpair", "sparse"])
+def test_ensemble_one_walk_large_recipe(handler):
+    # up to four lists: the sparse-accumulator and hub-pair rows are walked once
+    # for every list (one counting launch each), the other handlers per list
+    h = synth.large(m=20000)
+    s_list = [2, 3, 5, 8]
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    mode = slg.MODE_NAMES.index(handler)
+    try:
+        if handler == "hubpair":
+            slg.slg_set_bins(g, *FORCED["block_only"])
+            slg.slg_set_hub_pairs(g, 512, 0)
+        else:
+            slg.slg_set_bins(g, *FORCED["sparse_cta_only"])
+            slg.slg_set_hub_pairs(g, 0, 0)
+        slg.slg_set_timing(g, True)
+        slg.slg_kernel_stats(g, reset=True)
+        pairs, _ = slg.slg_ensemble_count(g, s_list)
+        assert slg.slg_kernel_stats(g)[1][0][mode] == 1
+        assert slg.slg_ensemble_mode_stats(g, s_list, 0)[mode][0] > 0
+        counts, digs, _ = oracle.rows(h.off, h.idx, None, s_list)
+        assert pairs == [int(x) for x in counts.sum(axis=0)]
+        for s, got in zip(s_list, slg.slg_ensemble_build(g, s_list)):
+            assert_same(got, oracle_list("large20000", h, s), f"{handler} s={s}")
+        for t in range(len(s_list)):
+            cap = max(int(counts[:, t].max()), int(counts[:, t].sum()) // 3 + 1)
+            I, J, O = (np.zeros(cap, np.int32) for _ in range(3))
+            splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                rd = np.zeros(r1 - r0, np.uint64)
+                slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap=cap,
+                                              digest=True, row_digests=rd, which=t)
+                assert np.array_equal(rd, digs[r0:r1, t]), (handler, t, r0)
+        # five lists go back to one launch per list
+        slg.slg_kernel_stats(g, reset=True)
+        slg.slg_ensemble_count(g, [2, 3, 5, 8, 13])
+        assert slg.slg_kernel_stats(g)[1][0][mode] == 5
+    finally:
+        g.free()

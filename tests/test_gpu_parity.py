@@ -631,3 +631,4 @@ def test_staged_counting_pass(handler, pool):
     finally:
         g.free()
 
+
