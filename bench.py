@@ -60,8 +60,7 @@ def parse_args():
                     default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
     ap.add_argument("--sweep", choices=["ensemble", "per_s"], default=None,
-                    help="medium: the s sweep as one ensemble (default) or one s at a time; "
-                         "large: one s at a time (default)")
+                    help="the s sweep as one ensemble (default) or one s at a time")
     ap.add_argument("--queries", type=int, default=1000, help="serve workload: queries per rate")
     ap.add_argument("--degree-cap", type=int, default=100_000,
                     help="large workload: cap on the Chung-Lu target degree (scale it with --m "
@@ -250,7 +249,7 @@ def bench_ours(args):
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
     h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
-    sweep = args.sweep or ("per_s" if args.workload == "large" else "ensemble")
+    sweep = args.sweep or "ensemble"
     # inputs resident in HBM before the timed region
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)
