@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
     ap.add_argument("--sweep", choices=["ensemble", "per_s"], default=None,
                     help="the s sweep as one ensemble (default) or one s at a time")
+    ap.add_argument("--ens-windows", choices=["per_list", "all"], default=None,
+                    help="ensemble sweep: each list in its own windows (medium default), or "
+                         "windows of every list, the later lists filtered from the one before "
+                         "where that reads less (large default)")
     ap.add_argument("--queries", type=int, default=1000, help="serve workload: queries per rate")
     ap.add_argument("--degree-cap", type=int, default=100_000,
                     help="large workload: cap on the Chung-Lu target degree (scale it with --m "
@@ -204,10 +208,14 @@ def run_sweep(slg, g, s_list, bufs, stream, per_s, mode_work=None):
         d["ms"].append(e0.elapsed_time(e1))
 
 
-def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None):
+def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None,
+                       all_lists=False):
     """The s sweep as one ensemble (Algorithm 3): one plan for min(s) and one
-    counting pass for every list, then each list's windows. Per s: its fill time,
-    with the shared counting pass recorded once."""
+    counting pass for every list, then each list's windows (per s: its fill time),
+    or windows holding every list (all_lists: the later lists filtered from the
+    one before where that reads less; per s: its share of the fill time, in
+    proportion to its pairs). The shared counting pass is charged to the lists in
+    equal parts."""
     import torch
     I, J, O = bufs
     cap = I.numel()
@@ -218,20 +226,29 @@ def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=No
     if mode_work is not None:
         for t, s in enumerate(s_list):
             mode_work[s] = slg.slg_ensemble_mode_stats(g, s_list, t)
-    for t, s in enumerate(s_list):
-        splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+    if all_lists:
+        splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=slg.ENSEMBLE_ALL)
         for r0, r1 in zip(splits[:-1], splits[1:]):
-            slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap, which=t)
-        ev[t + 2].record(stream)
+            slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap,
+                                          which=slg.ENSEMBLE_ALL)
+        ev[-1].record(stream)
+    else:
+        for t, s in enumerate(s_list):
+            splits = slg.slg_ensemble_plan_windows(g, s_list, cap, which=t)
+            for r0, r1 in zip(splits[:-1], splits[1:]):
+                slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap, which=t)
+            ev[t + 2].record(stream)
     ev[-1].synchronize()
     count_ms = ev[0].elapsed_time(ev[1])
+    fill_all = ev[1].elapsed_time(ev[-1])
+    ptot = max(sum(pairs), 1)
     for t, s in enumerate(s_list):
         d = per_s.setdefault(s, {"s": s, "wedges": wedges[s], "pairs": pairs[t], "ms": [],
                                  "fill_ms": [], "count_ms_shared": []})
-        fill = ev[t + 1].elapsed_time(ev[t + 2])
+        fill = (fill_all * pairs[t] / ptot if all_lists
+                else ev[t + 1].elapsed_time(ev[t + 2]))
         d["fill_ms"].append(fill)
         d["count_ms_shared"].append(count_ms)
-        # the shared counting pass is charged to the lists in equal parts
         d["ms"].append(fill + count_ms / len(s_list))
 
 
@@ -250,6 +267,7 @@ def bench_ours(args):
     dev = torch.cuda.current_device()
     h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
     sweep = args.sweep or "ensemble"
+    ens_all = (args.ens_windows or ("all" if args.workload == "large" else "per_list")) == "all"
     # inputs resident in HBM before the timed region
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)
@@ -274,7 +292,8 @@ def bench_ours(args):
             if timing:
                 slg.slg_set_timing(g, True)
             if sweep == "ensemble":
-                run_sweep_ensemble(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work)
+                run_sweep_ensemble(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work,
+                                   all_lists=ens_all)
             else:
                 run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
@@ -429,6 +448,10 @@ def bench_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": wl_text, "sweep": sweep,
+                   "ensemble_windows": (("all lists per window, later lists filtered from the "
+                                         "one before where that reads less") if ens_all else
+                                        "each list in its own windows") if sweep == "ensemble"
+                   else None,
                    "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": args.window,
                    "l2": "flushed before each step (512 MiB device write); inputs resident",
                    "parallelism": f"replicas x{world}"},

@@ -539,6 +539,21 @@ slg_status slg_set_bins(slg_graph* g, int32_t warp_max_wedges, int32_t block_ite
 slg_status slg_set_hub_pairs(slg_graph* g, int32_t max_hubs, int64_t min_sparse_wedges);
 
 /*
+ * slg_set_ensemble_filter -- how slg_ensemble_build_window with which =
+ * SLG_ENSEMBLE_ALL produces the lists after the first.
+ *
+ * Algorithm 3's lists are nested and in the same (i, j) order, so list t holds
+ * exactly the pairs of list t-1 with overlap >= s_list[t]. In a window holding
+ * every list, list t can be taken from list t-1's segment by a filter (12
+ * bytes read per pair of list t-1) instead of walking the window's rows again.
+ *   mode : -1 (default) whichever reads less: the filter when 6 * (pairs of list
+ *          t-1 in the window) < wedges of the window's rows; 0 always walk; 1
+ *          always filter.
+ * The lists are the same either way.
+ */
+slg_status slg_set_ensemble_filter(slg_graph* g, int32_t mode);
+
+/*
  * slg_set_staging -- one walk instead of two for the sparse-accumulator and
  * hub-pair rows.
  *

@@ -670,11 +670,31 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
     // each selected list from the shared plan with its own threshold, into its
     // segment (one fused pass over all lists was measured slower: the lists
     // after the first went out as partial-line stores)
+    // A list after the first in the window may instead be the list before it
+    // filtered by its threshold (the lists are nested and in the same order):
+    // that reads 12 bytes per pair of the list before, a walk about 4 per wedge of
+    // the window's rows, so the filter is taken when 6 * pairs < wedges (or as
+    // slg_set_ensemble_filter says)
+    int64_t wrows = -1;
     for (int32_t t = t0; t < t1; ++t) {
         const int32_t u = t - t0;
-        slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
-                      dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], &h->mtimer,
-                      h->st);
+        bool filt = false;
+        if (t > t0 && h->ens_filter != 0) {
+            if (h->ens_filter > 0) {
+                filt = true;
+            } else {
+                if (wrows < 0) wrows = slg::plan_row_wedges(h->g, p, r0, r1, h->st);
+                filt = 6 * (seg[u] - seg[u - 1]) < wrows;
+            }
+        }
+        if (filt)
+            slg::run_filter(dI + seg[u - 1], dJ + seg[u - 1], dO + seg[u - 1], seg[u] - seg[u - 1],
+                            p.ens.s[t], dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u],
+                            h->st);
+        else
+            slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
+                          dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], &h->mtimer,
+                          h->st);
     }
     h->timer.mark(4, h->st);
     if (dd) {
@@ -799,6 +819,14 @@ slg_status slg_set_hub_pairs(slg_graph* h, int32_t max_hubs, int64_t min_sparse_
     h->hp_max_hubs = max_hubs;
     h->hp_min_wedges = min_sparse_wedges;
     API_END
+}
+
+slg_status slg_set_ensemble_filter(slg_graph* h, int32_t mode) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    if (mode < -1 || mode > 1) return fail(SLG_EINVAL, "mode must be -1 (automatic), 0 or 1");
+    h->ens_filter = mode;
+    slg::g_last_error.clear();
+    return SLG_OK;
 }
 
 slg_status slg_set_staging(slg_graph* h, int64_t max_bytes) {

@@ -1061,6 +1061,78 @@ __global__ void k_place_staged(const Item* __restrict__ items, const int64_t* __
     }
 }
 
+// A list of an ensemble from the list before it: the lists are nested and in
+// the same (i, j) order, so list t is list t-1's pairs with overlap >= s, in
+// order. Blocks of FT_N = 4096 pairs: counted, scanned, then written.
+constexpr int FT_THREADS = 256;
+constexpr int FT_STEPS = 16;
+constexpr int64_t FT_N = (int64_t)FT_THREADS * FT_STEPS;
+
+__global__ void k_filter_count(const int32_t* __restrict__ O, int64_t n, int32_t s,
+                               int32_t* __restrict__ counts) {
+    __shared__ int32_t wsum[FT_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * FT_N;
+    int32_t c = 0;
+#pragma unroll
+    for (int u = 0; u < FT_STEPS; ++u) {
+        const int64_t x = base + u * FT_THREADS + tid;
+        c += (x < n && O[x] >= s) ? 1 : 0;
+    }
+    c = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)c);
+    if (lane == 0) wsum[warp] = c;
+    __syncthreads();
+    if (tid == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < FT_THREADS / 32; ++w) t += wsum[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_filter_write(const int32_t* __restrict__ I, const int32_t* __restrict__ J,
+                               const int32_t* __restrict__ O, int64_t n, int32_t s,
+                               const int64_t* __restrict__ boff, int32_t* __restrict__ I2,
+                               int32_t* __restrict__ J2, int32_t* __restrict__ O2,
+                               int64_t limit, int32_t* __restrict__ err) {
+    constexpr int NW = FT_THREADS / 32;
+    __shared__ int32_t at[FT_STEPS][NW];  // kept pairs before (step, warp), in pair order
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * FT_N;
+    unsigned bal[FT_STEPS];
+#pragma unroll
+    for (int u = 0; u < FT_STEPS; ++u) {
+        const int64_t x = base + u * FT_THREADS + tid;
+        bal[u] = __ballot_sync(0xffffffffu, x < n && O[x] >= s);
+        if (lane == 0) at[u][warp] = __popc(bal[u]);
+    }
+    __syncthreads();
+    if (tid == 0) {  // pair order is step-major, then warp
+        int32_t run = 0;
+        for (int u = 0; u < FT_STEPS; ++u)
+            for (int w = 0; w < NW; ++w) {
+                const int32_t v = at[u][w];
+                at[u][w] = run;
+                run += v;
+            }
+    }
+    __syncthreads();
+    const int64_t o0 = boff[blockIdx.x];
+#pragma unroll
+    for (int u = 0; u < FT_STEPS; ++u) {
+        if (!((bal[u] >> lane) & 1u)) continue;
+        const int64_t x = base + u * FT_THREADS + tid;
+        const int64_t p = o0 + at[u][warp] + __popc(bal[u] & lt);
+        if (p < limit) {
+            I2[p] = I[x];
+            J2[p] = J[x];
+            O2[p] = O[x];
+        } else {
+            atomicOr(err, ERR_BOUNDS);
+        }
+    }
+}
+
 template <bool FILL>
 void launch_items(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
                   int32_t* icnt, const int64_t* ioff, int32_t* I, int32_t* J, int32_t* O,
@@ -1232,6 +1304,30 @@ void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, in
     launch_items<true>(g, p, rs, item_lo, item_hi, nullptr, ioff, I, J, O, limit, sc, sc + NMODES,
                        mt, st, ALL_MODES, nullptr, skip);
     check_scratch(sc, st, "fill pass");
+}
+
+void run_filter(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n, int32_t s,
+                int32_t* I2, int32_t* J2, int32_t* O2, int64_t expect, cudaStream_t st) {
+    if (n <= 0) {
+        if (expect != 0) throw Error{SLG_EINTERNAL, "list filter: pairs expected from nothing"};
+        return;
+    }
+    const int64_t nb = (n + FT_N - 1) / FT_N;
+    int32_t* counts = dalloc<int32_t>((size_t)nb, st);
+    int64_t* boff = dalloc<int64_t>((size_t)nb + 1, st);
+    int32_t* sc = new_scratch(st);
+    k_filter_count<<<(unsigned)nb, FT_THREADS, 0, st>>>(O, n, s, counts);
+    SLG_LAUNCH_CHECK();
+    scan_i32_to_i64(counts, boff, nb, st);
+    k_filter_write<<<(unsigned)nb, FT_THREADS, 0, st>>>(I, J, O, n, s, boff, I2, J2, O2, expect,
+                                                        sc + NMODES);
+    SLG_LAUNCH_CHECK();
+    int64_t got = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&got, boff + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    check_scratch(sc, st, "list filter");  // synchronises
+    dfree(counts, st);
+    dfree(boff, st);
+    if (got != expect) throw Error{SLG_EINTERNAL, "list filter: pair count differs from the count"};
 }
 
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st) {

@@ -42,6 +42,9 @@ struct slg_graph {
     // staging pool of the counting pass (slg::StageArgs): -1 automatic, 0 off,
     // > 0 at most this many bytes
     int64_t stage_max_bytes = -1;
+    // an ensemble's window of every list: list t from list t-1 by filtering (1),
+    // by walking its rows (0), or whichever reads less (-1)
+    int32_t ens_filter = -1;
 };
 
 namespace slg {

@@ -718,6 +718,32 @@ int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st) {
     return (int64_t)h;
 }
 
+namespace {
+__global__ void k_row_wedges(const int64_t* __restrict__ W, int32_t r0, int32_t r1,
+                             unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    for (int64_t r = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < r1;
+         r += (int64_t)gridDim.x * blockDim.x)
+        acc += (unsigned long long)W[r];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+}  // namespace
+
+int64_t plan_row_wedges(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, cudaStream_t st) {
+    if (r1 <= r0) return 0;
+    unsigned long long* d = dalloc<unsigned long long>(1, st);
+    SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    k_row_wedges<<<grid_for(r1 - r0, 256), 256, 0, st>>>(p.W, r0, r1, d);
+    SLG_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(d, st);
+    return (int64_t)h;
+}
+
 int64_t plan_stage_bound(const GraphDev& g, const Plan& p, cudaStream_t st) {
     unsigned long long* d = dalloc<unsigned long long>(1, st);
     SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));

@@ -307,3 +307,35 @@ def test_ensemble_one_walk_large_recipe(handler):
         assert slg.slg_kernel_stats(g)[1][0][mode] == 5
     finally:
         g.free()
+
+
+@pytest.mark.parametrize("mode", [-1, 0, 1])
+def test_ensemble_lists_filtered_from_the_one_before(mode):
+    # windows of every list: a later list walked, or filtered from the list before
+    # it (the lists are nested and in the same order); the same lists either way
+    h = synth.large(m=20000)
+    s_list = [2, 3, 5, 8]
+    counts, digs, _ = oracle.rows(h.off, h.idx, None, s_list)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        slg.slg_set_hub_pairs(g, 512, 0)
+        slg.slg_set_ensemble_filter(g, mode)
+        for s, got in zip(s_list, slg.slg_ensemble_build(g, s_list)):
+            assert_same(got, oracle_list("large20000", h, s), f"filter {mode} s={s}")
+        tot = counts.sum(axis=1)
+        cap = max(int(tot.max()), int(tot.sum()) // 4 + 1)
+        I, J, O = (np.zeros(cap, np.int32) for _ in range(3))
+        splits = slg.slg_ensemble_plan_windows(g, s_list, cap)
+        assert len(splits) > 2
+        for r0, r1 in zip(splits[:-1], splits[1:]):
+            nr = int(r1 - r0)
+            rd = np.zeros(len(s_list) * nr, np.uint64)
+            got, _ = slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, cap,
+                                                   digest=True, row_digests=rd)
+            assert got == [int(x) for x in counts[r0:r1].sum(axis=0)]
+            for t in range(len(s_list)):
+                assert np.array_equal(rd[t * nr:(t + 1) * nr], digs[r0:r1, t]), (mode, t, r0)
+        with pytest.raises(slg.SlgError):
+            slg.slg_set_ensemble_filter(g, 2)
+    finally:
+        g.free()
