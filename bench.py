@@ -297,12 +297,19 @@ def bench_ours(args):
             else:
                 run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
+            if timing and sweep == "ensemble":
+                made = slg.slg_ensemble_fill_stats(g)
+                for t, s in enumerate(s_list):
+                    acc = fill_made.setdefault(s, [0, 0, 0, 0])
+                    for c in range(4):
+                        acc[c] += int(made[t][c])
             g.free()
         return ks
 
     # per-handler work of the sweep (for the roofline's algorithmic bytes),
     # recorded during the last warm-up step (or the first timed one)
     mode_work = {}
+    fill_made = {}  # per s over the timed steps: windows/pairs walked, windows/pairs filtered
     for w in range(args.warmup):
         step({}, mode_work=mode_work if w == args.warmup - 1 else None)
 
@@ -356,34 +363,55 @@ def bench_ours(args):
                 ms_tot[p][k] += ms[p][k]
                 ln_tot[p][k] += ln[p][k]
 
-    def tot(col):
-        return [sum(mode_work[s][k][col] for s in s_list) for k in range(NM)]
-
-    w_mode, inc_mode, pairs_mode = tot(1), tot(2), tot(3)
-    nonhub_mode, scan_c_mode, scan_f_mode = tot(4), tot(5), tot(6)
     names = list(slg.MODE_NAMES)
+    # Which walks ran. Counting: an ensemble's dense handlers count every list in
+    # one walk, and so do its sparse-accumulator and hub-pair handlers for up to
+    # four lists; every other counting walk is one per list. Fill: list s is
+    # walked in the share of its windows that did not filter it from the list
+    # before (fill_made), and its fill kernels write the pairs of those windows.
+    def one_walk(k):
+        return sweep == "ensemble" and (names[k] in ("dense", "wdense") or (
+            names[k] in ("sparse", "hubpair") and len(s_list) <= 4))
+
+    walk_f, pair_f = {}, {}
+    for s in s_list:
+        m = fill_made.get(s)
+        wins = (m[0] + m[2]) if m else 0
+        walk_f[s] = m[0] / wins if wins else 1.0
+        made = (m[1] + m[3]) if m else 0
+        pair_f[s] = m[1] / made if made else 1.0
+
+    def walked(col, k, fill):
+        if not fill:
+            if one_walk(k):
+                return mode_work[s_list[0]][k][col]
+            return sum(mode_work[s][k][col] for s in s_list)
+        return sum(walk_f[s] * mode_work[s][k][col] for s in s_list)
+
+    def filled_pairs(k):
+        return sum(pair_f[s] * mode_work[s][k][3] for s in s_list)
+
     # candidates: (pass, mode, kernel bytes per step, ms per step, launches per step,
-    # section 8(d) model bytes per step)
+    # section 8(d) model bytes per step, pairs the kernel wrote per step)
     cands = []
-    shared = 1.0 / len(s_list) if sweep == "ensemble" else 1.0
     for k in range(NM):
-        model_c = 4 * w_mode[k] + 8 * inc_mode[k]
-        if names[k] in ("dense", "wdense"):
-            # what these kernels move: adj_s entries of non-hub wedges only, one
-            # 4-byte hub mask per candidate partner scanned, the row's wedge-range
-            # bounds; hub wedges are popcounts and read nothing. In an ensemble
-            # their counting pass is one launch for every list.
-            kern_c = shared * (4 * nonhub_mode[k] + 4 * scan_c_mode[k] + 8 * inc_mode[k])
-            kern_f = 4 * nonhub_mode[k] + 4 * scan_f_mode[k] + 8 * inc_mode[k]
-        elif names[k] == "hubpair":
-            # entries walked (non-hub wedges + hub-pair list hits) and their bounds
-            kern_c = kern_f = 4 * nonhub_mode[k] + 8 * inc_mode[k]
-        else:
-            kern_c = kern_f = model_c
-        cands.append(("count", k, kern_c, ms_tot[0][k] / args.steps, ln_tot[0][k] / args.steps,
-                      model_c))
-        cands.append(("fill", k, kern_f + 12 * pairs_mode[k], ms_tot[1][k] / args.steps,
-                      ln_tot[1][k] / args.steps, model_c + 12 * pairs_mode[k]))
+        for fill in (False, True):
+            w, inc, nonhub = walked(1, k, fill), walked(2, k, fill), walked(4, k, fill)
+            model = 4 * w + 8 * inc
+            if names[k] in ("dense", "wdense"):
+                # what these kernels move: adj_s entries of non-hub wedges only, one
+                # 4-byte hub mask per candidate partner scanned, the row's
+                # wedge-range bounds; hub wedges are popcounts and read nothing
+                kern = 4 * nonhub + 4 * walked(6 if fill else 5, k, fill) + 8 * inc
+            elif names[k] == "hubpair":
+                # entries walked (non-hub wedges + hub-pair list hits) and their bounds
+                kern = 4 * nonhub + 8 * inc
+            else:
+                kern = model
+            pw = filled_pairs(k) if fill else 0
+            p = 1 if fill else 0
+            cands.append(("fill" if fill else "count", k, kern + 12 * pw, ms_tot[p][k] / args.steps,
+                          ln_tot[p][k] / args.steps, model + 12 * pw, pw))
     dom = max(cands, key=lambda c: c[3])
     # the kernel as ncu names it (dense handlers carry a second, ensemble flag)
     fill_flag = "1" if dom[0] == "fill" else "0"
@@ -393,12 +421,12 @@ def bench_ours(args):
     achieved = dom[2] / dsec / 1e9 if dom[3] > 0 else 0.0
     model_gbs = dom[5] / dsec / 1e9 if dom[3] > 0 else 0.0
     nl = max(dom[4], 1)
-    pairs_per_launch = (pairs_mode[dom[1]] / nl) if dom[0] == "fill" else 0
+    pairs_per_launch = dom[6] / nl
     traffic = profiled_traffic(kname, dom[2] / nl, pairs_per_launch)
     ms_launch = dom[3] / nl
     dram_gbs = traffic / (ms_launch / 1e3) / 1e9 if traffic and ms_launch > 0 else None
     # the output writes alone: 12 B per pair of the dominant kernel's handler
-    write_gbs = (12 * pairs_mode[dom[1]] / dsec / 1e9 if dom[0] == "fill" and dom[3] > 0 else None)
+    write_gbs = (12 * dom[6] / dsec / 1e9 if dom[0] == "fill" and dom[3] > 0 else None)
     frac = achieved / hbm_peak
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                 "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
@@ -413,6 +441,9 @@ def bench_ours(args):
                           "kernel bytes: 4 B per entry walked (non-hub wedges and hub-pair list "
                           "hits) + 8 B/incidence + 12 B/pair written" if names[dom[1]] == "hubpair"
                           else "kernel bytes: 4 B/wedge + 8 B/incidence + 12 B/pair written"),
+                "walks": ("one counting walk for every list where the ensemble counts them "
+                          "together; fill walks only of the windows that walked the list (the "
+                          "others filter it from the list before)"),
                 "frac_above_1": frac > 1.0,
                 "alg_model_GBps": round(model_gbs, 1),
                 "alg_model_frac": round(model_gbs / hbm_peak, 4),
@@ -431,7 +462,13 @@ def bench_ours(args):
         d = per_s[s]
         ms = statistics.mean(d["ms"])
         pw = mode_work[s]
-        alg = sum(4 * pw[k][1] + 8 * pw[k][2] for k in range(NM)) * 2 + 12 * d["pairs"]
+        # walks charged to s: its share of the counting walks, its fill walks,
+        # and, where it was filtered, the 12 B/pair read of the list before
+        walk = [4 * pw[k][1] + 8 * pw[k][2] for k in range(NM)]
+        cnt = sum(walk[k] / len(s_list) if one_walk(k) else walk[k] for k in range(NM))
+        prev = s_list[s_list.index(s) - 1] if s != s_list[0] else None
+        filt_read = 12 * per_s[prev]["pairs"] * (1 - walk_f[s]) if prev is not None else 0
+        alg = cnt + walk_f[s] * sum(walk) + 12 * d["pairs"] + filt_read
         rec = {"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
                "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
                "s_edges_per_s": d["pairs"] / (ms / 1e3),

@@ -554,6 +554,18 @@ slg_status slg_set_hub_pairs(slg_graph* g, int32_t max_hubs, int64_t min_sparse_
 slg_status slg_set_ensemble_filter(slg_graph* g, int32_t mode);
 
 /*
+ * slg_ensemble_fill_stats -- how the windows of every list (slg_ensemble_build_
+ * window with which = SLG_ENSEMBLE_ALL) made each list since the handle was
+ * loaded or last reset: out[4 * t + c] for list index t < SLG_ENSEMBLE_MAX
+ * (4 * SLG_ENSEMBLE_MAX entries, caller-owned host memory; NULL skips the
+ * copy), c = 0 windows walked by the fill, 1 pairs they wrote, 2 windows
+ * filtered from list t-1, 3 pairs the filter wrote. reset != 0 zeroes the
+ * counters after the copy. Host-side counters: no device work, no error
+ * besides a NULL graph (SLG_EINVAL).
+ */
+slg_status slg_ensemble_fill_stats(slg_graph* g, int32_t reset, int64_t* out);
+
+/*
  * slg_set_staging -- one walk instead of two for the sparse-accumulator and
  * hub-pair rows.
  *

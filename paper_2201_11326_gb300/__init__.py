@@ -24,7 +24,7 @@ __all__ = [
     "slg_mode_stats", "slg_ensemble_mode_stats", "slg_kernel_launches", "slg_scan_counts_noalloc", "slg_batch_load",
     "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
-    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "slg_set_staging", "slg_staging_stats", "slg_set_ensemble_filter",
+    "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "slg_set_staging", "slg_staging_stats", "slg_set_ensemble_filter", "slg_ensemble_fill_stats",
     "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
@@ -115,6 +115,7 @@ _SIGS = {
     "slg_set_staging": (_i32, [_vp, _i64]),
     "slg_set_ensemble_filter": (_i32, [_vp, _i32]),
     "slg_staging_stats": (_i32, [_vp, _i64p]),
+    "slg_ensemble_fill_stats": (_i32, [_vp, _i32, _i64p]),
     "slg_autotune": (_i32, [_vp, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "slg_kernel_stats": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), _i64p]),
     "slg_mode_stats": (_i32, [_vp, _i32, _i64p]),
@@ -622,6 +623,14 @@ def slg_set_staging(g: Graph, max_bytes: int = -1):
 def slg_set_ensemble_filter(g: Graph, mode: int = -1):
     """Lists after the first of an all-list ensemble window: -1 automatic, 0 walk, 1 filter."""
     _check(lib().slg_set_ensemble_filter(g.handle, mode))
+
+
+def slg_ensemble_fill_stats(g: Graph, reset: bool = False) -> np.ndarray:
+    """Per list index of all-list ensemble windows: [windows walked, pairs walked,
+    windows filtered, pairs filtered] (shape ENSEMBLE_MAX x 4)."""
+    out = np.zeros((ENSEMBLE_MAX, 4), np.int64)
+    _check(lib().slg_ensemble_fill_stats(g.handle, int(bool(reset)), out.ctypes.data_as(_i64p)))
+    return out
 
 
 def slg_staging_stats(g: Graph) -> dict:

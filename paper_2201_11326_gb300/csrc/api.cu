@@ -695,6 +695,11 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
             slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
                           dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], &h->mtimer,
                           h->st);
+        if (t1 - t0 == k) {  // windows of every list
+            int64_t* mk = h->ens_made[t];
+            mk[filt ? 2 : 0] += 1;
+            mk[filt ? 3 : 1] += seg[u + 1] - seg[u];
+        }
     }
     h->timer.mark(4, h->st);
     if (dd) {
@@ -746,6 +751,17 @@ slg_status slg_kernel_stats(slg_graph* h, int32_t reset, float* ms, int64_t* lau
                 h->mtimer.ms[pass][k] = 0;
                 h->mtimer.launches[pass][k] = 0;
             }
+        }
+    return SLG_OK;
+}
+
+slg_status slg_ensemble_fill_stats(slg_graph* h, int32_t reset, int64_t* out) {
+    if (!h) return fail(SLG_EINVAL, "graph is NULL");
+    static_assert(slg::ENS_MAX == SLG_ENSEMBLE_MAX, "ensemble size");
+    for (int t = 0; t < slg::ENS_MAX; ++t)
+        for (int c = 0; c < 4; ++c) {
+            if (out) out[t * 4 + c] = h->ens_made[t][c];
+            if (reset) h->ens_made[t][c] = 0;
         }
     return SLG_OK;
 }

@@ -45,6 +45,9 @@ struct slg_graph {
     // an ensemble's window of every list: list t from list t-1 by filtering (1),
     // by walking its rows (0), or whichever reads less (-1)
     int32_t ens_filter = -1;
+    // per ensemble list index, over windows of every list: {windows walked,
+    // pairs walked, windows filtered, pairs filtered} (slg_ensemble_fill_stats)
+    int64_t ens_made[slg::ENS_MAX][4] = {};
 };
 
 namespace slg {

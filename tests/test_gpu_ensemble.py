@@ -327,6 +327,7 @@ def test_ensemble_lists_filtered_from_the_one_before(mode):
         I, J, O = (np.zeros(cap, np.int32) for _ in range(3))
         splits = slg.slg_ensemble_plan_windows(g, s_list, cap)
         assert len(splits) > 2
+        slg.slg_ensemble_fill_stats(g, reset=True)
         for r0, r1 in zip(splits[:-1], splits[1:]):
             nr = int(r1 - r0)
             rd = np.zeros(len(s_list) * nr, np.uint64)
@@ -335,6 +336,19 @@ def test_ensemble_lists_filtered_from_the_one_before(mode):
             assert got == [int(x) for x in counts[r0:r1].sum(axis=0)]
             for t in range(len(s_list)):
                 assert np.array_equal(rd[t * nr:(t + 1) * nr], digs[r0:r1, t]), (mode, t, r0)
+        # how each list was made: every window either walked or filtered it, the
+        # first list always walked, and the pairs add up to the list's
+        made = slg.slg_ensemble_fill_stats(g)
+        nwin = len(splits) - 1
+        for t in range(len(s_list)):
+            assert made[t][0] + made[t][2] == nwin, (mode, t, made[t])
+            assert made[t][1] + made[t][3] == int(counts[:, t].sum()), (mode, t, made[t])
+        assert made[0][2] == 0
+        if mode == 0:
+            assert not made[1:, 2].any()
+        if mode == 1:
+            assert not made[1:len(s_list), 0].any()
+        assert not made[len(s_list):].any()
         with pytest.raises(slg.SlgError):
             slg.slg_set_ensemble_filter(g, 2)
     finally:
