@@ -500,7 +500,7 @@ def bench_ours(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O), sweep)
+        out["e2e"] = e2e(args, slg, h, s_list, stream, (I, J, O), sweep, all_lists=ens_all)
     if rank == 0 and world == 1 and not args.no_cpu:
         wedges, dt, cores, sample = oracle_sample(h, s_list, cpu_rows, seed=1)
         out["cpu_baseline"] = {"value": wedges / dt, "unit": "wedges/s", "cores": cores,
@@ -511,8 +511,10 @@ def bench_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s"):
-    """Same sweep through the public API from pinned host memory.
+def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s", all_lists=False):
+    """Same sweep through the public API from pinned host memory (an ensemble in
+    the same windows as the device-timed step: each list's own, or windows of
+    every list).
 
     Timed (wall clock): host->device copy of the CSR (inside slg_load), the
     transpose, every counting pass and window fill, and the device->host read
@@ -533,7 +535,7 @@ def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s"):
         if sweep == "ensemble":
             slg.slg_ensemble_count(g, s_list)
             rows = torch.empty((len(s_list), h.m + 1), dtype=torch.int64).pin_memory()
-            for t in range(len(s_list)):
+            for t in ([slg.ENSEMBLE_ALL] if all_lists else range(len(s_list))):
                 splits = slg.slg_ensemble_plan_windows(g, s_list, WINDOW, which=t)
                 for r0, r1 in zip(splits[:-1], splits[1:]):
                     slg.slg_ensemble_build_window(g, s_list, int(r0), int(r1), I, J, O, WINDOW,
