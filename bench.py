@@ -209,13 +209,15 @@ def run_sweep(slg, g, s_list, bufs, stream, per_s, mode_work=None):
 
 
 def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None,
-                       all_lists=False):
+                       all_lists=False, made=None):
     """The s sweep as one ensemble (Algorithm 3): one plan for min(s) and one
     counting pass for every list, then each list's windows (per s: its fill time),
     or windows holding every list (all_lists: the later lists filtered from the
-    one before where that reads less; per s: its share of the fill time, in
-    proportion to its pairs). The shared counting pass is charged to the lists in
-    equal parts."""
+    one before where that reads less; per s: its filters' time, measured, plus
+    its share of the walking fills, in proportion to the pairs they wrote). The
+    shared counting pass is charged to the lists in equal parts. made (per s:
+    windows walked, pairs walked, windows filtered, pairs filtered, filter
+    microseconds, pairs the filter read) accumulates slg_ensemble_fill_stats."""
     import torch
     I, J, O = bufs
     cap = I.numel()
@@ -241,12 +243,21 @@ def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=No
     ev[-1].synchronize()
     count_ms = ev[0].elapsed_time(ev[1])
     fill_all = ev[1].elapsed_time(ev[-1])
-    ptot = max(sum(pairs), 1)
+    fs = slg.slg_ensemble_fill_stats(g, reset=True)
+    if made is not None:
+        for t, s in enumerate(s_list):
+            acc = made.setdefault(s, [0] * 6)
+            for c in range(6):
+                acc[c] += int(fs[t][c])
+    filt_ms = [fs[t][4] / 1e3 for t in range(len(s_list))]
+    walked = max(sum(int(fs[t][1]) for t in range(len(s_list))), 1)
+    walk_ms = max(fill_all - sum(filt_ms), 0.0)
     for t, s in enumerate(s_list):
         d = per_s.setdefault(s, {"s": s, "wedges": wedges[s], "pairs": pairs[t], "ms": [],
-                                 "fill_ms": [], "count_ms_shared": []})
-        fill = (fill_all * pairs[t] / ptot if all_lists
+                                 "fill_ms": [], "count_ms_shared": [], "filter_ms": []})
+        fill = (filt_ms[t] + walk_ms * int(fs[t][1]) / walked if all_lists
                 else ev[t + 1].elapsed_time(ev[t + 2]))
+        d["filter_ms"].append(filt_ms[t])
         d["fill_ms"].append(fill)
         d["count_ms_shared"].append(count_ms)
         d["ms"].append(fill + count_ms / len(s_list))
@@ -293,16 +304,10 @@ def bench_ours(args):
                 slg.slg_set_timing(g, True)
             if sweep == "ensemble":
                 run_sweep_ensemble(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work,
-                                   all_lists=ens_all)
+                                   all_lists=ens_all, made=fill_made if timing else None)
             else:
                 run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
-            if timing and sweep == "ensemble":
-                made = slg.slg_ensemble_fill_stats(g)
-                for t, s in enumerate(s_list):
-                    acc = fill_made.setdefault(s, [0, 0, 0, 0])
-                    for c in range(4):
-                        acc[c] += int(made[t][c])
             g.free()
         return ks
 
@@ -466,8 +471,7 @@ def bench_ours(args):
         # and, where it was filtered, the 12 B/pair read of the list before
         walk = [4 * pw[k][1] + 8 * pw[k][2] for k in range(NM)]
         cnt = sum(walk[k] / len(s_list) if one_walk(k) else walk[k] for k in range(NM))
-        prev = s_list[s_list.index(s) - 1] if s != s_list[0] else None
-        filt_read = 12 * per_s[prev]["pairs"] * (1 - walk_f[s]) if prev is not None else 0
+        filt_read = 12 * fill_made[s][5] / args.steps if s in fill_made else 0
         alg = cnt + walk_f[s] * sum(walk) + 12 * d["pairs"] + filt_read
         rec = {"s": s, "wedges": d["wedges"], "pairs": d["pairs"],
                "ms": round(ms, 2), "wedges_per_s": d["wedges"] / (ms / 1e3),
@@ -477,6 +481,16 @@ def bench_ours(args):
         if "fill_ms" in d:
             rec["fill_ms"] = round(statistics.mean(d["fill_ms"]), 2)
             rec["count_ms_shared"] = round(statistics.mean(d["count_ms_shared"]), 2)
+        m = fill_made.get(s)
+        if m and m[2]:
+            # the list filter that made s from the list before: 12 B read per pair
+            # of that list in the filtered windows, 12 B written per pair kept
+            fbytes = 12 * m[5] + 12 * m[3]
+            fsec = m[4] / 1e6
+            rec["filter"] = {"windows": m[2] // args.steps, "pairs": m[3] // args.steps,
+                             "ms": round(m[4] / 1e3 / args.steps, 2),
+                             "GBps": round(fbytes / fsec / 1e9, 1) if fsec > 0 else None,
+                             "frac": round(fbytes / fsec / 1e9 / hbm_peak, 4) if fsec > 0 else None}
         per_s_out.append(rec)
 
     out = {

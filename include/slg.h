@@ -556,11 +556,14 @@ slg_status slg_set_ensemble_filter(slg_graph* g, int32_t mode);
 /*
  * slg_ensemble_fill_stats -- how the windows of every list (slg_ensemble_build_
  * window with which = SLG_ENSEMBLE_ALL) made each list since the handle was
- * loaded or last reset: out[4 * t + c] for list index t < SLG_ENSEMBLE_MAX
- * (4 * SLG_ENSEMBLE_MAX entries, caller-owned host memory; NULL skips the
+ * loaded or last reset: out[6 * t + c] for list index t < SLG_ENSEMBLE_MAX
+ * (6 * SLG_ENSEMBLE_MAX entries, caller-owned host memory; NULL skips the
  * copy), c = 0 windows walked by the fill, 1 pairs they wrote, 2 windows
- * filtered from list t-1, 3 pairs the filter wrote. reset != 0 zeroes the
- * counters after the copy. Host-side counters: no device work, no error
+ * filtered from list t-1, 3 pairs the filter wrote, 4 the filter's device
+ * time in microseconds (count, scan and write, CUDA events on the graph's
+ * stream), accumulated only while slg_set_timing is on, 5 pairs of list t-1
+ * the filter read. reset != 0 zeroes
+ * the counters after the copy. Host-side counters: no device work, no error
  * besides a NULL graph (SLG_EINVAL).
  */
 slg_status slg_ensemble_fill_stats(slg_graph* g, int32_t reset, int64_t* out);

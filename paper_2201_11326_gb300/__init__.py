@@ -627,8 +627,9 @@ def slg_set_ensemble_filter(g: Graph, mode: int = -1):
 
 def slg_ensemble_fill_stats(g: Graph, reset: bool = False) -> np.ndarray:
     """Per list index of all-list ensemble windows: [windows walked, pairs walked,
-    windows filtered, pairs filtered] (shape ENSEMBLE_MAX x 4)."""
-    out = np.zeros((ENSEMBLE_MAX, 4), np.int64)
+    windows filtered, pairs filtered, filter device microseconds while timing,
+    pairs the filter read] (shape ENSEMBLE_MAX x 6)."""
+    out = np.zeros((ENSEMBLE_MAX, 6), np.int64)
     _check(lib().slg_ensemble_fill_stats(g.handle, int(bool(reset)), out.ctypes.data_as(_i64p)))
     return out
 

@@ -100,6 +100,8 @@ void Timer::destroy() {
 void mtimer_init(ModeTimer& t) {
     for (auto& e : t.ev)
         if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
+    for (auto& e : t.fev)
+        if (!e) SLG_CUDA_TRY(cudaEventCreate(&e));
 }
 
 void build_plan(slg_graph* h, int32_t s, const BinParams& bp) {
@@ -407,6 +409,8 @@ void slg_free(slg_graph* h) {
     h->timer.destroy();
     for (auto& e : h->mtimer.ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : h->mtimer.fev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -687,11 +691,19 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
                 filt = 6 * (seg[u] - seg[u - 1]) < wrows;
             }
         }
+        const bool ftimed = filt && h->mtimer.on;
+        float fms = 0;
+        if (ftimed) SLG_CUDA_TRY(cudaEventRecord(h->mtimer.fev[0], h->st));
         if (filt)
             slg::run_filter(dI + seg[u - 1], dJ + seg[u - 1], dO + seg[u - 1], seg[u] - seg[u - 1],
                             p.ens.s[t], dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u],
                             h->st);
-        else
+        if (ftimed) {
+            SLG_CUDA_TRY(cudaEventRecord(h->mtimer.fev[1], h->st));
+            SLG_CUDA_TRY(cudaEventSynchronize(h->mtimer.fev[1]));
+            SLG_CUDA_TRY(cudaEventElapsedTime(&fms, h->mtimer.fev[0], h->mtimer.fev[1]));
+        }
+        if (!filt)
             slg::run_fill(h->g, p, p.rs_for(p.ens.s[t]), p.ens.ioff + t * (ni + 1), q0, q1,
                           dI + seg[u], dJ + seg[u], dO + seg[u], seg[u + 1] - seg[u], &h->mtimer,
                           h->st);
@@ -699,6 +711,8 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
             int64_t* mk = h->ens_made[t];
             mk[filt ? 2 : 0] += 1;
             mk[filt ? 3 : 1] += seg[u + 1] - seg[u];
+            mk[4] += (int64_t)(1000.0f * fms);
+            if (filt) mk[5] += seg[u] - seg[u - 1];
         }
     }
     h->timer.mark(4, h->st);
@@ -759,8 +773,8 @@ slg_status slg_ensemble_fill_stats(slg_graph* h, int32_t reset, int64_t* out) {
     if (!h) return fail(SLG_EINVAL, "graph is NULL");
     static_assert(slg::ENS_MAX == SLG_ENSEMBLE_MAX, "ensemble size");
     for (int t = 0; t < slg::ENS_MAX; ++t)
-        for (int c = 0; c < 4; ++c) {
-            if (out) out[t * 4 + c] = h->ens_made[t][c];
+        for (int c = 0; c < 6; ++c) {
+            if (out) out[t * 6 + c] = h->ens_made[t][c];
             if (reset) h->ens_made[t][c] = 0;
         }
     return SLG_OK;

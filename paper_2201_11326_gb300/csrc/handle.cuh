@@ -46,8 +46,10 @@ struct slg_graph {
     // by walking its rows (0), or whichever reads less (-1)
     int32_t ens_filter = -1;
     // per ensemble list index, over windows of every list: {windows walked,
-    // pairs walked, windows filtered, pairs filtered} (slg_ensemble_fill_stats)
-    int64_t ens_made[slg::ENS_MAX][4] = {};
+    // pairs walked, windows filtered, pairs filtered, filter device time in
+    // microseconds while timing is on, pairs the filter read}
+    // (slg_ensemble_fill_stats)
+    int64_t ens_made[slg::ENS_MAX][6] = {};
 };
 
 namespace slg {

@@ -109,6 +109,7 @@ struct ModeTimer {
     cudaEvent_t ev[2 * NMODES] = {};
     float ms[2][NMODES] = {};
     int64_t launches[2][NMODES] = {};
+    cudaEvent_t fev[2] = {};  // around one ensemble list filter
 };
 
 // Tunables of the binning (chosen per graph; defaults in plan.cu).

@@ -348,6 +348,9 @@ def test_ensemble_lists_filtered_from_the_one_before(mode):
             assert not made[1:, 2].any()
         if mode == 1:
             assert not made[1:len(s_list), 0].any()
+            for t in range(1, len(s_list)):  # each filter read the whole list before
+                assert made[t][5] == int(counts[:, t - 1].sum()), (t, made[t])
+        assert not made[:, 4].any()         # filter times only while timing is on
         assert not made[len(s_list):].any()
         with pytest.raises(slg.SlgError):
             slg.slg_set_ensemble_filter(g, 2)
