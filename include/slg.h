@@ -584,13 +584,17 @@ slg_status slg_ensemble_fill_stats(slg_graph* g, int32_t reset, int64_t* out);
  *   max_bytes : -1 (default) automatic: three quarters of the free device
  *               memory beyond 6 GiB (5 bytes per pair plus 8 bytes per work
  *               item), at most 2^34 pairs, and no more than the rows can fill
- *               (the entries they walk, plus a chunk per CTA); 0 disables
- *               staging; > 0 caps the pool at this many bytes.
+ *               (the entries they walk, plus a chunk per CTA); made only when
+ *               the rows can fill at least 2^26 pairs, and only while the
+ *               automatic pools of all handles stay under a quarter of the
+ *               device's memory; 0 disables staging; > 0 caps the pool at this
+ *               many bytes (made at any size).
  * CTAs take chunks of 2^12 to 2^20 pairs (a quarter CTA's share of what the
  * rows can fill); no pool is made below 16 chunks (automatic) or one chunk
  * (capped). The pool is allocated by each counting pass of a plan that has
  * such rows and released with the plan (a new s, slg_set_bins, slg_free). A
- * server's queries never stage. Releases the current plan.
+ * server's queries and batch handles (slg_batch_load, slg_batch) do not stage
+ * unless this call turns it on. Releases the current plan.
  */
 slg_status slg_set_staging(slg_graph* g, int64_t max_bytes);
 

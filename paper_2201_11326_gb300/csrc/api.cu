@@ -15,8 +15,10 @@ namespace slg {
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_stage_bytes{0};  // staging pools held by all handles
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void stage_bytes_add(int64_t d) { g_stage_bytes.fetch_add(d, std::memory_order_relaxed); }
 
 void set_error(slg_status code, const std::string& msg) {
     (void)code;
@@ -127,6 +129,9 @@ void build_plan(slg_graph* h, int32_t s, const BinParams& bp) {
 // sparse-accumulator or hub-pair items: three quarters of the free device
 // memory beyond 6 GiB, at most stage_max_bytes when set, at most 2^34 pairs,
 // and no more than those rows can fill (their walk, plus a chunk per CTA).
+// The pool lives as long as the plan, so the automatic one is only made when
+// the rows can fill at least 2^26 pairs (a second walk of fewer costs little)
+// and keeps the pools of all handles under a quarter of the device's memory.
 // Views (which share their device with other queries) stage nothing.
 void plan_staging(slg_graph* h) {
     Plan& p = h->plan;
@@ -138,8 +143,10 @@ void plan_staging(slg_graph* h) {
     SLG_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
     int64_t budget = ((int64_t)fr - ((int64_t)6 << 30)) / 4 * 3;
     if (h->stage_max_bytes > 0) budget = std::min(budget, h->stage_max_bytes);
+    else budget = std::min(budget, (int64_t)(tot / 4) - (int64_t)g_stage_bytes.load());
     // chunks: a CTA's share of what the rows can fill, between 2^12 and 2^20 pairs
     const int64_t bound = plan_stage_bound(h->g, p, h->st);
+    if (h->stage_max_bytes < 0 && bound < ((int64_t)1 << 26)) return;
     const int64_t ctas = 1024;  // CTAs of the two handlers' fill launches, about
     const int64_t chunk = std::max<int64_t>(4096, std::min<int64_t>(SG_CHUNK, bound / (4 * ctas)));
     int64_t cap = std::min<int64_t>((budget - 8 * p.nitems) / 5, (int64_t)1 << 34);
@@ -151,6 +158,8 @@ void plan_staging(slg_graph* h) {
     p.stage_O = dalloc<uint8_t>((size_t)cap, h->st);
     p.stage_cursor = dalloc<unsigned long long>(1, h->st);
     p.stage_cap = cap;
+    p.stage_bytes = 8 * p.nitems + 5 * cap;
+    stage_bytes_add(p.stage_bytes);
 }
 
 slg_graph* make_view(const slg_graph* base, cudaStream_t st) {
@@ -937,6 +946,9 @@ slg_status slg_batch_load(slg_graph* const* gs, const int32_t* s, int32_t k, voi
     }
     slg_graph* h = new slg_graph();
     h->st = (cudaStream_t)stream;
+    // a batch's many small graphs gain nothing from staging (measured on the
+    // 4,096-graph batch) and its pool would stay with the batch's plan
+    h->stage_max_bytes = 0;
     try {
         SLG_CUDA_TRY(cudaGetDevice(&h->device));
         slg::GraphDev& g = h->g;

@@ -446,6 +446,8 @@ void Plan::release_stage(cudaStream_t st) {
     dfree(stage_cursor, st);
     stage_cap = 0;
     stage_s = -1;
+    stage_bytes_add(-stage_bytes);
+    stage_bytes = 0;
 }
 
 void Plan::release(cudaStream_t st) {

@@ -180,6 +180,7 @@ struct Plan {
     int64_t stage_cap = 0;
     int64_t stage_chunk = SG_CHUNK;
     int32_t stage_s = -1;  // the threshold whose list the last counting pass staged
+    int64_t stage_bytes = 0;  // device bytes of the pool and its item positions
     StageArgs stage_args() const {
         return StageArgs{stage_J, stage_O, stage_cap, stage_cursor, stage_at, stage_chunk,
                          stage_chunk / 32};

@@ -42,6 +42,8 @@ void set_error(slg_status code, const std::string& msg);
 // Every kernel launch of the library is followed by SLG_LAUNCH_CHECK(), which
 // also counts it (reported by slg_kernel_launches()).
 void count_launch();
+// Bytes of staging pools held by all handles (plan_staging, Plan::release_stage).
+void stage_bytes_add(int64_t d);
 #define SLG_LAUNCH_CHECK()                    \
     do {                                      \
         ::slg::count_launch();                \

@@ -576,10 +576,11 @@ def test_hub_pairs_disabled_and_default_threshold():
         g.free()
 
 
-# staging pools: automatic, none, and one of three chunks (spent after three
-# CTAs' worth of items: the counting kernels take the others)
+# staging pools: automatic, capped (made at any size), none, and one of three
+# chunks (spent after three CTAs' worth of items: the counting kernels take the
+# others)
 @pytest.mark.parametrize("handler", ["hubpair", "sparse"])
-@pytest.mark.parametrize("pool", ["auto", "off", "three_chunks"])
+@pytest.mark.parametrize("pool", ["auto", "capped", "off", "three_chunks"])
 def test_staged_counting_pass(handler, pool):
     # the sparse-accumulator and hub-pair fill kernels run as the counting pass,
     # staging each item's pairs; windows copy staged items and fill the rest
@@ -594,22 +595,35 @@ def test_staged_counting_pass(handler, pool):
             slg.slg_set_bins(g, *FORCED["sparse_cta_only"])
             slg.slg_set_hub_pairs(g, 0, 0)
         if pool != "auto":
+            slg.slg_set_staging(g, 1 << 34)  # a capped pool is made at any size
             slg.slg_count(g, 2)
             st = slg.slg_staging_stats(g)
             assert st["pool_pairs"] > 0 and st["items_staged"] > 0, st
             # 8 bytes per item, 5 per pooled pair
-            slg.slg_set_staging(g, 0 if pool == "off" else 8 * st["items"] + 5 * 3 * st["chunk_pairs"])
+            if pool != "capped":
+                slg.slg_set_staging(g, 0 if pool == "off" else
+                                    8 * st["items"] + 5 * 3 * st["chunk_pairs"])
         slg.slg_set_timing(g, True)
         for s in (2, 4, 8):
             slg.slg_kernel_stats(g, reset=True)
             got = slg.slg_build(g, s)
             assert_same(got, oracle_list("large20000", h, s), f"{handler} {pool} s={s}")
             launches = slg.slg_kernel_stats(g)[1][0][mode]
-            rows = slg.slg_mode_stats(g, s)[mode][0]
+            ms = slg.slg_mode_stats(g, s)
+            rows = ms[mode][0]
             st = slg.slg_staging_stats(g)
             assert rows > 0
+            staged = st["pool_pairs"] > 0
+            if pool == "auto":
+                # made only when the rows can fill 2^26 pairs: their wedges (sparse
+                # accumulator) and walked entries (hub pairs)
+                bound = ms[slg.MODE_NAMES.index("sparse")][1] + \
+                    ms[slg.MODE_NAMES.index("hubpair")][4]
+                assert staged == (bound >= 1 << 26), (bound, st)
+            else:
+                assert staged == (pool != "off"), st
             # staging launches the fill kernel before the counting kernel
-            assert launches == (1 if pool == "off" else 2), (pool, s, launches)
+            assert launches == (2 if staged else 1), (pool, s, launches)
             if pool == "off":
                 assert st["items_staged"] == 0
             elif pool == "three_chunks":
