@@ -240,6 +240,52 @@ slg_status slg_ensemble_build_window(slg_graph* g, const int32_t* s_list, int32_
                                      uint64_t* row_digests);
 
 /*
+ * slg_ensemble_stream_window -- the lists window after window, each
+ * sparse-accumulator and hub-pair row walked once (Algorithm 2, Section
+ * III-C, counts a row's pairs and emits them from one pass over its wedges;
+ * Algorithm 3, Section III-D, gives every threshold from one count).
+ *
+ * No counting pass over the whole graph comes first: the rows of a window are
+ * chosen before they are walked, from an upper bound on their pairs (the
+ * exact count for table and dense rows, counted once before the first window;
+ * W_i / s_list[0] for sparse-accumulator rows; walked entries / (s_list[0] - 1)
+ * for hub-pair rows), scaled by what the windows before observed. The
+ * window's sparse-accumulator and hub-pair items are walked once, counting and
+ * staging their pairs in a pool (slg_set_staging; 5 bytes per pair, about
+ * 5 * cap bytes); their offsets are a scan of the window's counts; the pairs
+ * are then copied into place (items the pool could not hold are walked again).
+ * List t > 0 of the window is list t-1 filtered by s_list[t] (the lists are
+ * nested and in the same order). If the rows' pairs exceed cap after all, the
+ * window ends at the last row that fits.
+ *
+ *   s_list, k : 1 <= k <= SLG_ENSEMBLE_MAX ascending thresholds >= 1 (one
+ *               graph, not a batch).
+ *   r0        : the window's first row: 0, then the previous call's *r1.
+ *   I, J, O   : device arrays (of the current device) of cap pairs, written
+ *               with every list of rows [r0, *r1) back to back, each in
+ *               canonical (i, j) order; the caller owns them.
+ *   r1        : out: the end of the window's rows; r0 < *r1 <= m unless r0 == m
+ *               (then *r1 == m and nothing is written).
+ *   pairs     : out: k entries, the pairs of each list in the window.
+ * Windows of consecutive calls cover the rows once each, in order, and their
+ * lists concatenated are the lists of slg_ensemble_build. The plan for
+ * s_list[0] and the bounds are built by the first call and kept with the graph
+ * (another s, another call on the graph's plan, slg_set_bins, slg_free release
+ * them); the counts of the regular calls are recomputed after this one.
+ * Errors: SLG_EINVAL (NULL argument, bad s_list or r0, cap < 1, host or another
+ * GPU's arrays, a batch); SLG_ECAPACITY when one row's lists exceed cap
+ * (nothing is returned for it); SLG_ENOMEM; SLG_ECUDA; SLG_EINTERNAL when a
+ * device consistency check fails.
+ */
+slg_status slg_ensemble_stream_window(slg_graph* g, const int32_t* s_list, int32_t k, int32_t r0,
+                                      int32_t* I, int32_t* J, int32_t* O, int64_t cap,
+                                      int32_t* r1, int64_t* pairs);
+
+/* slg_stream_window -- slg_ensemble_stream_window for the one threshold s. */
+slg_status slg_stream_window(slg_graph* g, int32_t s, int32_t r0, int32_t* I, int32_t* J,
+                             int32_t* O, int64_t cap, int32_t* r1, int64_t* pairs);
+
+/*
  * Phase timing. When enabled, the library records CUDA events on the graph's
  * stream around each phase; slg_last_timing then returns, for the last
  * counting pass and the last fill, ms[0..4] = planning (pruning, per-row
@@ -555,8 +601,9 @@ slg_status slg_set_ensemble_filter(slg_graph* g, int32_t mode);
 
 /*
  * slg_ensemble_fill_stats -- how the windows of every list (slg_ensemble_build_
- * window with which = SLG_ENSEMBLE_ALL) made each list since the handle was
- * loaded or last reset: out[6 * t + c] for list index t < SLG_ENSEMBLE_MAX
+ * window with which = SLG_ENSEMBLE_ALL, and slg_ensemble_stream_window, whose
+ * list 0 counts as walked) made each list since the handle was loaded or last
+ * reset: out[6 * t + c] for list index t < SLG_ENSEMBLE_MAX
  * (6 * SLG_ENSEMBLE_MAX entries, caller-owned host memory; NULL skips the
  * copy), c = 0 windows walked by the fill, 1 pairs they wrote, 2 windows
  * filtered from list t-1, 3 pairs the filter wrote, 4 the filter's device

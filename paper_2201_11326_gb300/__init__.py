@@ -25,6 +25,7 @@ __all__ = [
     "slg_batch_info", "slg_batch_pair_offsets", "slg_batch", "slg_result_free", "slg_dual", "slg_ensemble_count",
     "slg_ensemble_row_offsets", "slg_ensemble_plan_windows", "slg_ensemble_build_window",
     "slg_ensemble_build", "ENSEMBLE_MAX", "ENSEMBLE_ALL", "slg_autotune", "slg_set_hub_pairs", "slg_set_staging", "slg_staging_stats", "slg_set_ensemble_filter", "slg_ensemble_fill_stats",
+    "slg_stream_window", "slg_ensemble_stream_window",
     "Server", "slg_serve_create", "slg_serve_destroy",
     "slg_serve_register", "slg_serve_submit", "slg_serve_poll", "slg_serve_fetch",
     "slg_serve_release", "slg_serve_stats", "library_path",
@@ -108,6 +109,9 @@ _SIGS = {
     "slg_ensemble_plan_windows": (_i32, [_vp, _i32p, _i32, _i32, _i64, _i32p, _i32, _i32p]),
     "slg_ensemble_build_window": (_i32, [_vp, _i32p, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _i64, _i64p, _u64p, _vp]),
+    "slg_ensemble_stream_window": (_i32, [_vp, _i32p, _i32, _i32, _vp, _vp, _vp, _i64, _i32p,
+                                          _i64p]),
+    "slg_stream_window": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _i64, _i32p, _i64p]),
     "slg_set_timing": (_i32, [_vp, _i32]),
     "slg_last_timing": (_i32, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "slg_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32]),
@@ -393,6 +397,32 @@ def slg_ensemble_build(g: Graph, s_list):
         out.append((I[b:b + p], J[b:b + p], O[b:b + p]))
         b += p
     return out
+
+
+def slg_ensemble_stream_window(g: Graph, s_list, row_begin: int, I, J, O,
+                               cap: int | None = None):
+    """The next one-walk window from row_begin: every list of rows
+    [row_begin, row_end) back to back in the device arrays I, J, O.
+    Returns (row_end, pairs per list)."""
+    a, ap, k = _s_list(s_list)
+    if cap is None:
+        cap = len(I)
+    r1 = _i32()
+    pairs = np.zeros(k, np.int64)
+    _check(lib().slg_ensemble_stream_window(g.handle, ap, k, row_begin, _ptr(I), _ptr(J), _ptr(O),
+                                            cap, ctypes.byref(r1), pairs.ctypes.data_as(_i64p)))
+    return int(r1.value), [int(x) for x in pairs]
+
+
+def slg_stream_window(g: Graph, s: int, row_begin: int, I, J, O, cap: int | None = None):
+    """The next one-walk window of L_s from row_begin. Returns (row_end, pairs)."""
+    if cap is None:
+        cap = len(I)
+    r1 = _i32()
+    pairs = _i64()
+    _check(lib().slg_stream_window(g.handle, s, row_begin, _ptr(I), _ptr(J), _ptr(O), cap,
+                                   ctypes.byref(r1), ctypes.byref(pairs)))
+    return int(r1.value), int(pairs.value)
 
 
 def slg_set_timing(g: Graph, enable: bool = True):

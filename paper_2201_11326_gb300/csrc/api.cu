@@ -125,33 +125,22 @@ void build_plan(slg_graph* h, int32_t s, const BinParams& bp) {
     plan_build(h->g, s, bp, p, h->st, h->hp.built ? &h->hp : nullptr);
 }
 
-// The counting pass's staging pool (StageArgs) for a plan with
-// sparse-accumulator or hub-pair items: three quarters of the free device
-// memory beyond 6 GiB, at most stage_max_bytes when set, at most 2^34 pairs,
-// and no more than those rows can fill (their walk, plus a chunk per CTA).
-// The pool lives as long as the plan, so the automatic one is only made when
-// the rows can fill at least 2^26 pairs (a second walk of fewer costs little)
-// and keeps the pools of all handles under a quarter of the device's memory.
-// Views (which share their device with other queries) stage nothing.
-void plan_staging(slg_graph* h) {
+// A staging pool (StageArgs) of at most `want` pairs in chunks of `chunk`:
+// three quarters of the free device memory beyond 6 GiB, at most
+// stage_max_bytes when set (else all handles' pools under a quarter of the
+// device's memory), at most 2^34 pairs. False (and no pool) when fewer than 16
+// chunks (automatic) or one chunk (capped) fit.
+bool alloc_stage(slg_graph* h, int64_t want, int64_t chunk) {
     Plan& p = h->plan;
-    p.release_stage(h->st);
-    if (h->stage_max_bytes == 0 || !h->owns_data) return;
-    if (p.mode_count[MODE_SPARSE] == 0 && (p.mode_count[MODE_HUBPAIR] == 0 || !p.hp)) return;
     SLG_CUDA_TRY(cudaStreamSynchronize(h->st));  // released buffers are back with the device
     size_t fr = 0, tot = 0;
     SLG_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
     int64_t budget = ((int64_t)fr - ((int64_t)6 << 30)) / 4 * 3;
     if (h->stage_max_bytes > 0) budget = std::min(budget, h->stage_max_bytes);
     else budget = std::min(budget, (int64_t)(tot / 4) - (int64_t)g_stage_bytes.load());
-    // chunks: a CTA's share of what the rows can fill, between 2^12 and 2^20 pairs
-    const int64_t bound = plan_stage_bound(h->g, p, h->st);
-    if (h->stage_max_bytes < 0 && bound < ((int64_t)1 << 26)) return;
-    const int64_t ctas = 1024;  // CTAs of the two handlers' fill launches, about
-    const int64_t chunk = std::max<int64_t>(4096, std::min<int64_t>(SG_CHUNK, bound / (4 * ctas)));
     int64_t cap = std::min<int64_t>((budget - 8 * p.nitems) / 5, (int64_t)1 << 34);
-    cap = std::min(cap, bound + (ctas + 16) * chunk);
-    if (cap < (h->stage_max_bytes > 0 ? chunk : 16 * chunk)) return;
+    cap = std::min(cap, want);
+    if (cap < (h->stage_max_bytes > 0 ? chunk : 16 * chunk)) return false;
     p.stage_chunk = chunk;
     p.stage_at = dalloc<int64_t>((size_t)p.nitems, h->st);
     p.stage_J = dalloc<int32_t>((size_t)cap, h->st);
@@ -160,6 +149,30 @@ void plan_staging(slg_graph* h) {
     p.stage_cap = cap;
     p.stage_bytes = 8 * p.nitems + 5 * cap;
     stage_bytes_add(p.stage_bytes);
+    return true;
+}
+
+bool can_stage(const slg_graph* h) {
+    const Plan& p = h->plan;
+    if (h->stage_max_bytes == 0 || !h->owns_data) return false;
+    return p.mode_count[MODE_SPARSE] > 0 || (p.mode_count[MODE_HUBPAIR] > 0 && p.hp);
+}
+
+// The counting pass's staging pool for a plan with sparse-accumulator or
+// hub-pair items: no more than those rows can fill (their walk, plus a chunk
+// per CTA). The pool lives as long as the plan, so the automatic one is only
+// made when the rows can fill at least 2^26 pairs (a second walk of fewer costs
+// little). Views (which share their device with other queries) stage nothing.
+void plan_staging(slg_graph* h) {
+    Plan& p = h->plan;
+    p.release_stage(h->st);
+    if (!can_stage(h)) return;
+    // chunks: a CTA's share of what the rows can fill, between 2^12 and 2^20 pairs
+    const int64_t bound = plan_stage_bound(h->g, p, h->st);
+    if (h->stage_max_bytes < 0 && bound < ((int64_t)1 << 26)) return;
+    const int64_t ctas = 1024;  // CTAs of the two handlers' fill launches, about
+    const int64_t chunk = std::max<int64_t>(4096, std::min<int64_t>(SG_CHUNK, bound / (4 * ctas)));
+    alloc_stage(h, bound + (ctas + 16) * chunk, chunk);
 }
 
 slg_graph* make_view(const slg_graph* base, cudaStream_t st) {
@@ -249,7 +262,7 @@ void ensure_counted(slg_graph* h, int32_t s) {
 
 // Ensemble for s_list (Algorithm 3): the plan built for s_list[0], every
 // list counted (cached per handle, like ensure_counted).
-void ensure_ensemble(slg_graph* h, const int32_t* s_list, int32_t k) {
+void check_s_list(const slg_graph* h, const int32_t* s_list, int32_t k) {
     if (h->g.srow) throw Error{SLG_EINVAL, "an ensemble takes one graph, not a batch"};
     if (!s_list || k < 1 || k > slg::ENS_MAX)
         throw Error{SLG_EINVAL, "an ensemble takes 1 to 16 thresholds"};
@@ -258,6 +271,10 @@ void ensure_ensemble(slg_graph* h, const int32_t* s_list, int32_t k) {
         if (t > 0 && s_list[t] <= s_list[t - 1])
             throw Error{SLG_EINVAL, "ensemble thresholds must be strictly ascending"};
     }
+}
+
+void ensure_ensemble(slg_graph* h, const int32_t* s_list, int32_t k) {
+    check_s_list(h, s_list, k);
     slg::Plan& p = h->plan;
     if (p.built && p.s == s_list[0] && p.ens.counted && p.ens.k == k &&
         std::equal(s_list, s_list + k, p.ens.s))
@@ -754,6 +771,26 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
     }
     slg::dfree(dd, h->st);
     API_END
+}
+
+slg_status slg_ensemble_stream_window(slg_graph* h, const int32_t* s_list, int32_t k, int32_t r0,
+                                      int32_t* I, int32_t* J, int32_t* O, int64_t cap,
+                                      int32_t* r1, int64_t* pairs) {
+    if (!h || !r1 || !pairs) return fail(SLG_EINVAL, "NULL argument");
+    if (r0 < 0 || r0 > h->g.m) return fail(SLG_EINVAL, "bad row range");
+    if (cap < 1) return fail(SLG_EINVAL, "cap must be >= 1");
+    if (!I || !J || !O) return fail(SLG_EINVAL, "NULL output array");
+    API_BEGIN
+    check_s_list(h, s_list, k);
+    if (!slg::is_device_ptr(I) || !slg::is_device_ptr(J) || !slg::is_device_ptr(O))
+        throw Error{SLG_EINVAL, "one-walk windows write device arrays only"};
+    slg::stream_window(h, s_list, k, r0, I, J, O, cap, r1, pairs);
+    API_END
+}
+
+slg_status slg_stream_window(slg_graph* h, int32_t s, int32_t r0, int32_t* I, int32_t* J,
+                             int32_t* O, int64_t cap, int32_t* r1, int64_t* pairs) {
+    return slg_ensemble_stream_window(h, &s, 1, r0, I, J, O, cap, r1, pairs);
 }
 
 slg_status slg_set_timing(slg_graph* h, int32_t enable) {

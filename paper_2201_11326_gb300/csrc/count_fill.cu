@@ -1287,6 +1287,31 @@ void run_count(const GraphDev& g, const Plan& p, RowS rs, int32_t* icnt, ModeTim
     check_scratch(sc, st, "counting pass");
 }
 
+void run_count_modes(const GraphDev& g, const Plan& p, RowS rs, unsigned modes, int32_t* icnt,
+                     ModeTimer* mt, cudaStream_t st) {
+    int32_t* sc = new_scratch(st);
+    launch_items<false>(g, p, rs, 0, (int32_t)p.nitems, icnt, nullptr, nullptr, nullptr, nullptr,
+                        0, sc, sc + NMODES, mt, st, modes & ALL_MODES);
+    check_scratch(sc, st, "counting pass");
+}
+
+void run_count_staged(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
+                      int32_t* icnt, ModeTimer* mt, cudaStream_t st) {
+    if (item_hi <= item_lo) return;
+    constexpr unsigned STAGED = (1u << MODE_SPARSE) | (1u << MODE_HUBPAIR);
+    int32_t* sc = new_scratch(st);
+    if (p.stage_at && p.stage_cap > 0) {
+        SLG_CUDA_TRY(cudaMemsetAsync(p.stage_at + item_lo, 0xff,
+                                     sizeof(int64_t) * (size_t)(item_hi - item_lo), st));
+        SLG_CUDA_TRY(cudaMemsetAsync(p.stage_cursor, 0, sizeof(unsigned long long), st));
+        launch_items<true>(g, p, rs, item_lo, item_hi, icnt, nullptr, nullptr, nullptr, nullptr, 0,
+                           sc, sc + NMODES, mt, st, STAGED, nullptr, p.stage_args());
+    }
+    launch_items<false>(g, p, rs, item_lo, item_hi, icnt, nullptr, nullptr, nullptr, nullptr, 0,
+                        sc, sc + NMODES, mt, st, STAGED);
+    check_scratch(sc, st, "counting pass");
+}
+
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
               cudaStream_t st, StageUse su) {
@@ -1328,6 +1353,30 @@ void run_filter(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n,
     dfree(counts, st);
     dfree(boff, st);
     if (got != expect) throw Error{SLG_EINTERNAL, "list filter: pair count differs from the count"};
+}
+
+int64_t run_filter_room(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n, int32_t s,
+                        int32_t* I2, int32_t* J2, int32_t* O2, int64_t room, cudaStream_t st) {
+    if (n <= 0) return 0;
+    const int64_t nb = (n + FT_N - 1) / FT_N;
+    int32_t* counts = dalloc<int32_t>((size_t)nb, st);
+    int64_t* boff = dalloc<int64_t>((size_t)nb + 1, st);
+    k_filter_count<<<(unsigned)nb, FT_THREADS, 0, st>>>(O, n, s, counts);
+    SLG_LAUNCH_CHECK();
+    scan_i32_to_i64(counts, boff, nb, st);
+    int64_t got = 0;
+    SLG_CUDA_TRY(cudaMemcpyAsync(&got, boff + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SLG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (I2 && got <= room) {
+        int32_t* sc = new_scratch(st);
+        k_filter_write<<<(unsigned)nb, FT_THREADS, 0, st>>>(I, J, O, n, s, boff, I2, J2, O2, got,
+                                                            sc + NMODES);
+        SLG_LAUNCH_CHECK();
+        check_scratch(sc, st, "list filter");  // synchronises
+    }
+    dfree(counts, st);
+    dfree(boff, st);
+    return got;
 }
 
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st) {

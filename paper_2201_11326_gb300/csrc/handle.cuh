@@ -66,4 +66,16 @@ void build_plan(slg_graph* h, int32_t s, const BinParams& bp);
 // released.
 void autotune(slg_graph* h, int32_t s, int32_t max_trials, float* best_ms);
 
+// Whether h's plan has rows a staging pool serves (and h may stage).
+bool can_stage(const slg_graph* h);
+// A staging pool for h's plan of at most `want` pairs in chunks of `chunk`,
+// within the device-memory budget; false (no pool) when too little fits.
+bool alloc_stage(slg_graph* h, int64_t want, int64_t chunk);
+
+// The next window of one-walk construction (stream.cu): rows r0 .. *r1 of the
+// lists for s[0..k-1], back to back in I/J/O (device, cap pairs), pairs[t]
+// each. Builds the plan and its bounds on first use.
+void stream_window(slg_graph* h, const int32_t* s, int32_t k, int32_t r0, int32_t* I,
+                   int32_t* J, int32_t* O, int64_t cap, int32_t* r1, int64_t* pairs);
+
 }  // namespace slg

@@ -450,9 +450,16 @@ void Plan::release_stage(cudaStream_t st) {
     stage_bytes = 0;
 }
 
+void Plan::release_stream(cudaStream_t st) {
+    dfree(stream_cum, st);
+    stream_cum = nullptr;
+    stream_k = 0;
+}
+
 void Plan::release(cudaStream_t st) {
     release_ensemble(st);
     release_stage(st);
+    release_stream(st);
     if (idxTs_owned) dfree(idxTs, st);
     idxTs = nullptr;
     dfree(ks, st);

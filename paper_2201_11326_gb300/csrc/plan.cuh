@@ -187,6 +187,15 @@ struct Plan {
     }
     void release_stage(cudaStream_t st);
 
+    // one-walk windows (stream_window): their thresholds, the cumulative bound
+    // on each row's list-0 pairs, and what the last window observed
+    int64_t* stream_cum = nullptr;  // [m+1]
+    int32_t stream_k = 0;
+    int32_t stream_s[ENS_MAX] = {};
+    double stream_lambda = 1.0;  // list-0 pairs per unit of bound
+    double stream_phi = 1.0;     // pairs of every list per list-0 pair
+    void release_stream(cudaStream_t st);
+
     RowS rs_for(int32_t s_t) const { return RowS{rs.srow, rs.rbase, s_t}; }
     void release_ensemble(cudaStream_t st);
     void release(cudaStream_t st);
@@ -229,6 +238,18 @@ struct StageUse {
 void run_fill(const GraphDev& g, const Plan& p, RowS rs, const int64_t* ioff, int32_t item_lo,
               int32_t item_hi, int32_t* I, int32_t* J, int32_t* O, int64_t limit, ModeTimer* mt,
               cudaStream_t st, StageUse su = StageUse{});
+// Counting pass of the handlers in the bit set `modes` only, over every item.
+void run_count_modes(const GraphDev& g, const Plan& p, RowS rs, unsigned modes, int32_t* icnt,
+                     ModeTimer* mt, cudaStream_t st);
+// Counting pass of the sparse-accumulator and hub-pair items of
+// [item_lo, item_hi): their fill kernels count and stage while the plan's pool
+// lasts (stage_at of the range reset first), the counting kernels take the rest.
+void run_count_staged(const GraphDev& g, const Plan& p, RowS rs, int32_t item_lo, int32_t item_hi,
+                      int32_t* icnt, ModeTimer* mt, cudaStream_t st);
+// The pairs of one list with overlap >= s, in order, into I2/J2/O2 when they
+// are at most `room` (and I2 is not null); returns their number either way.
+int64_t run_filter_room(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n, int32_t s,
+                        int32_t* I2, int32_t* J2, int32_t* O2, int64_t room, cudaStream_t st);
 // The pairs of one list with overlap >= s (n in, expect out, order kept): a list
 // of an ensemble from the list before it.
 void run_filter(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n, int32_t s,
