@@ -59,8 +59,9 @@ def parse_args():
     ap.add_argument("--workload", choices=["medium", "large", "batch", "serve", "ensemble"],
                     default="medium")
     ap.add_argument("--graphs", type=int, default=4096, help="batch workload: number of graphs")
-    ap.add_argument("--sweep", choices=["ensemble", "per_s"], default=None,
-                    help="the s sweep as one ensemble (default) or one s at a time")
+    ap.add_argument("--sweep", choices=["ensemble", "stream", "per_s"], default=None,
+                    help="the s sweep as one ensemble (default), as one-walk windows of every "
+                         "list, or one s at a time")
     ap.add_argument("--ens-windows", choices=["per_list", "all"], default=None,
                     help="ensemble sweep: each list in its own windows (medium default), or "
                          "windows of every list, the later lists filtered from the one before "
@@ -263,6 +264,46 @@ def run_sweep_ensemble(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=No
         d["ms"].append(fill + count_ms / len(s_list))
 
 
+def run_sweep_stream(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None, made=None):
+    """The s sweep as one-walk windows of every list (slg_ensemble_stream_window):
+    no counting pass over the whole graph; each window's sparse-accumulator and
+    hub-pair rows are walked once, the later lists filtered from the one before.
+    Per s: its filters' time (measured) for s after the first; the rest of the
+    step for the first. made accumulates slg_ensemble_fill_stats."""
+    import torch
+    I, J, O = bufs
+    cap = I.numel()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tot = [0] * len(s_list)
+    r0 = 0
+    while r0 < g.m:
+        r0, pairs = slg.slg_ensemble_stream_window(g, s_list, r0, I, J, O, cap)
+        tot = [a + b for a, b in zip(tot, pairs)]
+    e1.record(stream)
+    e1.synchronize()
+    all_ms = e0.elapsed_time(e1)
+    fs = slg.slg_ensemble_fill_stats(g, reset=True)
+    if made is not None:
+        for t, s in enumerate(s_list):
+            acc = made.setdefault(s, [0] * 6)
+            for c in range(6):
+                acc[c] += int(fs[t][c])
+    if mode_work is not None:  # per-handler work of every list (runs their count)
+        for t, s in enumerate(s_list):
+            mode_work[s] = slg.slg_ensemble_mode_stats(g, s_list, t)
+    filt_ms = [fs[t][4] / 1e3 for t in range(len(s_list))]
+    for t, s in enumerate(s_list):
+        d = per_s.setdefault(s, {"s": s, "wedges": wedges[s], "pairs": tot[t], "ms": [],
+                                 "fill_ms": [], "count_ms_shared": [], "filter_ms": []})
+        ms = filt_ms[t] if t else all_ms - sum(filt_ms[1:])
+        d["filter_ms"].append(filt_ms[t])
+        d["fill_ms"].append(ms)
+        d["count_ms_shared"].append(0.0)
+        d["ms"].append(ms)
+
+
 def bench_ours(args):
     import torch
     import paper_2201_11326_gb300 as slg
@@ -284,7 +325,7 @@ def bench_ours(args):
     idx_d = torch.from_numpy(h.idx).to(dev)
     stream = torch.cuda.Stream(dev)
     wedges = {}
-    if sweep == "ensemble":
+    if sweep in ("ensemble", "stream"):
         # W_s of every s (the metric's work), outside the timed region
         with torch.cuda.stream(stream):
             g0 = slg.slg_load(off_d, idx_d, h.m, h.n, stream=stream)
@@ -305,6 +346,9 @@ def bench_ours(args):
             if sweep == "ensemble":
                 run_sweep_ensemble(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work,
                                    all_lists=ens_all, made=fill_made if timing else None)
+            elif sweep == "stream":
+                run_sweep_stream(slg, g, s_list, (I, J, O), stream, per_s, wedges, mode_work,
+                                 made=fill_made if timing else None)
             else:
                 run_sweep(slg, g, s_list, (I, J, O), stream, per_s, mode_work)
             ks = slg.slg_kernel_stats(g) if timing else None
@@ -374,9 +418,13 @@ def bench_ours(args):
     # four lists; every other counting walk is one per list. Fill: list s is
     # walked in the share of its windows that did not filter it from the list
     # before (fill_made), and its fill kernels write the pairs of those windows.
+    staged = ("sparse", "hubpair")
+
     def one_walk(k):
+        if sweep == "stream":  # one walk of list 0's plan, whatever the handler
+            return True
         return sweep == "ensemble" and (names[k] in ("dense", "wdense") or (
-            names[k] in ("sparse", "hubpair") and len(s_list) <= 4))
+            names[k] in staged and len(s_list) <= 4))
 
     walk_f, pair_f = {}, {}
     for s in s_list:
@@ -414,12 +462,21 @@ def bench_ours(args):
             else:
                 kern = model
             pw = filled_pairs(k) if fill else 0
+            if sweep == "stream" and names[k] in staged:
+                # their fill kernels run in the counting pass, writing 5 B per
+                # pair (id and overlap byte) to the pool; the fill pass walks only
+                # the items the pool could not hold (their bytes not modelled)
+                if fill:
+                    kern, model, pw = 0, 0, 0
+                else:
+                    kern += 5 * mode_work[s_list[0]][k][3]
+                    model += 5 * mode_work[s_list[0]][k][3]
             p = 1 if fill else 0
             cands.append(("fill" if fill else "count", k, kern + 12 * pw, ms_tot[p][k] / args.steps,
                           ln_tot[p][k] / args.steps, model + 12 * pw, pw))
     dom = max(cands, key=lambda c: c[3])
     # the kernel as ncu names it (dense handlers carry a second, ensemble flag)
-    fill_flag = "1" if dom[0] == "fill" else "0"
+    fill_flag = "1" if dom[0] == "fill" or (sweep == "stream" and names[dom[1]] in staged) else "0"
     kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>" if names[dom[1]] in ("dense", "wdense")
              else f"k_{names[dom[1]]}_items<{fill_flag}>")
     dsec = dom[3] / 1e3
@@ -502,6 +559,8 @@ def bench_ours(args):
                    "ensemble_windows": (("all lists per window, later lists filtered from the "
                                          "one before where that reads less") if ens_all else
                                         "each list in its own windows") if sweep == "ensemble"
+                   else ("one-walk windows of every list (rows chosen from a bound on their "
+                         "pairs), later lists filtered from the one before") if sweep == "stream"
                    else None,
                    "m": h.m, "n": h.n, "nnz": h.nnz, "s": s_list, "window_pairs": args.window,
                    "l2": "flushed before each step (512 MiB device write); inputs resident",
@@ -546,7 +605,14 @@ def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s", all_lists=False):
     W = 0
     with torch.cuda.stream(stream):
         g = slg.slg_load(off_h, idx_h, h.m, h.n, stream=stream)
-        if sweep == "ensemble":
+        if sweep == "stream":
+            nwin, r0 = 0, 0
+            tot = [0] * len(s_list)
+            while r0 < h.m:  # |L_s| of every list comes back with each window
+                r0, pairs = slg.slg_ensemble_stream_window(g, s_list, r0, I, J, O, WINDOW)
+                tot = [a + b for a, b in zip(tot, pairs)]
+                nwin += 1
+        elif sweep == "ensemble":
             slg.slg_ensemble_count(g, s_list)
             rows = torch.empty((len(s_list), h.m + 1), dtype=torch.int64).pin_memory()
             for t in ([slg.ENSEMBLE_ALL] if all_lists else range(len(s_list))):
@@ -569,6 +635,12 @@ def e2e(args, slg, h, s_list, stream, bufs, sweep="per_s", all_lists=False):
         g = slg.slg_load(h.off, h.idx, h.m, h.n, stream=stream)
         W = sum(slg.slg_count(g, s)[1] for s in s_list)
         g.free()
+    if sweep == "stream":
+        return {"value": W / dt, "unit": "wedges/s",
+                "h2d_bytes_per_step": int(h.off.nbytes + h.idx.nbytes),
+                "d2h_bytes_per_step": int(nwin * (4 + 8 * len(s_list))), "seconds": round(dt, 3),
+                "note": "lists stay in the device window; host reads each window's end and "
+                        "pairs per list (|L_s| summed)"}
     return {"value": W / dt, "unit": "wedges/s", "h2d_bytes_per_step": int(h.off.nbytes + h.idx.nbytes),
             "d2h_bytes_per_step": int(8 * (h.m + 1) * len(s_list)), "seconds": round(dt, 3),
             "note": "lists stay in the device window; host reads |L_s| and row offsets"}
