@@ -590,11 +590,13 @@ slg_status slg_set_hub_pairs(slg_graph* g, int32_t max_hubs, int64_t min_sparse_
  *
  * Algorithm 3's lists are nested and in the same (i, j) order, so list t holds
  * exactly the pairs of list t-1 with overlap >= s_list[t]. In a window holding
- * every list, list t can be taken from list t-1's segment by a filter (12
- * bytes read per pair of list t-1) instead of walking the window's rows again.
+ * every list, list t can be taken from list t-1's segment by a filter (16
+ * bytes read per pair of list t-1) instead of walking the window's rows again
+ * (about 4 bytes per entry read: wedges through vertices that are not mask
+ * hubs, and the walked entries of hub-pair rows).
  *   mode : -1 (default) whichever reads less: the filter when 6 * (pairs of list
- *          t-1 in the window) < wedges of the window's rows; 0 always walk; 1
- *          always filter.
+ *          t-1 in the window) < the entries a walk of the window's rows reads;
+ *          0 always walk; 1 always filter.
  * The lists are the same either way.
  */
 slg_status slg_set_ensemble_filter(slg_graph* g, int32_t mode);

@@ -702,9 +702,10 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
     // after the first went out as partial-line stores)
     // A list after the first in the window may instead be the list before it
     // filtered by its threshold (the lists are nested and in the same order):
-    // that reads 12 bytes per pair of the list before, a walk about 4 per wedge of
-    // the window's rows, so the filter is taken when 6 * pairs < wedges (or as
-    // slg_set_ensemble_filter says)
+    // that reads 16 bytes per pair of the list before (12 to copy, 4 to count), a
+    // walk about 4 per entry it reads (wedges through vertices that are not mask
+    // hubs; hub-pair rows' walked entries), so the filter is taken when
+    // 6 * pairs < entries (or as slg_set_ensemble_filter says)
     int64_t wrows = -1;
     for (int32_t t = t0; t < t1; ++t) {
         const int32_t u = t - t0;
@@ -713,7 +714,7 @@ slg_status slg_ensemble_build_window(slg_graph* h, const int32_t* s_list, int32_
             if (h->ens_filter > 0) {
                 filt = true;
             } else {
-                if (wrows < 0) wrows = slg::plan_row_wedges(h->g, p, r0, r1, h->st);
+                if (wrows < 0) wrows = slg::plan_row_walk(h->g, p, r0, r1, h->st);
                 filt = 6 * (seg[u] - seg[u - 1]) < wrows;
             }
         }

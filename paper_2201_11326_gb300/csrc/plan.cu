@@ -728,23 +728,38 @@ int64_t plan_sparse_wedges(const GraphDev& g, const Plan& p, cudaStream_t st) {
 }
 
 namespace {
-__global__ void k_row_wedges(const int64_t* __restrict__ W, int32_t r0, int32_t r1,
-                             unsigned long long* __restrict__ out) {
+// Entries a walk of rows [r0, r1) reads: wedges through vertices that are not
+// mask hubs (a mask hub's share of an overlap is a popcount), and for hub-pair
+// rows the entries they walk.
+__global__ void k_row_walk(const int32_t* __restrict__ row_item, const Item* __restrict__ items,
+                           const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                           const int32_t* __restrict__ hubidx, const int32_t* __restrict__ wbeg,
+                           const int32_t* __restrict__ wend, const int64_t* __restrict__ Wp,
+                           int32_t r0, int32_t r1, unsigned long long* __restrict__ out) {
     unsigned long long acc = 0;
     for (int64_t r = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < r1;
-         r += (int64_t)gridDim.x * blockDim.x)
-        acc += (unsigned long long)W[r];
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q0 = row_item[r];
+        if (row_item[r + 1] == q0) continue;
+        if (items[q0].mode == MODE_HUBPAIR && Wp) {
+            acc += (unsigned long long)max(Wp[r], (int64_t)0);
+            continue;
+        }
+        for (int32_t e = off[r]; e < off[r + 1]; ++e)
+            if (hubidx[idx[e]] < 0) acc += (unsigned long long)(wend[e] - wbeg[e]);
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 }  // namespace
 
-int64_t plan_row_wedges(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, cudaStream_t st) {
+int64_t plan_row_walk(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, cudaStream_t st) {
     if (r1 <= r0) return 0;
     unsigned long long* d = dalloc<unsigned long long>(1, st);
     SLG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
-    k_row_wedges<<<grid_for(r1 - r0, 256), 256, 0, st>>>(p.W, r0, r1, d);
+    k_row_walk<<<grid_for(r1 - r0, 256), 256, 0, st>>>(p.row_item, p.items, g.off, g.idx, g.hubidx,
+                                                       p.wbeg, p.wend, p.Wp, r0, r1, d);
     SLG_LAUNCH_CHECK();
     unsigned long long h = 0;
     SLG_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));

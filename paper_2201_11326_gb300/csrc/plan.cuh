@@ -254,8 +254,9 @@ int64_t run_filter_room(const int32_t* I, const int32_t* J, const int32_t* O, in
 // of an ensemble from the list before it.
 void run_filter(const int32_t* I, const int32_t* J, const int32_t* O, int64_t n, int32_t s,
                 int32_t* I2, int32_t* J2, int32_t* O2, int64_t expect, cudaStream_t st);
-// Wedges of rows [r0, r1) of the plan (what a walk of those rows reads).
-int64_t plan_row_wedges(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, cudaStream_t st);
+// Entries a walk of rows [r0, r1) of the plan reads: wedges through vertices
+// that are not mask hubs, and the walked entries of hub-pair rows.
+int64_t plan_row_walk(const GraphDev& g, const Plan& p, int32_t r0, int32_t r1, cudaStream_t st);
 // Ensemble counting pass over the plan's items (p.ens.k lists, thresholds
 // p.ens.s): counts into p.ens.icnt. Lists are filled one at a time by run_fill.
 void run_count_ensemble(const GraphDev& g, const Plan& p, ModeTimer* mt, cudaStream_t st);

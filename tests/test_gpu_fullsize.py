@@ -193,6 +193,65 @@ def test_large_full_size_sampled_rows(large):
         assert np.array_equal(digs[s][rows], odig[:, k]), f"s={s}"
 
 
+def test_large_full_size_one_walk_windows(large):
+    """The large workload as its benchmark runs it: one-walk windows of every
+    list (s in {2, 4, 8, 16}, windows of 2^33 pairs). The windows cover the rows
+    once, in order; the pairs per list add up to the ensemble's |L_s|; and for
+    80 seeded random rows and the 20 rows with the most wedges, each list's
+    pairs of the row (found in the window by binary search on I) have the
+    oracle's count and digest."""
+    torch, h = large
+    dev = torch.device("cuda")
+    s_list = [2, 4, 8, 16]
+    rng = np.random.default_rng([7, 21])
+    offT, idxT = oracle.transpose(h.off, h.idx, h.n)
+    vert = np.repeat(np.arange(h.n, dtype=np.int64), np.diff(offT))
+    later = offT[1:][vert] - np.arange(idxT.size, dtype=np.int64) - 1
+    w = np.bincount(idxT, weights=later, minlength=h.m)
+    heavy = np.argsort(-w, kind="stable")[:20]
+    rows = np.unique(np.concatenate([rng.choice(h.m, size=80, replace=False), heavy]))
+    rows = rows.astype(np.int32)
+    ocount, odig, _ = oracle.rows(h.off, h.idx, rows, s_list)
+    got_count = np.zeros((rows.size, len(s_list)), np.int64)
+    got_dig = np.zeros((rows.size, len(s_list)), np.uint64)
+    g = slg.slg_load(h.off, h.idx, h.m, h.n)
+    try:
+        I = torch.empty(WINDOW, dtype=torch.int32, device=dev)
+        J = torch.empty_like(I)
+        O = torch.empty_like(I)
+        tot = [0] * len(s_list)
+        r0, nwin = 0, 0
+        while r0 < h.m:
+            r1, pairs = slg.slg_ensemble_stream_window(g, s_list, r0, I, J, O, WINDOW)
+            assert r0 < r1 <= h.m
+            assert sum(pairs) <= WINDOW
+            sel = np.flatnonzero((rows >= r0) & (rows < r1))
+            b = 0
+            for t, p in enumerate(pairs):
+                if sel.size and p:
+                    seg = I[b:b + p]
+                    key = torch.from_numpy(rows[sel]).to(dev)
+                    lo = torch.searchsorted(seg, key, right=False).cpu().numpy()
+                    hi = torch.searchsorted(seg, key, right=True).cpu().numpy()
+                    for x, a, z in zip(sel, lo, hi):
+                        got_count[x, t] = z - a
+                        got_dig[x, t] = oracle.list_digest(I[b + a:b + z].cpu().numpy(),
+                                                           J[b + a:b + z].cpu().numpy(),
+                                                           O[b + a:b + z].cpu().numpy())
+                tot[t] += p
+                b += p
+            r0 = r1
+            nwin += 1
+        assert r0 == h.m and nwin > 1
+        want, _ = slg.slg_ensemble_count(g, s_list)
+        assert tot == want
+    finally:
+        g.free()
+    for k, s in enumerate(s_list):
+        assert np.array_equal(got_count[:, k], ocount[:, k]), f"s={s}"
+        assert np.array_equal(got_dig[:, k], odig[:, k]), f"s={s}"
+
+
 # ------------------------------------------------------- the batched workload
 
 @pytest.fixture(scope="module")
