@@ -499,13 +499,22 @@ def bench_ours(args):
                 "launches_per_step": dom[4],
                 "ms_per_launch": round(ms_launch, 3),
                 "kernel_share_of_step": round(dom[3] / (elapsed_ms / args.steps), 4),
-                "model": ("kernel bytes: 12 B/pair written + 4 B per non-hub wedge (adj_s entry) "
+                "model": ("kernel bytes (its fill kernel run as the counting pass of one-walk "
+                          "windows): 4 B per entry walked (non-hub wedges and hub-pair list hits, "
+                          "or wedges for the sparse accumulator) + 8 B/incidence + 5 B per pair "
+                          "staged (id and overlap byte)"
+                          if sweep == "stream" and names[dom[1]] in staged else
+                          "kernel bytes: 12 B/pair written + 4 B per non-hub wedge (adj_s entry) "
                           "+ 4 B per candidate partner scanned (hub mask) + 8 B per incidence "
                           "(wedge-range bounds)" if names[dom[1]] in ("dense", "wdense") else
                           "kernel bytes: 4 B per entry walked (non-hub wedges and hub-pair list "
                           "hits) + 8 B/incidence + 12 B/pair written" if names[dom[1]] == "hubpair"
                           else "kernel bytes: 4 B/wedge + 8 B/incidence + 12 B/pair written"),
-                "walks": ("one counting walk for every list where the ensemble counts them "
+                "walks": ("one-walk windows: sparse-accumulator and hub-pair rows walked once "
+                          "(counting and staging list 0); table and dense rows counted once before "
+                          "the windows and filled in them; later lists filtered"
+                          if sweep == "stream" else
+                          "one counting walk for every list where the ensemble counts them "
                           "together; fill walks only of the windows that walked the list (the "
                           "others filter it from the list before)"),
                 "frac_above_1": frac > 1.0,
