@@ -479,7 +479,9 @@ def bench_ours(args):
     dom = max(cands, key=lambda c: c[3])
     # the kernel as ncu names it (dense handlers carry a second, ensemble flag)
     fill_flag = "1" if dom[0] == "fill" or (sweep == "stream" and names[dom[1]] in staged) else "0"
-    kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>" if names[dom[1]] in ("dense", "wdense")
+    # (the dense, sparse-accumulator and hub-pair kernels carry a second, ensemble flag)
+    kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>"
+             if names[dom[1]] in ("dense", "wdense", "sparse", "hubpair")
              else f"k_{names[dom[1]]}_items<{fill_flag}>")
     dsec = dom[3] / 1e3
     achieved = dom[2] / dsec / 1e9 if dom[3] > 0 else 0.0
