@@ -477,7 +477,7 @@ def bench_ours(args):
             cands.append(("fill" if fill else "count", k, kern + 12 * pw, ms_tot[p][k] / args.steps,
                           ln_tot[p][k] / args.steps, model + 12 * pw, pw))
     dom = max(cands, key=lambda c: c[3])
-    # the kernel as ncu names it (dense handlers carry a second, ensemble flag)
+    # the kernel as ncu names it
     fill_flag = "1" if dom[0] == "fill" or (sweep == "stream" and names[dom[1]] in staged) else "0"
     # (the dense, sparse-accumulator and hub-pair kernels carry a second, ensemble flag)
     kname = (f"k_{names[dom[1]]}_items<{fill_flag}, 0>"
