@@ -63,9 +63,9 @@ def parse_args():
                     help="the s sweep as one ensemble (medium default), as one-walk windows of "
                          "every list (large default), or one s at a time")
     ap.add_argument("--ens-windows", choices=["per_list", "all"], default=None,
-                    help="ensemble sweep: each list in its own windows (medium default), or "
-                         "windows of every list, the later lists filtered from the one before "
-                         "where that reads less (large default)")
+                    help="--sweep ensemble: each list in its own windows (the medium "
+                         "default), or windows of every list, the later lists filtered from the "
+                         "one before where that reads less (the large default)")
     ap.add_argument("--queries", type=int, default=1000, help="serve workload: queries per rate")
     ap.add_argument("--degree-cap", type=int, default=100_000,
                     help="large workload: cap on the Chung-Lu target degree (scale it with --m "
