@@ -304,6 +304,80 @@ def run_sweep_stream(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None
         d["ms"].append(ms)
 
 
+STAGED_MODES = ("sparse", "hubpair")  # handlers whose fill kernels can stage pairs
+
+
+def walk_candidates(names, mode_work, s_list, sweep, fill_made, ms_tot, ln_tot, steps):
+    """Roofline candidates of a step: for each handler k and pass, (pass, k, kernel
+    bytes per step, ms per step, launches per step, section 8(d) model bytes per
+    step, pairs the kernel wrote per step), from the per-list handler work
+    mode_work[s][k] (slg_ensemble_mode_stats columns), the walks each list took
+    (fill_made[s]: windows and pairs walked, windows and pairs filtered, ...) and
+    the handlers' CUDA-event totals ms_tot/ln_tot[pass][k] over `steps` steps.
+
+    Which walks ran. Counting: an ensemble's dense handlers count every list in
+    one walk, and so do its sparse-accumulator and hub-pair handlers for up to
+    four lists; one-walk windows walk list 0's plan once whatever the handler;
+    every other counting walk is one per list. Fill: list s is walked in the
+    share of its windows that did not filter it from the list before, and its
+    fill kernels write the pairs of those windows. In one-walk windows the
+    sparse-accumulator and hub-pair fill kernels run as the counting pass,
+    writing 5 B per pair (id and overlap byte) to the pool; their fill pass walks
+    only the items the pool could not hold (not modelled).
+
+    Returns (candidates, one_walk(k), walk_f[s])."""
+    def one_walk(k):
+        if sweep == "stream":
+            return True
+        return sweep == "ensemble" and (names[k] in ("dense", "wdense") or (
+            names[k] in STAGED_MODES and len(s_list) <= 4))
+
+    walk_f, pair_f = {}, {}
+    for s in s_list:
+        m = fill_made.get(s)
+        wins = (m[0] + m[2]) if m else 0
+        walk_f[s] = m[0] / wins if wins else 1.0
+        made = (m[1] + m[3]) if m else 0
+        pair_f[s] = m[1] / made if made else 1.0
+
+    def walked(col, k, fill):
+        if not fill:
+            if one_walk(k):
+                return mode_work[s_list[0]][k][col]
+            return sum(mode_work[s][k][col] for s in s_list)
+        return sum(walk_f[s] * mode_work[s][k][col] for s in s_list)
+
+    def filled_pairs(k):
+        return sum(pair_f[s] * mode_work[s][k][3] for s in s_list)
+
+    cands = []
+    for k in range(len(names)):
+        for fill in (False, True):
+            w, inc, nonhub = walked(1, k, fill), walked(2, k, fill), walked(4, k, fill)
+            model = 4 * w + 8 * inc
+            if names[k] in ("dense", "wdense"):
+                # what these kernels move: adj_s entries of non-hub wedges only, one
+                # 4-byte hub mask per candidate partner scanned, the row's
+                # wedge-range bounds; hub wedges are popcounts and read nothing
+                kern = 4 * nonhub + 4 * walked(6 if fill else 5, k, fill) + 8 * inc
+            elif names[k] == "hubpair":
+                # entries walked (non-hub wedges + hub-pair list hits) and their bounds
+                kern = 4 * nonhub + 8 * inc
+            else:
+                kern = model
+            pw = filled_pairs(k) if fill else 0
+            if sweep == "stream" and names[k] in STAGED_MODES:
+                if fill:
+                    kern, model, pw = 0, 0, 0
+                else:
+                    kern += 5 * mode_work[s_list[0]][k][3]
+                    model += 5 * mode_work[s_list[0]][k][3]
+            p = 1 if fill else 0
+            cands.append(("fill" if fill else "count", k, kern + 12 * pw, ms_tot[p][k] / steps,
+                          ln_tot[p][k] / steps, model + 12 * pw, pw))
+    return cands, one_walk, walk_f
+
+
 def bench_ours(args):
     import torch
     import paper_2201_11326_gb300 as slg
@@ -415,67 +489,9 @@ def bench_ours(args):
                 ln_tot[p][k] += ln[p][k]
 
     names = list(slg.MODE_NAMES)
-    # Which walks ran. Counting: an ensemble's dense handlers count every list in
-    # one walk, and so do its sparse-accumulator and hub-pair handlers for up to
-    # four lists; every other counting walk is one per list. Fill: list s is
-    # walked in the share of its windows that did not filter it from the list
-    # before (fill_made), and its fill kernels write the pairs of those windows.
-    staged = ("sparse", "hubpair")
-
-    def one_walk(k):
-        if sweep == "stream":  # one walk of list 0's plan, whatever the handler
-            return True
-        return sweep == "ensemble" and (names[k] in ("dense", "wdense") or (
-            names[k] in staged and len(s_list) <= 4))
-
-    walk_f, pair_f = {}, {}
-    for s in s_list:
-        m = fill_made.get(s)
-        wins = (m[0] + m[2]) if m else 0
-        walk_f[s] = m[0] / wins if wins else 1.0
-        made = (m[1] + m[3]) if m else 0
-        pair_f[s] = m[1] / made if made else 1.0
-
-    def walked(col, k, fill):
-        if not fill:
-            if one_walk(k):
-                return mode_work[s_list[0]][k][col]
-            return sum(mode_work[s][k][col] for s in s_list)
-        return sum(walk_f[s] * mode_work[s][k][col] for s in s_list)
-
-    def filled_pairs(k):
-        return sum(pair_f[s] * mode_work[s][k][3] for s in s_list)
-
-    # candidates: (pass, mode, kernel bytes per step, ms per step, launches per step,
-    # section 8(d) model bytes per step, pairs the kernel wrote per step)
-    cands = []
-    for k in range(NM):
-        for fill in (False, True):
-            w, inc, nonhub = walked(1, k, fill), walked(2, k, fill), walked(4, k, fill)
-            model = 4 * w + 8 * inc
-            if names[k] in ("dense", "wdense"):
-                # what these kernels move: adj_s entries of non-hub wedges only, one
-                # 4-byte hub mask per candidate partner scanned, the row's
-                # wedge-range bounds; hub wedges are popcounts and read nothing
-                kern = 4 * nonhub + 4 * walked(6 if fill else 5, k, fill) + 8 * inc
-            elif names[k] == "hubpair":
-                # entries walked (non-hub wedges + hub-pair list hits) and their bounds
-                kern = 4 * nonhub + 8 * inc
-            else:
-                kern = model
-            pw = filled_pairs(k) if fill else 0
-            if sweep == "stream" and names[k] in staged:
-                # their fill kernels run in the counting pass, writing 5 B per
-                # pair (id and overlap byte) to the pool; the fill pass walks only
-                # the items the pool could not hold (their bytes not modelled)
-                if fill:
-                    kern, model, pw = 0, 0, 0
-                else:
-                    kern += 5 * mode_work[s_list[0]][k][3]
-                    model += 5 * mode_work[s_list[0]][k][3]
-            p = 1 if fill else 0
-            cands.append(("fill" if fill else "count", k, kern + 12 * pw, ms_tot[p][k] / args.steps,
-                          ln_tot[p][k] / args.steps, model + 12 * pw, pw))
+    cands, one_walk, walk_f = walk_candidates(names, mode_work, s_list, sweep, fill_made,
+                                              ms_tot, ln_tot, args.steps)
+    staged = STAGED_MODES
     dom = max(cands, key=lambda c: c[3])
     # the kernel as ncu names it
     fill_flag = "1" if dom[0] == "fill" or (sweep == "stream" and names[dom[1]] in staged) else "0"

@@ -77,3 +77,70 @@ def test_traffic_scaled_by_pairs_and_dropped_on_change(tmp_path, monkeypatch):
     rec["source_sha"] = "0" * 16
     json.dump({k: rec}, open(root / "profiles" / "traffic.json", "w"))
     assert bench.profiled_traffic(k, 1e12, 1e9) is None
+
+
+NAMES = ["warp", "block", "dense", "wdense", "sparse", "wsparse", "hubpair"]
+
+
+def work(rows=0, w=0, inc=0, pairs=0, nonhub=0, scan_c=0, scan_f=0):
+    return [rows, w, inc, pairs, nonhub, scan_c, scan_f]
+
+
+def mode_work_of(per_list):
+    """per_list[s] = {handler name: work(...)}; other handlers do nothing."""
+    return {s: [per_list[s].get(n, work()) for n in NAMES] for s in per_list}
+
+
+def cand(cands, pas, name):
+    return next(c for c in cands if c[0] == pas and c[1] == NAMES.index(name))
+
+
+def zero_times():
+    return [[1.0] * len(NAMES), [1.0] * len(NAMES)], [[1] * len(NAMES), [1] * len(NAMES)]
+
+
+def test_walk_candidates_one_walk_windows():
+    # one-walk windows: the hub-pair counting pass walks list 0's plan once and
+    # stages its pairs (5 B each); its fill pass is not charged; list 4 is
+    # filtered, so nothing of it is charged to the walks
+    mw = mode_work_of({2: {"hubpair": work(w=1000, inc=10, pairs=100, nonhub=300)},
+                       4: {"hubpair": work(w=1000, inc=10, pairs=7, nonhub=300)}})
+    made = {2: [3, 100, 0, 0, 0, 0], 4: [0, 0, 3, 7, 5, 100]}
+    ms, ln = zero_times()
+    cands, one_walk, walk_f = bench.walk_candidates(NAMES, mw, [2, 4], "stream", made, ms, ln, 1)
+    assert cand(cands, "count", "hubpair")[2] == 4 * 300 + 8 * 10 + 5 * 100
+    assert cand(cands, "fill", "hubpair")[2] == 0
+    assert walk_f == {2: 1.0, 4: 0.0}
+    assert all(one_walk(k) for k in range(len(NAMES)))
+
+
+def test_walk_candidates_ensemble_filter_and_per_s():
+    # an ensemble in windows of every list: one counting walk of the sparse
+    # accumulator for both lists; list 2 walked in every window, list 3 in half
+    # of them (its pairs split the same way between fill and filter)
+    mw = mode_work_of({2: {"sparse": work(w=800, inc=20, pairs=50)},
+                       3: {"sparse": work(w=800, inc=20, pairs=20)}})
+    made = {2: [4, 50, 0, 0, 0, 0], 3: [2, 12, 2, 8, 1, 30]}
+    ms, ln = zero_times()
+    cands, _, walk_f = bench.walk_candidates(NAMES, mw, [2, 3], "ensemble", made, ms, ln, 1)
+    assert cand(cands, "count", "sparse")[2] == 4 * 800 + 8 * 20
+    walk = 4 * 800 + 8 * 20
+    assert cand(cands, "fill", "sparse")[2] == walk * (1 + 0.5) + 12 * (50 + 20 * 12 / 20)
+    assert walk_f == {2: 1.0, 3: 0.5}
+    # one s at a time: every list counted and filled by its own walk
+    cands, one_walk, _ = bench.walk_candidates(NAMES, mw, [2, 3], "per_s", {}, ms, ln, 2)
+    assert cand(cands, "count", "sparse")[2] == 2 * walk
+    assert cand(cands, "fill", "sparse")[2] == 2 * walk + 12 * 70
+    assert cand(cands, "fill", "sparse")[3] == 0.5  # ms per step over 2 steps
+    assert not any(one_walk(k) for k in range(len(NAMES)))
+
+
+def test_walk_candidates_dense_bytes():
+    # dense handlers: non-hub wedges, one hub mask per scanned partner, bounds
+    mw = mode_work_of({1: {"wdense": work(w=10**6, inc=40, pairs=900, nonhub=15000, scan_c=3000,
+                                          scan_f=2500)}})
+    ms, ln = zero_times()
+    cands, _, _ = bench.walk_candidates(NAMES, mw, [1], "ensemble", {}, ms, ln, 1)
+    assert cand(cands, "count", "wdense")[2] == 4 * 15000 + 4 * 3000 + 8 * 40
+    assert cand(cands, "fill", "wdense")[2] == 4 * 15000 + 4 * 2500 + 8 * 40 + 12 * 900
+    assert cand(cands, "fill", "wdense")[5] == 4 * 10**6 + 8 * 40 + 12 * 900
