@@ -304,6 +304,16 @@ def run_sweep_stream(slg, g, s_list, bufs, stream, per_s, wedges, mode_work=None
         d["ms"].append(ms)
 
 
+def sweep_of(args):
+    """(sweep, windows of every list?) for the workload: the large sweep as one-walk
+    windows (its hub-pair and sparse-accumulator rows dominate and are walked
+    once), the medium one as an ensemble in per-list windows; --sweep and
+    --ens-windows override."""
+    sweep = args.sweep or ("stream" if args.workload == "large" else "ensemble")
+    ens_all = (args.ens_windows or ("all" if args.workload == "large" else "per_list")) == "all"
+    return sweep, ens_all
+
+
 STAGED_MODES = ("sparse", "hubpair")  # handlers whose fill kernels can stage pairs
 
 
@@ -392,10 +402,7 @@ def bench_ours(args):
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
     h, s_list, wl_text, metric, cpu_rows = workload_spec(args)
-    # the large sweep as one-walk windows (its hub-pair and sparse-accumulator
-    # rows dominate and are walked once); the medium one as an ensemble
-    sweep = args.sweep or ("stream" if args.workload == "large" else "ensemble")
-    ens_all = (args.ens_windows or ("all" if args.workload == "large" else "per_list")) == "all"
+    sweep, ens_all = sweep_of(args)
     # inputs resident in HBM before the timed region
     off_d = torch.from_numpy(h.off).to(dev)
     idx_d = torch.from_numpy(h.idx).to(dev)

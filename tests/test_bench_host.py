@@ -144,3 +144,11 @@ def test_walk_candidates_dense_bytes():
     assert cand(cands, "count", "wdense")[2] == 4 * 15000 + 4 * 3000 + 8 * 40
     assert cand(cands, "fill", "wdense")[2] == 4 * 15000 + 4 * 2500 + 8 * 40 + 12 * 900
     assert cand(cands, "fill", "wdense")[5] == 4 * 10**6 + 8 * 40 + 12 * 900
+
+
+def test_default_sweeps():
+    assert bench.sweep_of(args(sweep=None, ens_windows=None)) == ("ensemble", False)
+    assert bench.sweep_of(args(workload="large", sweep=None, ens_windows=None)) == ("stream", True)
+    assert bench.sweep_of(args(sweep="per_s", ens_windows="all")) == ("per_s", True)
+    assert bench.sweep_of(args(workload="large", sweep="ensemble", ens_windows="per_list")) == \
+        ("ensemble", False)
