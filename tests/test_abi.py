@@ -84,3 +84,31 @@ def test_no_gpu_means_an_error_not_a_cpu_fallback(lib):
     import numpy as np
     with pytest.raises(slg.SlgError):
         slg.slg_load(np.array([0, 2, 3], np.int32), np.array([0, 1, 1], np.int32), 2, 2)
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    # the boundary is plain C: it compiles alone as C99 and as C++, without warnings
+    import shutil
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "slg.h"\nint main(void) { return slg_version() > 0 ? 0 : 1; }\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, extra in (("gcc", ["-std=c99"]), ("g++", ["-std=c++17", "-x", "c++"])):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, *extra, "-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(src),
+                            "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def test_new_entry_points_reject_null_without_device(lib):
+    i32 = ctypes.c_int32()
+    i64 = ctypes.c_int64()
+    s = (ctypes.c_int32 * 2)(2, 4)
+    assert lib.slg_stream_window(None, 2, 0, None, None, None, 16, ctypes.byref(i32),
+                                 ctypes.byref(i64)) == slg.SLG_EINVAL
+    assert lib.slg_ensemble_stream_window(None, s, 2, 0, None, None, None, 16, ctypes.byref(i32),
+                                          ctypes.byref(i64)) == slg.SLG_EINVAL
+    assert lib.slg_ensemble_fill_stats(None, 0, None) == slg.SLG_EINVAL
+    assert lib.slg_set_ensemble_filter(None, 0) == slg.SLG_EINVAL
+    assert lib.slg_set_staging(None, -1) == slg.SLG_EINVAL
